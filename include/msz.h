@@ -1,0 +1,183 @@
+/*
+ * msz.h -- C ABI of the GB300 correction engine for piecewise-linear
+ * Morse-Smale segmentations under error-bounded lossy compression
+ * (pMSz, arXiv 2601.01787).
+ *
+ * Problem (Sec. III-B): given the original field f, its decompressed copy
+ * fhat and a global error bound xi, find a corrected field g <= fhat (edits
+ * only lower values, Eq. 1) with |f_i - g_i| <= xi everywhere such that every
+ * vertex has the same extremum status and the same steepest ascending and
+ * descending neighbours in g as in f (the relaxed sufficient condition of
+ * Sec. IV-A), which preserves the segmentation.
+ *
+ * Conventions shared by every entry point:
+ *   - Grids are regular 2D or 3D, x fastest: linear index i = x + nx*(y + ny*z).
+ *     The piecewise-linear interpolant lives on the Kuhn (Freudenthal)
+ *     triangulation along the main diagonal (Sec. III-A "constant
+ *     triangular/tetrahedral mesh"): neighbour offsets are d and -d for
+ *     d in {0,1}^n \ {0}, 6 neighbours in 2D and 14 in 3D.
+ *   - Neighbour slots (the numbers stored in direction codes):
+ *       3D: 0 (+1,0,0) 1 (0,+1,0) 2 (0,0,+1) 3 (+1,+1,0) 4 (+1,0,+1)
+ *           5 (0,+1,+1) 6 (+1,+1,+1), 7..13 the negatives of 0..6 in order;
+ *       2D: 0 (+1,0) 1 (0,+1) 2 (+1,+1), 3..5 the negatives of 0..2.
+ *   - Order (Sec. III-A assumes distinct values; ties are broken by index):
+ *     j is above i  <=>  v_j > v_i  or  (v_j == v_i and j > i).  -0 == +0.
+ *   - Error bound: L_i = smallest float32 >= f_i - xi, U_i = largest float32
+ *     <= f_i + xi (exact real arithmetic); inputs must satisfy
+ *     L_i <= fhat_i <= U_i and be finite.
+ *   - Pointers named d_* are DEVICE pointers of the current CUDA device;
+ *     pointers named h_* are HOST pointers (pinned memory is fastest).  The
+ *     caller owns every buffer; the library allocates no device memory: all
+ *     scratch lives in the caller's workspace.
+ *   - Every call is ordered on `stream` (NULL = legacy default stream).  Calls
+ *     that return results to host memory (counts, stats, status) synchronize
+ *     that stream before returning; this is stated per call.
+ *   - No call throws or aborts; failures come back as msz_status.  After
+ *     MSZ_ERR_CUDA the CUDA context may be unusable (sticky CUDA error).
+ *   - At most MSZ_MAX_VERTICES vertices per field (labels are int32, edit
+ *     indices uint32).
+ */
+#ifndef MSZ_H
+#define MSZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* = cudaStream_t */
+typedef struct CUstream_st *msz_stream_t;
+
+#define MSZ_SELF 15                    /* code nibble of an extremum */
+#define MSZ_MAX_VERTICES 2147483647LL  /* 2^31 - 1 */
+#define MSZ_MAX_SWEEPS_LIMIT 65536     /* upper limit of msz_options.max_sweeps */
+#define MSZ_SMALL_WORKSPACE 65536      /* bytes needed by msz_segment / msz_compare */
+
+typedef enum {
+    MSZ_OK = 0,
+    MSZ_ERR_INVALID_ARG = 1,  /* null pointer, bad grid, xi < 0 or not finite, bad option */
+    MSZ_ERR_INPUT_BOUND = 2,  /* some value not finite, or fhat (or g_init) outside [L_i, U_i] */
+    MSZ_ERR_CAPACITY = 3,     /* loop converged but the edit list did not fit; *edit_count = needed */
+    MSZ_ERR_WORKSPACE = 4,    /* workspace too small (or NULL) for this grid */
+    MSZ_ERR_CUDA = 5,         /* a CUDA runtime call or launch failed */
+    MSZ_ERR_MAX_SWEEPS = 6,   /* still distorted after max_sweeps sweeps */
+    MSZ_ERR_TIMEOUT = 7,      /* a bounded device-side wait ran out (grid barrier) */
+    MSZ_STUCK = 8,            /* a sweep found distortions but every target was at its floor */
+    MSZ_ERR_UNSUPPORTED = 9   /* no sm_103a device / not enough co-resident blocks */
+} msz_status;
+
+typedef struct {
+    int32_t ndim;     /* 2 or 3 */
+    int32_t reserved; /* 0 */
+    int64_t nx, ny, nz; /* >= 1 each; nz == 1 when ndim == 2 */
+} msz_grid;
+
+/* Eq. 1 leaves the edit amount delta open.  HALVE moves g halfway to its floor
+ * L (s = g - L; h = g - 0.5*s; h = max(h, L); h = L when h is not below g),
+ * SNAP moves it to the floor in one edit (Fig. nonextrema (c): 0.1 -> 0). */
+typedef enum { MSZ_RULE_HALVE = 0, MSZ_RULE_SNAP = 1 } msz_rule;
+
+typedef struct {
+    int32_t rule;             /* msz_rule; default HALVE */
+    int32_t reserved;         /* 0 */
+    int64_t max_sweeps;       /* <= 0: MSZ_MAX_SWEEPS_LIMIT; else 1..MSZ_MAX_SWEEPS_LIMIT */
+    int64_t dense_min_items;  /* next sweep scans the whole grid when 8*targets + distorted
+                                 >= this; 0: N/16 (default); -1: always use the worklist */
+    const float *d_g_init;    /* NULL: start from fhat.  Else N floats, each in [L_i, U_i]: a
+                                 proposed start (the learned proposal); edits are still
+                                 reported against fhat */
+    int64_t *h_sweep_log;     /* NULL, or 4*log_capacity int64 filled per sweep k with
+                                 |worklist_k|, distorted_k, distinct targets_k, changed_k */
+    int64_t log_capacity;
+    int64_t *h_timeline;      /* NULL, or 2*log_capacity int64 (needs h_sweep_log): device
+                                 time in ns from the start of the correction kernel to the
+                                 end of sweep k's detection and of its edit phase (-1: none) */
+} msz_options;
+
+typedef struct {
+    int64_t sweeps;           /* sweeps that applied edits (0: fhat already correct) */
+    int64_t edits;            /* total value decreases applied */
+    int64_t edited;           /* distinct vertices with g != fhat (= edit list length) */
+    int64_t first_distorted;  /* distorted vertices found in sweep 0 */
+    int64_t left;             /* distorted vertices left (STUCK / MAX_SWEEPS), else 0 */
+    int64_t examined;         /* vertices examined over all sweeps (dense sweeps count N) */
+    int64_t dense_sweeps;     /* sweeps run as whole-grid scans, sweep 0 included */
+    int64_t kernel_ns;        /* device time of the correction kernel (globaltimer) */
+} msz_stats;
+
+/* Bytes of device workspace msz_correct needs for this grid (about 13.5 bytes
+ * per vertex plus 1.2 MB); 0 for an invalid grid. */
+size_t msz_workspace_size(msz_grid grid);
+
+/* Sec. IV-A / Sec. III-A: steepest-neighbour codes of one field.
+ * codes[i] low nibble = slot of n_max(i) = argmax over N(i) when it is above i,
+ * else MSZ_SELF (i is a maximum); high nibble = slot of n_min(i) when below i,
+ * else MSZ_SELF (i is a minimum).  d_v: N floats (finite); d_codes: N bytes.
+ * Asynchronous (no host sync). */
+msz_status msz_directions(const float *d_v, msz_grid grid, uint8_t *d_codes, msz_stream_t stream);
+
+/* The correction loop (Sec. III-B iterative edit strategy with the redesigned
+ * C-loop of Sec. IV-A, synchronous Jacobi sweeps):
+ *   sweep k detects every vertex whose code in g^k differs from its code in f
+ *   and edits, once each (Eq. 1), the distinct targets:
+ *     ascending mismatch  -> the vertex itself when g makes it a maximum (FPmax),
+ *                            else its largest neighbour in g (FNmax / spurious max);
+ *     descending mismatch -> the vertex itself when f makes it a minimum (FNmin),
+ *                            else its smallest neighbour in f (FPmin / original min);
+ *   it stops when nothing is distorted (MSZ_OK), when a sweep changes nothing
+ *   (MSZ_STUCK) or after max_sweeps sweeps (MSZ_ERR_MAX_SWEEPS).
+ * Inputs: d_f, d_fhat (N floats each, finite, L_i <= fhat_i <= U_i), xi >= 0.
+ * Output: d_out (N floats, must not alias the inputs) = g; the edit list
+ *   d_edit_idx / d_edit_delta (edit_capacity entries each, may be NULL when
+ *   edit_capacity == 0): every i with g_i != fhat_i (bitwise), ascending i,
+ *   delta = float32(g_i - fhat_i); *h_edit_count = the number of such i (may
+ *   exceed edit_capacity: then MSZ_ERR_CAPACITY on an otherwise OK run; d_out
+ *   is complete either way).
+ * Workspace: d_workspace of at least msz_workspace_size(grid) bytes, 256-byte
+ *   aligned, not used by any concurrent call.
+ * Synchronizes `stream` before returning (status, counts and stats are read back). */
+msz_status msz_correct(const float *d_f, const float *d_fhat, float xi, msz_grid grid, float *d_out,
+                       uint32_t *d_edit_idx, float *d_edit_delta, int64_t edit_capacity,
+                       int64_t *h_edit_count, const msz_options *opt, msz_stats *h_stats,
+                       void *d_workspace, size_t workspace_bytes, msz_stream_t stream);
+
+/* Bytes of device workspace msz_correct_host needs: msz_workspace_size plus
+ * room for f, fhat, g and an edit list of edit_capacity entries. */
+size_t msz_host_workspace_size(msz_grid grid, int64_t edit_capacity);
+
+/* msz_correct with HOST buffers: copies h_f and h_fhat to the device, runs the
+ * correction, and copies g and the edit list back into h_out / h_edit_idx /
+ * h_edit_delta.  Same semantics and statuses as msz_correct.  Synchronizes
+ * `stream`. */
+msz_status msz_correct_host(const float *h_f, const float *h_fhat, float xi, msz_grid grid, float *h_out,
+                            uint32_t *h_edit_idx, float *h_edit_delta, int64_t edit_capacity,
+                            int64_t *h_edit_count, const msz_options *opt, msz_stats *h_stats,
+                            void *d_workspace, size_t workspace_bytes, msz_stream_t stream);
+
+/* Sec. III-A ascending/descending segmentations, for verification:
+ * d_max_label[i] = index of the maximum reached by following n_max (the low
+ * nibble of d_codes) from i; d_min_label[i] likewise through n_min.  Computed
+ * by pointer jumping to a fixed point.  Either label pointer may be NULL.
+ * Workspace: at least MSZ_SMALL_WORKSPACE bytes.  Synchronizes `stream`. */
+msz_status msz_segment(const uint8_t *d_codes, msz_grid grid, int32_t *d_min_label, int32_t *d_max_label,
+                       void *d_workspace, size_t workspace_bytes, msz_stream_t stream);
+
+/* Sec. V-C verification counts between the segmentations of f and g:
+ * h_counts[0] wrongly labelled vertices (either label differs), [1] false
+ * positive maxima (maximum in g only), [2] false negative maxima, [3] false
+ * positive minima, [4] false negative minima.  All device arrays hold n
+ * entries.  Workspace: at least MSZ_SMALL_WORKSPACE bytes.  Synchronizes `stream`. */
+msz_status msz_compare(const uint8_t *d_codes_f, const uint8_t *d_codes_g, const int32_t *d_min_f,
+                       const int32_t *d_max_f, const int32_t *d_min_g, const int32_t *d_max_g, int64_t n,
+                       int64_t h_counts[5], void *d_workspace, size_t workspace_bytes, msz_stream_t stream);
+
+/* Human-readable name of a status. */
+const char *msz_status_str(msz_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSZ_H */

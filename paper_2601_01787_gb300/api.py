@@ -1,0 +1,287 @@
+"""Python binding of the C ABI in include/msz.h (ctypes).
+
+Argument marshalling only: every step of the correction runs in the CUDA
+kernels of libmsz.so.  PyTorch provides device memory and the stream.  There
+is no CPU fallback: loading fails loudly when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import _build
+
+OK, ERR_INVALID_ARG, ERR_INPUT_BOUND, ERR_CAPACITY, ERR_WORKSPACE, ERR_CUDA = 0, 1, 2, 3, 4, 5
+ERR_MAX_SWEEPS, ERR_TIMEOUT, STUCK, ERR_UNSUPPORTED = 6, 7, 8, 9
+RULES = {"halve": 0, "snap": 1}
+SELF = 15
+MAX_SWEEPS_LIMIT = 65536
+SMALL_WORKSPACE = 65536
+
+
+class MszError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_str(status)}")
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("rule", ctypes.c_int32), ("reserved", ctypes.c_int32), ("max_sweeps", ctypes.c_int64),
+                ("dense_min_items", ctypes.c_int64), ("d_g_init", ctypes.c_void_p),
+                ("h_sweep_log", ctypes.c_void_p), ("log_capacity", ctypes.c_int64),
+                ("h_timeline", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("sweeps", "edits", "edited", "first_distorted", "left",
+                                              "examined", "dense_sweeps", "kernel_ns")]
+
+    def as_dict(self) -> dict:
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libmsz.so (building it first when asked).  Raises if it cannot load."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build_if_missing else _build.LIB
+        if not os.path.exists(path):
+            raise ImportError(f"libmsz.so not found at {path}; run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        P, I64, SZ = ctypes.c_void_p, ctypes.c_int64, ctypes.c_size_t
+        st = ctypes.c_int
+        lib.msz_workspace_size.argtypes = [Grid]
+        lib.msz_workspace_size.restype = SZ
+        lib.msz_host_workspace_size.argtypes = [Grid, I64]
+        lib.msz_host_workspace_size.restype = SZ
+        lib.msz_directions.argtypes = [P, Grid, P, P]
+        lib.msz_directions.restype = st
+        lib.msz_correct.argtypes = [P, P, ctypes.c_float, Grid, P, P, P, I64, ctypes.POINTER(I64),
+                                    ctypes.POINTER(Options), ctypes.POINTER(Stats), P, SZ, P]
+        lib.msz_correct.restype = st
+        lib.msz_correct_host.argtypes = lib.msz_correct.argtypes
+        lib.msz_correct_host.restype = st
+        lib.msz_segment.argtypes = [P, Grid, P, P, P, SZ, P]
+        lib.msz_segment.restype = st
+        lib.msz_compare.argtypes = [P, P, P, P, P, P, I64, ctypes.POINTER(I64), P, SZ, P]
+        lib.msz_compare.restype = st
+        lib.msz_status_str.argtypes = [st]
+        lib.msz_status_str.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def status_str(status: int) -> str:
+    return load().msz_status_str(int(status)).decode()
+
+
+def grid_of(shape) -> Grid:
+    """C grid for a tensor shape (ny, nx) or (nz, ny, nx), x fastest."""
+    if len(shape) == 2:
+        return Grid(2, 0, int(shape[1]), int(shape[0]), 1)
+    if len(shape) == 3:
+        return Grid(3, 0, int(shape[2]), int(shape[1]), int(shape[0]))
+    raise ValueError("grid must be 2D or 3D")
+
+
+def _dptr(t: torch.Tensor | None) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+_ws_cache: dict = {}
+
+
+def workspace(nbytes: int, device=None) -> torch.Tensor:
+    """A cached device byte buffer of at least nbytes (256-byte aligned)."""
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else torch.device(device).index)
+    key = dev.index
+    buf = _ws_cache.get(key)
+    if buf is None or buf.numel() < nbytes:
+        _ws_cache.pop(key, None)
+        buf = torch.empty(max(int(nbytes), SMALL_WORKSPACE), dtype=torch.uint8, device=dev)
+        assert buf.data_ptr() % 256 == 0
+        _ws_cache[key] = buf
+    return buf
+
+
+def workspace_size(shape) -> int:
+    return int(load().msz_workspace_size(grid_of(shape)))
+
+
+def directions(v: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Packed steepest-neighbour codes of a float32 CUDA field (msz_directions)."""
+    assert v.dtype == torch.float32
+    if out is None:
+        out = torch.empty(v.shape, dtype=torch.uint8, device=v.device)
+    st = load().msz_directions(_dptr(v), grid_of(v.shape), _dptr(out), _stream(stream))
+    if st != OK:
+        raise MszError(st, "msz_directions")
+    return out
+
+
+@dataclass
+class CorrectResult:
+    status: int
+    out: object
+    edit_idx: object
+    edit_delta: object
+    edit_count: int
+    stats: dict
+    sweep_log: np.ndarray = field(default_factory=lambda: np.zeros((0, 4), np.int64))
+
+    @property
+    def ok(self) -> bool:
+        return self.status == OK
+
+
+def _options(rule, max_sweeps, dense_min_items, g_init, log_capacity):
+    log = np.zeros(max(4 * log_capacity, 4), dtype=np.int64)
+    tl = np.full(max(2 * log_capacity, 2), -1, dtype=np.int64)
+    opt = Options(RULES[rule] if isinstance(rule, str) else int(rule), 0, int(max_sweeps), int(dense_min_items),
+                  _dptr(g_init), log.ctypes.data if log_capacity else None, int(log_capacity),
+                  tl.ctypes.data if log_capacity else None)
+    opt._keep = (log, tl)
+    return opt, log
+
+
+def correct(f: torch.Tensor, fhat: torch.Tensor, xi: float, *, rule="halve", max_sweeps: int = 0,
+            dense_min_items: int = 0, g_init: torch.Tensor | None = None, edit_capacity: int | None = None,
+            log_capacity: int = 0, out: torch.Tensor | None = None, edit_idx: torch.Tensor | None = None,
+            edit_delta: torch.Tensor | None = None, ws: torch.Tensor | None = None, stream=None,
+            check: bool = False) -> CorrectResult:
+    """Run the correction loop on device tensors (msz_correct)."""
+    assert f.dtype == torch.float32 and fhat.dtype == torch.float32 and f.shape == fhat.shape
+    lib = load()
+    g = grid_of(f.shape)
+    n = f.numel()
+    cap = n if edit_capacity is None else int(edit_capacity)
+    if out is None:
+        out = torch.empty_like(f)
+    if edit_idx is None or edit_idx.numel() < cap:
+        edit_idx = torch.empty(max(cap, 1), dtype=torch.int32, device=f.device)
+    if edit_delta is None or edit_delta.numel() < cap:
+        edit_delta = torch.empty(max(cap, 1), dtype=torch.float32, device=f.device)
+    need = int(lib.msz_workspace_size(g))
+    if ws is None:
+        ws = workspace(need, f.device)
+    opt, log = _options(rule, max_sweeps, dense_min_items, g_init, log_capacity)
+    stats = Stats()
+    count = ctypes.c_int64()
+    st = lib.msz_correct(_dptr(f), _dptr(fhat), ctypes.c_float(np.float32(xi)), g, _dptr(out),
+                         _dptr(edit_idx), _dptr(edit_delta), cap, ctypes.byref(count), ctypes.byref(opt),
+                         ctypes.byref(stats), _dptr(ws), ws.numel(), _stream(stream))
+    if check and st not in (OK,):
+        raise MszError(st, "msz_correct")
+    m = min(int(count.value), cap)
+    nlog = min(stats.sweeps + 1, log_capacity)
+    res = CorrectResult(int(st), out, edit_idx[:m], edit_delta[:m], int(count.value), stats.as_dict(),
+                        log[:4 * nlog].reshape(-1, 4).copy())
+    res.timeline = opt._keep[1][:2 * nlog].reshape(-1, 2).copy()
+    return res
+
+
+def host_workspace_size(shape, edit_capacity: int) -> int:
+    return int(load().msz_host_workspace_size(grid_of(shape), int(edit_capacity)))
+
+
+def correct_host(f: np.ndarray | torch.Tensor, fhat, xi: float, *, out=None, edit_idx=None, edit_delta=None,
+                 edit_capacity: int | None = None, rule="halve", max_sweeps: int = 0, dense_min_items: int = 0,
+                 ws: torch.Tensor | None = None, stream=None) -> CorrectResult:
+    """msz_correct_host: host buffers in, host buffers out (copies inside the call)."""
+    def host_ptr(a):
+        if isinstance(a, torch.Tensor):
+            assert not a.is_cuda and a.is_contiguous()
+            return a.data_ptr()
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+
+    lib = load()
+    shape = tuple(f.shape)
+    n = int(np.prod(shape))
+    cap = n if edit_capacity is None else int(edit_capacity)
+    if out is None:
+        out = np.empty(shape, dtype=np.float32)
+    if edit_idx is None:
+        edit_idx = np.empty(max(cap, 1), dtype=np.uint32)
+    if edit_delta is None:
+        edit_delta = np.empty(max(cap, 1), dtype=np.float32)
+    g = grid_of(shape)
+    need = int(lib.msz_host_workspace_size(g, cap))
+    if ws is None:
+        ws = workspace(need)
+    opt, log = _options(rule, max_sweeps, dense_min_items, None, 0)
+    stats = Stats()
+    count = ctypes.c_int64()
+    st = lib.msz_correct_host(host_ptr(f), host_ptr(fhat), ctypes.c_float(np.float32(xi)), g, host_ptr(out),
+                              host_ptr(edit_idx), host_ptr(edit_delta), cap, ctypes.byref(count),
+                              ctypes.byref(opt), ctypes.byref(stats), _dptr(ws), ws.numel(), _stream(stream))
+    m = min(int(count.value), cap)
+    return CorrectResult(int(st), out, edit_idx[:m], edit_delta[:m], int(count.value), stats.as_dict())
+
+
+def segment(codes: torch.Tensor, ws: torch.Tensor | None = None, stream=None):
+    """(min_label, max_label) int32 tensors by pointer jumping (msz_segment)."""
+    assert codes.dtype == torch.uint8
+    mn = torch.empty(codes.shape, dtype=torch.int32, device=codes.device)
+    mx = torch.empty(codes.shape, dtype=torch.int32, device=codes.device)
+    if ws is None:
+        ws = workspace(SMALL_WORKSPACE, codes.device)
+    st = load().msz_segment(_dptr(codes), grid_of(codes.shape), _dptr(mn), _dptr(mx), _dptr(ws), ws.numel(),
+                            _stream(stream))
+    if st != OK:
+        raise MszError(st, "msz_segment")
+    return mn, mx
+
+
+def compare(codes_f, codes_g, min_f, max_f, min_g, max_g, ws: torch.Tensor | None = None, stream=None) -> dict:
+    """Wrong labels and false extrema between two segmentations (msz_compare)."""
+    counts = (ctypes.c_int64 * 5)()
+    if ws is None:
+        ws = workspace(SMALL_WORKSPACE, codes_f.device)
+    st = load().msz_compare(_dptr(codes_f), _dptr(codes_g), _dptr(min_f), _dptr(max_f), _dptr(min_g),
+                            _dptr(max_g), codes_f.numel(), counts, _dptr(ws), ws.numel(), _stream(stream))
+    if st != OK:
+        raise MszError(st, "msz_compare")
+    return dict(wrong_labels=counts[0], fp_max=counts[1], fn_max=counts[2], fp_min=counts[3], fn_min=counts[4])
+
+
+def verify(f: torch.Tensor, g: torch.Tensor) -> dict:
+    """Codes, labels and the verification counts of g against f, all on the GPU."""
+    cf, cg = directions(f), directions(g)
+    mf, Mf = segment(cf)
+    mg, Mg = segment(cg)
+    res = compare(cf, cg, mf, Mf, mg, Mg)
+    res["codes_equal"] = bool(torch.equal(cf, cg))
+    return res

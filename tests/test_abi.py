@@ -1,0 +1,68 @@
+"""The C ABI library builds, loads without a GPU, and exports every entry point
+that include/*.h declares.  No compute call is made here."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b(msz_\w+)\s*\(", text, flags=re.M):
+            names[m.group(1)] = os.path.basename(h)
+    return names
+
+
+def test_headers_declare_entry_points():
+    names = _declared()
+    for n in ("msz_directions", "msz_correct", "msz_segment", "msz_compare", "msz_correct_host",
+              "msz_workspace_size", "msz_status_str"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2601_01787_gb300 import _build
+    path = _build.build()
+    lib = ctypes.CDLL(path)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings_and_sizes_without_gpu():
+    from paper_2601_01787_gb300 import api
+    lib = api.load()
+    assert api.status_str(api.OK) == "MSZ_OK"
+    assert api.status_str(api.STUCK) == "MSZ_STUCK"
+    assert lib.msz_workspace_size(api.grid_of((4, 5, 6))) > 4 * 5 * 6 * 13
+    assert lib.msz_workspace_size(api.Grid(4, 0, 1, 1, 1)) == 0       # bad ndim
+    assert lib.msz_workspace_size(api.Grid(2, 0, 3, 3, 2)) == 0       # 2D with nz != 1
+    assert lib.msz_workspace_size(api.Grid(3, 0, 2048, 2048, 1024)) == 0  # > 2^31 - 1 vertices
+
+
+def test_invalid_arguments_rejected_on_host():
+    """Argument checks run before any CUDA call, so they work without a GPU."""
+    from paper_2601_01787_gb300 import api
+    lib = api.load()
+    g = api.grid_of((3, 4, 5))
+    cnt = ctypes.c_int64()
+    fake = ctypes.c_void_p(256)
+    st = lib.msz_correct(None, fake, ctypes.c_float(0.1), g, fake, None, None, 0, ctypes.byref(cnt), None, None,
+                         fake, 1 << 30, None)
+    assert st == api.ERR_INVALID_ARG
+    st = lib.msz_correct(fake, fake, ctypes.c_float(-1.0), g, fake, None, None, 0, ctypes.byref(cnt), None, None,
+                         fake, 1 << 30, None)
+    assert st == api.ERR_INVALID_ARG
+    st = lib.msz_correct(fake, fake, ctypes.c_float(0.1), g, fake, None, None, 0, ctypes.byref(cnt), None, None,
+                         fake, 16, None)
+    assert st == api.ERR_WORKSPACE
+    bad_opt = api.Options(7, 0, 0, 0, None, None, 0)
+    st = lib.msz_correct(fake, fake, ctypes.c_float(0.1), g, fake, None, None, 0, ctypes.byref(cnt),
+                         ctypes.byref(bad_opt), None, fake, 1 << 30, None)
+    assert st == api.ERR_INVALID_ARG
