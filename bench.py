@@ -1,0 +1,365 @@
+"""Benchmark of the correction engine (one JSON line on rank 0).
+
+Metric: Gvertices/s to zero-mismatch correction of a 512^3 Perlin field
+prequantized with relative error bound 1e-4 (5 octaves, period 64, seed 2):
+the vertices of the field divided by the device time from f and fhat resident
+in HBM to the corrected field and the sorted edit list complete.  One step =
+one msz_correct call (the whole hot path: codes, every sweep, edit list).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun, one rank per GPU, each rank correcting its own
+512^3 field (independent problems: weak scaling, no collective on the data
+path); value = all ranks' vertices / the slowest rank's time.
+--impl reference times the CPU oracle (single thread, as it stands) on a
+bounded z-slab of the same field.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+SHAPE = (512, 512, 512)  # (nz, ny, nx); --shape overrides (profiling captures only)
+SEED = 2
+EB_REL = 1e-4
+METRIC = "Gvertices/s to zero-mismatch correction at 512^3 (plain)"
+UNIT = "Gvertices/s"
+def workload_name():
+    nz, ny, nx = SHAPE
+    return f"perlin3d_prequant_{nx}x{ny}x{nz}"
+
+
+def workload_config(n):
+    return {"workload": workload_name(), "field": "fractal Perlin noise, 5 octaves, base period 64, min-max scaled to [0,1]",
+            "fhat": "2*xi*round(f/(2*xi)) (uniform prequantization)", "eb_rel": EB_REL, "seed": SEED,
+            "n_vertices": n, "neighbourhood": "Freudenthal, 14 neighbours", "rule": "halve",
+            "l2": "no flush: inputs f+fhat (1.07 GB) exceed the 129 MB L2"}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms; only the
+    samples read between mark_start() and mark_end() (the timed region) count."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def mark_start(self):
+        self.t0 = time.perf_counter()
+
+    def mark_end(self):
+        self.t1 = time.perf_counter()
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ts, ln in self.lines:
+            if self.t0 is not None and not (self.t0 <= ts <= (self.t1 or ts) + 0.06):
+                continue
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- roofline
+def algorithmic_bytes(n: int, log: np.ndarray, edited: int) -> int:
+    """Compulsory HBM bytes of one correction:
+    sweep 0 reads f, fhat and writes codes_f, g (13 B/vertex); a later sweep
+    reads g and codes_f of every examined vertex (5 B each: the whole grid for
+    dense sweeps, the worklist otherwise); every distinct target reads f and g
+    and writes g (12 B); the edit list reads the edited bitmap (N/8 B) and
+    writes 8 B per edit."""
+    total = 13 * n
+    for k in range(1, log.shape[0]):
+        total += 5 * int(log[k, 0])
+    total += 12 * int(log[:, 2].sum())
+    total += n // 8 + 8 * edited
+    return total
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def max_over_ranks(value: float, ws: int) -> float:
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- ours
+def run_ours(args, ws, rank, local):
+    import torch
+
+    from paper_2601_01787_gb300 import api, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    fl = synth.perlin3d_prequant(SHAPE, seed=SEED, eb_rel=EB_REL)
+    n = fl.n
+    f = torch.from_numpy(fl.f).to(dev)
+    fh = torch.from_numpy(fl.fhat).to(dev)
+    out = torch.empty_like(f)
+    cap = n // 4
+    eidx = torch.empty(cap, dtype=torch.int32, device=dev)
+    edel = torch.empty(cap, dtype=torch.float32, device=dev)
+    ws_buf = api.workspace(api.workspace_size(f.shape), dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(log=0):
+        return api.correct(f, fh, fl.xi, out=out, edit_idx=eidx, edit_delta=edel, edit_capacity=cap,
+                           ws=ws_buf, stream=stream, log_capacity=log)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    first = step(log=4096)
+    assert first.status == api.OK, api.status_str(first.status)
+    for _ in range(max(args.warmup - 1, 0)):
+        step()
+    time.sleep(0.2)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.mark_start()
+    t_wall = time.perf_counter()
+    kernel_ns = []
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        r = step()
+        ev[i][1].record(stream)
+        kernel_ns.append(r.stats["kernel_ns"])
+        assert r.status == api.OK
+    torch.cuda.synchronize()
+    barrier(ws)
+    wall = time.perf_counter() - t_wall
+    clocks.mark_end()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms_local = sum(step_ms) / len(step_ms)
+    ms = max_over_ranks(ms_local, ws)
+    value = ws * n / (ms * 1e-3) / 1e9
+
+    # roofline of the (single) correction kernel
+    peak, peak_kind = load_peaks()
+    log = first.sweep_log
+    alg = algorithmic_bytes(n, log, first.edit_count)
+    kernel_ms = statistics.mean(kernel_ns) / 1e6
+    achieved = alg / (ms_local * 1e-3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "k_correct_perlin512_traffic.json")
+    if os.path.exists(tfile):
+        try:
+            with open(tfile) as fh_:
+                tj = json.load(fh_)
+            if tj.get("source_hash") == api_source_hash():
+                traffic = tj.get("traffic_bytes")
+        except Exception:
+            traffic = None
+
+    # end to end through the host-buffer entry point (pinned buffers)
+    hf = torch.from_numpy(fl.f).pin_memory()
+    hfh = torch.from_numpy(fl.fhat).pin_memory()
+    hout = torch.empty(fl.shape, dtype=torch.float32).pin_memory()
+    hidx = torch.empty(cap, dtype=torch.int32).pin_memory()
+    hdel = torch.empty(cap, dtype=torch.float32).pin_memory()
+    hws = api.workspace(api.host_workspace_size(fl.shape, cap), dev)
+    e2e_steps = max(5, args.steps // 10)
+
+    def hstep():
+        return api.correct_host(hf, hfh, fl.xi, out=hout, edit_idx=hidx, edit_delta=hdel, edit_capacity=cap,
+                                ws=hws, stream=stream)
+
+    for _ in range(2):
+        hr = hstep()
+    assert hr.status == api.OK
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        hr = hstep()
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) / e2e_steps * 1e3, ws)
+    e2e_value = ws * n / (e2e_ms * 1e-3) / 1e9
+
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 5), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(n) | {"parallelism": f"independent fields x{ws}" if ws > 1 else "single"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
+                     "algorithmic_bytes": alg, "kernel": "k_correct<3>",
+                     "kernel_ms_device": round(kernel_ms, 5)},
+        "e2e": {"value": round(e2e_value, 4), "unit": UNIT, "h2d_bytes_per_step": 8 * n,
+                "d2h_bytes_per_step": 4 * n + 8 * hr.edit_count, "ms_per_step": round(e2e_ms, 4)},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+        "sweeps": first.stats["sweeps"], "edited": first.edit_count, "first_distorted": first.stats["first_distorted"],
+        "sweep_log": log.tolist(),
+        "phase_ms": [[round(a / 1e6, 4), round(b / 1e6, 4)] for a, b in first.timeline.tolist()],
+        "wall_s_timed": round(wall, 4),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(fl, args.cpu_slab)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def api_source_hash() -> str:
+    from paper_2601_01787_gb300 import _build
+    return _build.source_hash()
+
+
+# ------------------------------------------------------------ CPU oracle
+def cpu_baseline(fl, slab: int) -> dict:
+    """The CPU oracle, as it stands (single thread), on the first `slab` z-planes
+    of the same field and bound."""
+    import oracle
+    f = np.ascontiguousarray(fl.f[:slab])
+    fh = np.ascontiguousarray(fl.fhat[:slab])
+    oracle.build()
+    t0 = time.perf_counter()
+    r = oracle.correct(f, fh, fl.xi)
+    dt = time.perf_counter() - t0
+    assert r.status == oracle.OK
+    return {"value": round(f.size / dt / 1e9, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {slab} z-planes of the {workload_name()} workload ({f.size} vertices), worklist mode",
+            "seconds": round(dt, 3), "sweeps": r.sweeps}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import oracle
+    from paper_2601_01787_gb300 import synth
+    fl = synth.perlin3d_prequant(SHAPE, seed=SEED, eb_rel=EB_REL)
+    slab = args.ref_slab
+    f = np.ascontiguousarray(fl.f[:slab])
+    fh = np.ascontiguousarray(fl.fhat[:slab])
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle.correct(f, fh, fl.xi)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle.correct(f, fh, fl.xi)
+        times.append(time.perf_counter() - t0)
+        assert r.status == oracle.OK
+    ms = statistics.mean(times) * 1e3
+    value = f.size / (ms * 1e-3) / 1e9
+    sample = f"first {slab} z-planes of the {workload_name()} workload ({f.size} vertices), worklist mode"
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(fl.n),
+            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-slab", type=int, default=128, help="z-planes of the CPU-baseline sample")
+    ap.add_argument("--ref-slab", type=int, default=24, help="z-planes per reference-arm step")
+    ap.add_argument("--shape", default=None, help="nz,ny,nx of a smaller field (profiling captures only)")
+    args = ap.parse_args(argv)
+    if args.shape:
+        global SHAPE
+        SHAPE = tuple(int(v) for v in args.shape.split(","))
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    ws, rank, local = dist_info()
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+    try:
+        if args.impl == "reference":
+            run_reference(args, ws, rank)
+        else:
+            run_ours(args, ws, rank, local)
+    finally:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -41,7 +41,9 @@ def _nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libmsz.so")
 
 
-def _stamp() -> str:
+def source_hash() -> str:
+    """Hash of the CUDA sources, the public header and the compile flags
+    (machine independent): identifies the kernels a profile was taken of."""
     h = hashlib.sha256()
     files = sorted(os.listdir(CSRC)) + ["../../include/msz.h"]
     for name in files:
@@ -50,9 +52,12 @@ def _stamp() -> str:
             h.update(name.encode())
             with open(p, "rb") as fh:
                 h.update(fh.read())
-    h.update(repr((COMMON, UNITS)).encode())
-    h.update(os.uname().machine.encode())
-    return h.hexdigest()
+    h.update(repr(([c for c in COMMON if not c.startswith("/")], UNITS)).encode())
+    return h.hexdigest()[:16]
+
+
+def _stamp() -> str:
+    return source_hash() + "-" + os.uname().machine
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
