@@ -173,6 +173,24 @@ msz_status msz_compare(const uint8_t *d_codes_f, const uint8_t *d_codes_g, const
                        const int32_t *d_max_f, const int32_t *d_min_g, const int32_t *d_max_g, int64_t n,
                        int64_t h_counts[5], void *d_workspace, size_t workspace_bytes, msz_stream_t stream);
 
+/* msz_correct for callers that cannot allocate device memory.  (The paper has
+ * no counterpart: this entry point exists for how callers use the library.)
+ * Some callers cannot call cudaMalloc -- a plugin whose host application owns
+ * every device allocation, code where an allocation would block or synchronize
+ * the device, a process that must keep its footprint fixed after start-up --
+ * so this variant takes no workspace: its scratch memory is a fixed array of
+ * about 8.0 MB compiled into the library, held by every GPU that loads it until
+ * the process exits.  Grids of more than MSZ_STATIC_MAX_VERTICES vertices are
+ * rejected with MSZ_ERR_WORKSPACE.  Arguments, results and synchronization are
+ * those of msz_correct.  The first call on a device looks up the array's device
+ * address (make that call before any stream capture).  Every call shares the
+ * array: calls that overlap on the GPU race, so serialize them. */
+#define MSZ_STATIC_MAX_VERTICES 4194304LL
+msz_status msz_correct_static(const float *d_f, const float *d_fhat, float xi, msz_grid grid, float *d_out,
+                              uint32_t *d_edit_idx, float *d_edit_delta, int64_t edit_capacity,
+                              int64_t *h_edit_count, const msz_options *opt, msz_stats *h_stats,
+                              msz_stream_t stream);
+
 /* Human-readable name of a status. */
 const char *msz_status_str(msz_status status);
 

@@ -31,6 +31,7 @@ EXACT = ["-fmad=false", "-ftz=false", "-prec-div=true", "-prec-sqrt=true"]
 UNITS = [
     ("msz_correct.cu", EXACT),
     ("msz_segment.cu", EXACT),
+    ("msz_static.cu", EXACT),
 ]
 
 

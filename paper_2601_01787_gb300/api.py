@@ -85,6 +85,9 @@ def load(build_if_missing: bool = True):
         lib.msz_segment.restype = st
         lib.msz_compare.argtypes = [P, P, P, P, P, P, I64, ctypes.POINTER(I64), P, SZ, P]
         lib.msz_compare.restype = st
+        lib.msz_correct_static.argtypes = [P, P, ctypes.c_float, Grid, P, P, P, I64, ctypes.POINTER(I64),
+                                           ctypes.POINTER(Options), ctypes.POINTER(Stats), P]
+        lib.msz_correct_static.restype = st
         lib.msz_status_str.argtypes = [st]
         lib.msz_status_str.restype = ctypes.c_char_p
         _lib = lib

@@ -44,7 +44,7 @@ constexpr size_t kAlign = 256;
 constexpr uint32_t kMaxBlocks = 4096;  // cooperative grid upper bound (block sums)
 constexpr size_t kLogEntries = (size_t)MSZ_MAX_SWEEPS_LIMIT + 2;
 
-inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+constexpr size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 // Byte offsets of each region for a grid of n vertices (bitmaps: one bit per
 // vertex).
@@ -53,7 +53,7 @@ struct Layout {
     size_t zero_bytes;  // [0, zero_bytes) is cleared at the start of every call
 };
 
-inline Layout layout_for(uint64_t n) {
+constexpr Layout layout_for(uint64_t n) {
     Layout L{};
     const uint64_t words = (n + 31) / 32;
     size_t o = 0;
