@@ -105,6 +105,7 @@ typedef struct {
     int64_t examined;         /* vertices examined over all sweeps (dense sweeps count N) */
     int64_t dense_sweeps;     /* sweeps run as whole-grid scans, sweep 0 included */
     int64_t kernel_ns;        /* device time of the correction kernel (globaltimer) */
+    int64_t codes_ns;         /* ... of its first phase: the codes of f and their certification */
 } msz_stats;
 
 /* Bytes of device workspace msz_correct needs for this grid (about 13.5 bytes

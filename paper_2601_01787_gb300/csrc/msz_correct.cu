@@ -38,6 +38,7 @@ constexpr uint32_t kTileZ = 32;          // planes per tile of a whole-grid pass
 #endif
 constexpr int kMinBlocks = MSZ_MIN_BLOCKS;  // resident blocks per SM the register budget aims at
 constexpr uint32_t kDenseFactor = 6;        // worklist estimate: 6 x distorted vertices
+constexpr int kDenseWord = 6;               // set bits from which a bitmap word is walked by the whole warp
 
 struct Problem {
     GridDev G;
@@ -48,7 +49,8 @@ struct Problem {
     uint8_t *codes_f;
     uint32_t *tb;      // targets of the current sweep
     uint32_t *dm[2];   // worklist of a sweep, by sweep parity
-    uint32_t *eb;      // edited vertices (one level)
+    uint32_t *eb;      // edited vertices
+    uint32_t *ub;      // uncertified vertices: the only ones that can ever be distorted
     Ctrl *ctrl;
     SweepRec *log;
     uint32_t *bsum;
@@ -56,6 +58,7 @@ struct Problem {
     float *edit_delta;
     unsigned long long edit_cap;
     float xi;
+    float two_xi;      // 2 xi rounded up: the certification margin
     int rule;
     uint32_t max_sweeps;
     long long dense_min;  // < 0: never scan densely after sweep 0
@@ -87,11 +90,14 @@ __device__ __forceinline__ bool report(const Problem &P, Emitter &E, bool valid,
     return dist;
 }
 
-// Warp-collective walk over the set bits of a bitmap, clearing them: each warp
-// takes 32 consecutive words (1024 vertices) at a time, grid-stride; fn(valid,
-// v) is called once per round with one vertex per lane.
-template <class F>
-__device__ __forceinline__ void walk_bits(uint32_t *bm, const GridDev &G, F &&fn) {
+// Warp-collective walk over the set bits of a bitmap: each warp takes 32
+// consecutive words (1024 vertices) at a time, grid-stride.  CLEAR zeroes the
+// visited words; `seen` counts their set bits; a non-null filter restricts the
+// calls to the vertices also set there.  fn(valid, v) runs once per round
+// with one vertex per lane.
+template <bool CLEAR, class F>
+__device__ __forceinline__ void walk_bits(uint32_t *bm, const uint32_t *filter, const GridDev &G, uint32_t &seen,
+                                          F &&fn) {
     const uint32_t lane = lane_id();
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
@@ -100,8 +106,22 @@ __device__ __forceinline__ void walk_bits(uint32_t *bm, const GridDev &G, F &&fn
         uint32_t bits = 0;
         if (wi < G.words) {
             bits = bm[wi];
-            if (bits) bm[wi] = 0u;
+            if (CLEAR && bits) bm[wi] = 0u;
+            seen += (uint32_t)__popc(bits);
+            if (filter && bits) bits &= filter[wi];
         }
+        // words with many set bits: the whole warp takes one word at a time,
+        // lane l on vertex 32*word + l, so neighbour loads coalesce
+        const bool dense = __popc(bits) >= kDenseWord;
+        uint32_t dm = __ballot_sync(kFull, dense);
+        while (dm) {
+            const int j = __ffs(dm) - 1;
+            dm &= dm - 1u;
+            const uint32_t word = __shfl_sync(kFull, bits, j);
+            fn(((word >> lane) & 1u) != 0u, (base + (uint32_t)j) * 32u + lane);
+        }
+        if (dense) bits = 0u;
+        // the remaining sparse words: each lane walks its own word's bits
         while (__any_sync(kFull, bits != 0u)) {
             const bool has = bits != 0u;
             uint32_t v = 0;
@@ -114,74 +134,64 @@ __device__ __forceinline__ void walk_bits(uint32_t *bm, const GridDev &G, F &&fn
     }
 }
 
-// ------------------------------------------------ generic (2D) whole-grid pass
+// Detection of one vertex in the current g (warp-collective).
 template <int NDIM>
-__device__ void first_generic(const Problem &P, Emitter &S) {
+__device__ __forceinline__ void detect_vertex(const Problem &P, Emitter &E, bool has, uint32_t v) {
+    uint32_t cf = 0, cg = 0;
+    if (has) {
+        uint32_t x, y, z;
+        coords_of(P.G, v, x, y, z);
+        cg = code_global<NDIM>(P.g, P.G, v, x, y, z);
+        cf = __ldg(&P.codes_f[v]);
+    }
+    report(P, E, has, v, cf, cg);
+}
+
+// ------------------------------------------------ generic (2D) codes of f
+template <int NDIM>
+__device__ void first_generic(const Problem &P) {
     const GridDev &G = P.G;
     const uint32_t lane = lane_id();
     const uint32_t stride = gridDim.x * blockDim.x;
-    const float *gsrc = P.ginit ? P.ginit : P.fhat;
     bool bad = false;
     for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < G.n; base += stride) {
         const uint32_t i = base + lane;
         const bool valid = i < G.n;
-        bool differs = false;
-        uint32_t cf = 0, cg = 0;
+        bool differs = false, uncert = false;
         if (valid) {
             uint32_t x, y, z;
             coords_of(G, i, x, y, z);
-            const float fi = P.f[i], fh = P.fhat[i], gs = gsrc[i];
+            const float fi = P.f[i], fh = P.fhat[i];
+            const float gs = P.ginit ? P.ginit[i] : fh;
             const float L = floor_bound(fi, P.xi), U = ceil_bound(fi, P.xi);
             bad = bad || !(isfinite(fi) && isfinite(fh) && fh >= L && fh <= U);
             if (P.ginit) {
                 bad = bad || !(isfinite(gs) && gs >= L && gs <= U);
                 differs = __float_as_uint(gs) != __float_as_uint(fh);
             }
-            cf = code_global<NDIM>(P.f, G, i, x, y, z);
-            P.codes_f[i] = (uint8_t)cf;
+            bool cert;
+            P.codes_f[i] = code_global_cert<NDIM>(P.f, G, i, x, y, z, P.two_xi, cert);
+            uncert = !cert;
             P.g[i] = gs;
-            cg = code_global<NDIM>(gsrc, G, i, x, y, z);
         }
+        // base is a multiple of 32: this warp owns whole bitmap words
+        const uint32_t um = __ballot_sync(kFull, uncert);
+        if (lane == 0) P.ub[base >> 5] = um;
         if (P.ginit) {
             const uint32_t m = __ballot_sync(kFull, differs);
-            if (lane == 0 && m) P.eb[base >> 5] = m;  // base is a multiple of 32
+            if (lane == 0 && m) P.eb[base >> 5] = m;
         }
-        report(P, S, valid, i, cf, cg);
     }
     if (bad) atomicOr(&P.ctrl->error, kErrInput);
 }
 
-template <int NDIM>
-__device__ void detect_generic(const Problem &P, Emitter &S) {
-    const GridDev &G = P.G;
-    const uint32_t lane = lane_id();
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < G.n; base += stride) {
-        const uint32_t v = base + lane;
-        uint32_t cf = 0, cg = 0;
-        if (v < G.n) {
-            uint32_t x, y, z;
-            coords_of(G, v, x, y, z);
-            cg = code_global<NDIM>(P.g, G, v, x, y, z);
-            cf = __ldg(&P.codes_f[v]);
-        }
-        report(P, S, v < G.n, v, cf, cg);
-    }
-}
-
-// ------------------------------------------------ tiled (3D) whole-grid pass
-// FIRST: fields (f, g-start); writes codes_f and g, checks the bound.
-// !FIRST: field g; reads codes_f.
-template <bool FIRST>
-__device__ void dense_tiled(const Problem &P, Emitter &S, uint32_t *tile_next, float *smem) {
+// ------------------------------------------------ tiled (3D) codes of f
+// Codes of f with their certification, g = start value, bound check.
+__device__ void first_tiled(const Problem &P, uint32_t *tile_next, float *smem) {
     using namespace tile;
-    constexpr int NF = FIRST ? 2 : 1;
     const GridDev &G = P.G;
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
     const TileGeom tg = tile_geom(G.nx, G.ny, G.nz, kTileZ);
-    // staged fields: (f, start of g) in sweep 0, g afterwards
-    const float *src0 = FIRST ? P.f : P.g;
-    const float *src1 = FIRST ? (P.ginit ? P.ginit : P.fhat) : P.g;
     __shared__ uint32_t s_tile;
     bool bad = false;
     for (;;) {
@@ -210,26 +220,51 @@ __device__ void dense_tiled(const Problem &P, Emitter &S, uint32_t *tile_next, f
         }
         const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
         const int gbase = (y0 - 1) * (int)G.nx + (x0 - 1);  // plane offset of staged element 0
-        // asynchronous copy of plane p of every staged field into its ring slot
+        const float qnan = __int_as_float(0x7fffffff);
+        // Positions outside the grid hold NaN: a NaN candidate never wins a
+        // comparison, so the codes need no domain masks (it only withholds the
+        // certification of vertices on the grid boundary, which is safe).
+#pragma unroll
+        for (int j = 0; j < PER_THREAD; ++j) {
+            const int e = (int)tid + j * THREADS;
+            if (e >= ELEMS || (inm >> j & 1u)) continue;
+            const int r = e / LOADW, c = e - r * LOADW;
+            for (int sl = 0; sl < NSLOT; ++sl) smem[sl * SLOT + r * PW + c + 3] = qnan;
+        }
+        // asynchronous copy of plane p (f over the staged region, fhat over the
+        // owned region) into its ring slot; planes outside the grid become NaN
         auto issue = [&](int p) {
-            if (p >= 0 && p < (int)G.nz && p <= ze) {
+            if (p >= 0 && p <= ze) {
                 const int slot = (p - zb + 1) % NSLOT;
+                const bool inside = p < (int)G.nz;
                 const size_t pb = (size_t)p * G.nxy;
 #pragma unroll
                 for (int j = 0; j < PER_THREAD; ++j) {
                     if (!(inm >> j & 1u)) continue;
                     const int e = (int)tid + j * THREADS;
                     const int r = e / LOADW, c = e - r * LOADW;
+                    const uint32_t so = (uint32_t)(slot * SLOT + r * PW + c + 3);
+                    if (!inside) {
+                        smem[so] = qnan;
+                        continue;
+                    }
                     const size_t gi = pb + (size_t)(gbase + r * (int)G.nx + c);
-                    const uint32_t so = (uint32_t)(slot * NF * PLANE + r * PW + c + 3);
+                    cp_async4(sbase + 4u * so, P.f + gi);
+                    if (ownm >> j & 1u) cp_async4(sbase + 4u * (so + (uint32_t)PLANE), P.fhat + gi);
+                }
+            } else if (p < 0) {
+                const int slot = (p - zb + 1) % NSLOT;
 #pragma unroll
-                    cp_async4(sbase + 4u * so, src0 + gi);
-                    if (NF == 2) cp_async4(sbase + 4u * (so + (uint32_t)PLANE), src1 + gi);
+                for (int j = 0; j < PER_THREAD; ++j) {
+                    if (!(inm >> j & 1u)) continue;
+                    const int e = (int)tid + j * THREADS;
+                    const int r = e / LOADW, c = e - r * LOADW;
+                    smem[slot * SLOT + r * PW + c + 3] = qnan;
                 }
             }
             cp_async_commit();
         };
-        // owned vertices of plane p (sweep 0): bound check and g = start value
+        // owned vertices of plane p: bound check and g = start value
         auto own = [&](int p) {
             const int slot = (p - zb + 1) % NSLOT;
             const size_t pb = (size_t)p * G.nxy;
@@ -238,15 +273,14 @@ __device__ void dense_tiled(const Problem &P, Emitter &S, uint32_t *tile_next, f
                 if (!(ownm >> j & 1u)) continue;
                 const int e = (int)tid + j * THREADS;
                 const int r = e / LOADW, c = e - r * LOADW;
-                const int so = slot * NF * PLANE + r * PW + c + 3;
-                const float fi = smem[so];
-                const float gs = smem[so + (NF - 1) * PLANE];
-                const float L = floor_bound(fi, P.xi), U = ceil_bound(fi, P.xi);
-                bool ok = isfinite(fi) && isfinite(gs) && gs >= L && gs <= U;
+                const int so = slot * SLOT + r * PW + c + 3;
+                const float fi = smem[so], fh = smem[so + PLANE];
                 const size_t gi = pb + (size_t)(gbase + r * (int)G.nx + c);
+                const float gs = P.ginit ? P.ginit[gi] : fh;
+                const float L = floor_bound(fi, P.xi), U = ceil_bound(fi, P.xi);
+                bool ok = isfinite(fi) && isfinite(fh) && fh >= L && fh <= U;
                 if (P.ginit) {
-                    const float fh = P.fhat[gi];
-                    ok = ok && isfinite(fh) && fh >= L && fh <= U;
+                    ok = ok && isfinite(gs) && gs >= L && gs <= U;
                     if (__float_as_uint(fh) != __float_as_uint(gs)) red_or(&P.eb[gi >> 5], 1u << (gi & 31u));
                 }
                 bad = bad || !ok;
@@ -261,70 +295,43 @@ __device__ void dense_tiled(const Problem &P, Emitter &S, uint32_t *tile_next, f
         const int xl = x0 + 4 * (int)lane;
         for (int z = zb; z < ze; ++z) {
             cp_async_wait<1>();  // planes up to z+1 of this thread have landed (z+2 may be in flight)
-            __syncthreads();     // ... of every thread; slot of z-2 is free
+            __syncthreads();     // ... of every thread; the slot of z-2 is free
             issue(z + 3);
-            if (FIRST) own(z);
+            own(z);
             if (y >= (int)G.ny) continue;
-            const float *base = smem;
-            auto plane = [&](int p, int f) { return base + (((p - zb + 1) % NSLOT) * NF + f) * PLANE; };
-            const bool interior = x0 >= 1 && x0 + BX < (int)G.nx && y >= 1 && y + 1 < (int)G.ny && z >= 1 &&
-                                  z + 1 < (int)G.nz;
-            tile::Dom d;
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                d.xm[e] = xl + e >= 1;
-                d.xp[e] = xl + e + 1 < (int)G.nx;
-            }
-            d.ym = y >= 1;
-            d.yp = y + 1 < (int)G.ny;
-            d.zm = z >= 1;
-            d.zp = z + 1 < (int)G.nz;
-            uint32_t cg[4], cf[4];
-            if (interior) tile::codes4<false>(plane(z - 1, NF - 1), plane(z, NF - 1), plane(z + 1, NF - 1), r, lane, d, cg);
-            else tile::codes4<true>(plane(z - 1, NF - 1), plane(z, NF - 1), plane(z + 1, NF - 1), r, lane, d, cg);
+            auto plane = [&](int p) { return smem + ((p - zb + 1) % NSLOT) * SLOT; };
+            uint32_t cf[4], cert;
+            tile::codes4_cert(plane(z - 1), plane(z), plane(z + 1), r, lane, P.two_xi, cf, cert);
             const size_t rowbase = (size_t)z * G.nxy + (size_t)y * G.nx;
-            if (FIRST) {
-                if (interior) tile::codes4<false>(plane(z - 1, 0), plane(z, 0), plane(z + 1, 0), r, lane, d, cf);
-                else tile::codes4<true>(plane(z - 1, 0), plane(z, 0), plane(z + 1, 0), r, lane, d, cf);
-                const size_t i0 = rowbase + xl;
-                if (xl + 3 < (int)G.nx && (i0 & 3) == 0) {
-                    *reinterpret_cast<uint32_t *>(P.codes_f + i0) = cf[0] | cf[1] << 8 | cf[2] << 16 | cf[3] << 24;
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        if (xl + e < (int)G.nx) P.codes_f[i0 + e] = (uint8_t)cf[e];
-                }
+            const size_t i0 = rowbase + xl;
+            if (xl + 3 < (int)G.nx && (i0 & 3) == 0) {
+                *reinterpret_cast<uint32_t *>(P.codes_f + i0) = cf[0] | cf[1] << 8 | cf[2] << 16 | cf[3] << 24;
             } else {
-                const size_t i0 = rowbase + xl;
-                if (xl + 3 < (int)G.nx && (i0 & 3) == 0) {
-                    const uint32_t w4 = __ldg(reinterpret_cast<const uint32_t *>(P.codes_f + i0));
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) cf[e] = (w4 >> (8 * e)) & 0xffu;
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) cf[e] = xl + e < (int)G.nx ? __ldg(&P.codes_f[i0 + e]) : 0u;
-                }
+                for (int e = 0; e < 4; ++e)
+                    if (xl + e < (int)G.nx) P.codes_f[i0 + e] = (uint8_t)cf[e];
             }
-            // this warp's 128 vertices fill 4 whole bitmap words when the row run is
-            // word aligned: mark distorted vertices with one reduction per word
-            const bool words_ok = ((rowbase + (size_t)x0) & 31u) == 0 && x0 + BX <= (int)G.nx;
+            // uncertified bits of this lane's vertices (outside the grid: 0)
             uint32_t nib = 0;
 #pragma unroll
-            for (int e = 0; e < 4; ++e)
-                nib |= (uint32_t)report(P, S, xl + e < (int)G.nx, (uint32_t)(rowbase + xl + e), cf[e], cg[e],
-                                        words_ok)
-                       << e;
-            if (words_ok && __any_sync(kFull, nib != 0u)) {
+            for (int e = 0; e < 4; ++e) nib |= (uint32_t)(xl + e < (int)G.nx && !((cert >> e) & 1u)) << e;
+            const bool words_ok = ((rowbase + (size_t)x0) & 31u) == 0 && x0 + BX <= (int)G.nx;
+            if (words_ok) {
+                // the warp's 128 vertices are 4 whole bitmap words
                 uint32_t w = nib << (4u * (lane & 7u));
                 w |= __shfl_xor_sync(kFull, w, 1);
                 w |= __shfl_xor_sync(kFull, w, 2);
                 w |= __shfl_xor_sync(kFull, w, 4);
-                if ((lane & 7u) == 0 && w) red_or(&S.dnext[(rowbase + (size_t)x0 + 4u * lane) >> 5], w);
+                if ((lane & 7u) == 0) P.ub[(i0) >> 5] = w;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if ((nib >> e) & 1u) red_or(&P.ub[(i0 + e) >> 5], 1u << ((i0 + e) & 31u));
             }
         }
         cp_async_wait<0>();
     }
-    if (FIRST && bad) atomicOr(&P.ctrl->error, kErrInput);
+    if (bad) atomicOr(&P.ctrl->error, kErrInput);
 }
 
 // ------------------------------------------------------ the persistent kernel
@@ -339,11 +346,16 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
     const bool leader = gtid == 0;
     if (leader) C->t_start = global_ns();
 
-    // ---- sweep 0: codes of f, g = start, bound check, detection
-    {
+    // ---- sweep 0: codes of f with their certification, g = start, bound check
+    if (NDIM == 3) first_tiled(P, &P.log[0].tile_next, smem);
+    else first_generic<NDIM>(P);
+    bool ok = grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
+    if (leader) C->t_codes = global_ns();
+    // ---- detection of sweep 0: only uncertified vertices can be distorted
+    if (ok) {
         Emitter E{P.dm[1], 0};
-        if (NDIM == 3) dense_tiled<true>(P, E, &P.log[0].tile_next, smem);
-        else first_generic<NDIM>(P, E);
+        uint32_t seen = 0;
+        walk_bits<false>(P.ub, nullptr, G, seen, [&](bool has, uint32_t v) { detect_vertex<NDIM>(P, E, has, v); });
         warp_add(E.distorted, &P.log[0].distorted);
     }
     if (leader) {
@@ -351,7 +363,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
         C->examined = G.n;
         C->dense_sweeps = 1;
     }
-    bool ok = grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
+    ok = ok && grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
     if (leader) P.log[0].t_detect = global_ns();
     uint32_t k = 0;
     while (ok) {
@@ -363,7 +375,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
         if (k >= P.max_sweeps) {
             // count the distinct targets this sweep found, for the record
             uint32_t nt = 0;
-            walk_bits(P.tb, G, [&](bool has, uint32_t) { nt += has; });
+            walk_bits<true>(P.tb, nullptr, G, nt, [&](bool, uint32_t) {});
             warp_add(nt, &P.log[k].targets);
             if (leader) { C->status = MSZ_ERR_MAX_SWEEPS; C->sweeps = k; C->left = m; }
             ok = grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
@@ -375,9 +387,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
         {
             uint32_t *dnext = P.dm[(k + 1) & 1];
             uint32_t targets = 0, changed_here = 0;
-            walk_bits(P.tb, G, [&](bool has, uint32_t t) {
+            walk_bits<true>(P.tb, nullptr, G, targets, [&](bool has, uint32_t t) {
                 if (!has) return;
-                ++targets;
                 const float gt = P.g[t];
                 const float L = floor_bound(__ldg(&P.f[t]), P.xi);
                 float h;
@@ -413,28 +424,19 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
         const uint32_t k1 = k + 1;
         Emitter E{P.dm[(k1 + 1) & 1], 0};
         uint32_t *dcur = P.dm[k1 & 1];
+        uint32_t seen = 0;
         if (dense_next) {
+            // whole grid: every uncertified vertex
             if (leader) {
                 P.log[k1].worklist = G.n;
                 C->examined += G.n;
                 C->dense_sweeps += 1;
             }
             for (uint32_t w = gtid; w < G.words; w += stride) dcur[w] = 0;
-            if (NDIM == 3) dense_tiled<false>(P, E, &P.log[k1].tile_next, smem);
-            else detect_generic<NDIM>(P, E);
+            walk_bits<false>(P.ub, nullptr, G, seen, [&](bool has, uint32_t v) { detect_vertex<NDIM>(P, E, has, v); });
         } else {
-            uint32_t seen = 0;
-            walk_bits(dcur, G, [&](bool has, uint32_t v) {
-                uint32_t cf = 0, cg = 0;
-                if (has) {
-                    ++seen;
-                    uint32_t x, y, z;
-                    coords_of(G, v, x, y, z);
-                    cg = code_global<NDIM>(P.g, G, v, x, y, z);
-                    cf = __ldg(&P.codes_f[v]);
-                }
-                report(P, E, has, v, cf, cg);
-            });
+            // the worklist, restricted to uncertified vertices
+            walk_bits<true>(dcur, P.ub, G, seen, [&](bool has, uint32_t v) { detect_vertex<NDIM>(P, E, has, v); });
             warp_add(seen, &P.log[k1].worklist);
         }
         warp_add(E.distorted, &P.log[k1].distorted);
@@ -527,7 +529,7 @@ msz_status current_device(DeviceInfo &info) {
 }
 
 template <int NDIM>
-static size_t correct_smem() { return NDIM == 3 ? tile::smem_bytes(2) : 0; }
+static size_t correct_smem() { return NDIM == 3 ? tile::kRingBytes : 0; }
 
 template <int NDIM>
 static msz_status correct_blocks(const DeviceInfo &d, int &blocks) {
@@ -622,6 +624,7 @@ extern "C" msz_status msz_correct(const float *d_f, const float *d_fhat, float x
     P.dm[0] = (uint32_t *)(ws + L.d0);
     P.dm[1] = (uint32_t *)(ws + L.d1);
     P.eb = (uint32_t *)(ws + L.eb);
+    P.ub = (uint32_t *)(ws + L.ub);
     P.ctrl = (Ctrl *)(ws + L.ctrl);
     P.log = (SweepRec *)(ws + L.log);
     P.bsum = (uint32_t *)(ws + L.bsum);
@@ -629,6 +632,7 @@ extern "C" msz_status msz_correct(const float *d_f, const float *d_fhat, float x
     P.edit_delta = d_edit_delta;
     P.edit_cap = (unsigned long long)edit_capacity;
     P.xi = xi;
+    P.two_xi = 2.0f * xi;  // exact (power-of-two scaling), +inf on overflow
     P.rule = o.rule;
     P.max_sweeps = o.max_sweeps <= 0 ? (uint32_t)MSZ_MAX_SWEEPS_LIMIT : (uint32_t)o.max_sweeps;
     P.dense_min = o.dense_min_items == 0 ? (long long)(G.n / 16 > 0 ? G.n / 16 : 1) : (long long)o.dense_min_items;
@@ -673,6 +677,7 @@ extern "C" msz_status msz_correct(const float *d_f, const float *d_fhat, float x
         h_stats->examined = (int64_t)hc.examined;
         h_stats->dense_sweeps = hc.dense_sweeps;
         h_stats->kernel_ns = hc.t_end > hc.t_start ? (int64_t)(hc.t_end - hc.t_start) : 0;
+        h_stats->codes_ns = hc.t_codes > hc.t_start ? (int64_t)(hc.t_codes - hc.t_start) : 0;
     }
     const msz_status loop = (msz_status)hc.status;
     if (loop == MSZ_OK && (int64_t)hc.edit_count > edit_capacity) return MSZ_ERR_CAPACITY;

@@ -131,6 +131,57 @@ __device__ __forceinline__ uint8_t code_global(const float *v, const GridDev &G,
     return e.code();
 }
 
+// Code of vertex i of field v plus its certification: the winner of each
+// direction beats the runner-up by more than two_xi (rounded down), so that
+// no field within xi of v can change the code.
+template <int NDIM>
+__device__ __forceinline__ uint8_t code_global_cert(const float *v, const GridDev &G, uint32_t i, uint32_t x,
+                                                    uint32_t y, uint32_t z, float two_xi, bool &cert) {
+    float hv = -__int_as_float(0x7f800000), h2 = hv, lv = __int_as_float(0x7f800000), l2 = lv;
+    uint32_t hs = kSelf, ls = kSelf;
+    auto take = [&](float w, uint32_t slot) {
+        const bool p = w >= hv;
+        h2 = fmaxf(h2, p ? hv : w);
+        hv = fmaxf(hv, w);
+        hs = p ? slot : hs;
+        const bool q = w < lv;
+        l2 = fminf(l2, q ? lv : w);
+        lv = fminf(lv, w);
+        ls = q ? slot : ls;
+    };
+    const bool xm = x > 0, xp = x + 1 < G.nx, ym = y > 0, yp = y + 1 < G.ny;
+    if (NDIM == 3) {
+        const bool zm = z > 0, zp = z + 1 < G.nz;
+        const uint32_t nx = G.nx, nxy = G.nxy;
+        if (xm && ym && zm) take(v[i - 1 - nx - nxy], 13);
+        if (ym && zm) take(v[i - nx - nxy], 12);
+        if (xm && zm) take(v[i - 1 - nxy], 11);
+        if (zm) take(v[i - nxy], 9);
+        if (xm && ym) take(v[i - 1 - nx], 10);
+        if (ym) take(v[i - nx], 8);
+        if (xm) take(v[i - 1], 7);
+        take(v[i], kSelf);
+        if (xp) take(v[i + 1], 0);
+        if (yp) take(v[i + nx], 1);
+        if (xp && yp) take(v[i + 1 + nx], 3);
+        if (zp) take(v[i + nxy], 2);
+        if (xp && zp) take(v[i + 1 + nxy], 4);
+        if (yp && zp) take(v[i + nx + nxy], 5);
+        if (xp && yp && zp) take(v[i + 1 + nx + nxy], 6);
+    } else {
+        const uint32_t nx = G.nx;
+        if (xm && ym) take(v[i - 1 - nx], 5);
+        if (ym) take(v[i - nx], 4);
+        if (xm) take(v[i - 1], 3);
+        take(v[i], kSelf);
+        if (xp) take(v[i + 1], 0);
+        if (yp) take(v[i + nx], 1);
+        if (xp && yp) take(v[i + 1 + nx], 2);
+    }
+    cert = __fsub_rd(hv, h2) > two_xi && __fsub_rd(l2, lv) > two_xi;
+    return (uint8_t)(hs | (ls << 4));
+}
+
 // L = smallest float32 >= f - xi and U = largest float32 <= f + xi: one
 // directed-rounding subtraction / addition of the exact operands.
 __device__ __forceinline__ float floor_bound(float f, float xi) { return __fsub_ru(f, xi); }

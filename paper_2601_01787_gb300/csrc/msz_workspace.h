@@ -37,6 +37,7 @@ struct Ctrl {
     unsigned long long examined;
     unsigned long long counts[8]; // compare counters
     unsigned long long t_start, t_end;  // %globaltimer at kernel start / edit list written
+    unsigned long long t_codes;         // ... when the codes of f were complete
     uint32_t pad[16];
 };
 
@@ -49,7 +50,7 @@ constexpr size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign;
 // Byte offsets of each region for a grid of n vertices (bitmaps: one bit per
 // vertex).
 struct Layout {
-    size_t ctrl, log, bsum, tb, d0, d1, eb, codes, total;
+    size_t ctrl, log, bsum, tb, d0, d1, eb, ub, codes, total;
     size_t zero_bytes;  // [0, zero_bytes) is cleared at the start of every call
 };
 
@@ -64,6 +65,7 @@ constexpr Layout layout_for(uint64_t n) {
     L.d0 = o;     o = align_up(o + words * 4);
     L.d1 = o;     o = align_up(o + words * 4);
     L.eb = o;     o = align_up(o + words * 4);
+    L.ub = o;     o = align_up(o + words * 4);
     L.zero_bytes = o;
     L.codes = o;  o = align_up(o + n);
     L.total = o;
