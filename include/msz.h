@@ -94,6 +94,9 @@ typedef struct {
     int64_t *h_timeline;      /* NULL, or 2*log_capacity int64 (needs h_sweep_log): device
                                  time in ns from the start of the correction kernel to the
                                  end of sweep k's detection and of its edit phase (-1: none) */
+    int32_t tile_z;           /* z-planes per tile of the code pass (3D); 0: 32; at most 1024.
+                                 Affects speed only (see the autotuner), never results */
+    int32_t reserved2;
 } msz_options;
 
 typedef struct {
@@ -173,6 +176,48 @@ msz_status msz_segment(const uint8_t *d_codes, msz_grid grid, int32_t *d_min_lab
 msz_status msz_compare(const uint8_t *d_codes_f, const uint8_t *d_codes_g, const int32_t *d_min_f,
                        const int32_t *d_max_f, const int32_t *d_min_g, const int32_t *d_max_g, int64_t n,
                        int64_t h_counts[5], void *d_workspace, size_t workspace_bytes, msz_stream_t stream);
+
+/* One field of a batch (msz_correct_batch).  Inputs: d_f, d_fhat, xi, grid
+ * (ndim 3), d_out and the edit-list arrays as in msz_correct.  Outputs, written
+ * by the call: edit_count, status (the msz_correct status this field alone
+ * would get) and stats. */
+typedef struct {
+    const float *d_f;
+    const float *d_fhat;
+    float xi;
+    int32_t status;         /* out */
+    msz_grid grid;
+    float *d_out;
+    uint32_t *d_edit_idx;
+    float *d_edit_delta;
+    int64_t edit_capacity;
+    int64_t edit_count;     /* out */
+    msz_stats stats;        /* out */
+    int32_t tile_z;         /* 0: msz_options.tile_z */
+    int32_t reserved;
+} msz_field;
+
+#define MSZ_BATCH_MAX_FIELDS 256
+#define MSZ_BATCH_MAX_SWEEPS 4096
+
+/* Bytes of device workspace msz_correct_batch needs for these fields and sweep
+ * cap (max_sweeps <= 0: MSZ_BATCH_MAX_SWEEPS); 0 for an invalid batch. */
+size_t msz_batch_workspace_size(int32_t n, const msz_field *fields, int64_t max_sweeps);
+
+/* Batched form of msz_correct (the benchmark spec's batching direction; the paper has
+ * no batched form): n 3D fields of any sizes, each with its own xi, corrected
+ * by one cooperative persistent launch.  The fields share one tile queue for
+ * the code pass and one set of sweeps; each field stops taking part when it is
+ * done, stuck or capped, and every field gets exactly the g, edit list,
+ * status and per-sweep counts that a separate msz_correct call would give
+ * (with the same options; d_g_init must be NULL).  h_sweep_log (may be NULL):
+ * 4*log_capacity int64 per field, field-major, as msz_options.h_sweep_log.
+ * Returns MSZ_OK when the launch completed (per-field statuses in fields[k]);
+ * MSZ_ERR_INPUT_BOUND when some field's input is out of bound (that field's
+ * status says so; no results); otherwise an error for the whole call.
+ * Synchronizes `stream`. */
+msz_status msz_correct_batch(int32_t n, msz_field *fields, const msz_options *opt, int64_t *h_sweep_log,
+                             int64_t log_capacity, void *d_workspace, size_t workspace_bytes, msz_stream_t stream);
 
 /* msz_correct for callers that cannot allocate device memory.  (The paper has
  * no counterpart: this entry point exists for how callers use the library.)

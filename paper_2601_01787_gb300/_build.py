@@ -32,6 +32,7 @@ UNITS = [
     ("msz_correct.cu", EXACT),
     ("msz_segment.cu", EXACT),
     ("msz_static.cu", EXACT),
+    ("msz_batch.cu", EXACT),
 ]
 
 

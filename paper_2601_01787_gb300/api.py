@@ -39,7 +39,7 @@ class Options(ctypes.Structure):
     _fields_ = [("rule", ctypes.c_int32), ("reserved", ctypes.c_int32), ("max_sweeps", ctypes.c_int64),
                 ("dense_min_items", ctypes.c_int64), ("d_g_init", ctypes.c_void_p),
                 ("h_sweep_log", ctypes.c_void_p), ("log_capacity", ctypes.c_int64),
-                ("h_timeline", ctypes.c_void_p)]
+                ("h_timeline", ctypes.c_void_p), ("tile_z", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -49,6 +49,18 @@ class Stats(ctypes.Structure):
     def as_dict(self) -> dict:
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
 
+
+class Field(ctypes.Structure):
+    """msz_field: one field of a batch (inputs, then outputs written by the call)."""
+    _fields_ = [("d_f", ctypes.c_void_p), ("d_fhat", ctypes.c_void_p), ("xi", ctypes.c_float),
+                ("status", ctypes.c_int32), ("grid", Grid), ("d_out", ctypes.c_void_p),
+                ("d_edit_idx", ctypes.c_void_p), ("d_edit_delta", ctypes.c_void_p),
+                ("edit_capacity", ctypes.c_int64), ("edit_count", ctypes.c_int64), ("stats", Stats),
+                ("tile_z", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+BATCH_MAX_FIELDS = 256
+BATCH_MAX_SWEEPS = 4096
 
 _lock = threading.Lock()
 _lib = None
@@ -88,6 +100,11 @@ def load(build_if_missing: bool = True):
         lib.msz_correct_static.argtypes = [P, P, ctypes.c_float, Grid, P, P, P, I64, ctypes.POINTER(I64),
                                            ctypes.POINTER(Options), ctypes.POINTER(Stats), P]
         lib.msz_correct_static.restype = st
+        lib.msz_batch_workspace_size.argtypes = [ctypes.c_int32, ctypes.POINTER(Field), I64]
+        lib.msz_batch_workspace_size.restype = SZ
+        lib.msz_correct_batch.argtypes = [ctypes.c_int32, ctypes.POINTER(Field), ctypes.POINTER(Options), P, I64, P,
+                                          SZ, P]
+        lib.msz_correct_batch.restype = st
         lib.msz_status_str.argtypes = [st]
         lib.msz_status_str.restype = ctypes.c_char_p
         _lib = lib
@@ -169,12 +186,12 @@ class CorrectResult:
         return self.status == OK
 
 
-def _options(rule, max_sweeps, dense_min_items, g_init, log_capacity):
+def _options(rule, max_sweeps, dense_min_items, g_init, log_capacity, tile_z=0):
     log = np.zeros(max(4 * log_capacity, 4), dtype=np.int64)
     tl = np.full(max(2 * log_capacity, 2), -1, dtype=np.int64)
     opt = Options(RULES[rule] if isinstance(rule, str) else int(rule), 0, int(max_sweeps), int(dense_min_items),
                   _dptr(g_init), log.ctypes.data if log_capacity else None, int(log_capacity),
-                  tl.ctypes.data if log_capacity else None)
+                  tl.ctypes.data if log_capacity else None, int(tile_z), 0)
     opt._keep = (log, tl)
     return opt, log
 
@@ -183,7 +200,7 @@ def correct(f: torch.Tensor, fhat: torch.Tensor, xi: float, *, rule="halve", max
             dense_min_items: int = 0, g_init: torch.Tensor | None = None, edit_capacity: int | None = None,
             log_capacity: int = 0, out: torch.Tensor | None = None, edit_idx: torch.Tensor | None = None,
             edit_delta: torch.Tensor | None = None, ws: torch.Tensor | None = None, stream=None,
-            check: bool = False) -> CorrectResult:
+            check: bool = False, tile_z: int = 0) -> CorrectResult:
     """Run the correction loop on device tensors (msz_correct)."""
     assert f.dtype == torch.float32 and fhat.dtype == torch.float32 and f.shape == fhat.shape
     lib = load()
@@ -199,7 +216,7 @@ def correct(f: torch.Tensor, fhat: torch.Tensor, xi: float, *, rule="halve", max
     need = int(lib.msz_workspace_size(g))
     if ws is None:
         ws = workspace(need, f.device)
-    opt, log = _options(rule, max_sweeps, dense_min_items, g_init, log_capacity)
+    opt, log = _options(rule, max_sweeps, dense_min_items, g_init, log_capacity, tile_z)
     stats = Stats()
     count = ctypes.c_int64()
     st = lib.msz_correct(_dptr(f), _dptr(fhat), ctypes.c_float(np.float32(xi)), g, _dptr(out),
@@ -288,3 +305,50 @@ def verify(f: torch.Tensor, g: torch.Tensor) -> dict:
     res = compare(cf, cg, mf, Mf, mg, Mg)
     res["codes_equal"] = bool(torch.equal(cf, cg))
     return res
+
+
+@dataclass
+class BatchResult:
+    status: int
+    fields: list  # CorrectResult per field
+
+
+def correct_batch(fs, fhats, xis, *, rule="halve", max_sweeps: int = 0, dense_min_items: int = 0,
+                  edit_capacities=None, log_capacity: int = 0, outs=None, ws: torch.Tensor | None = None,
+                  stream=None, tile_z=None) -> BatchResult:
+    """msz_correct_batch: many 3D fields (CUDA tensors) in one persistent launch."""
+    lib = load()
+    n = len(fs)
+    arr = (Field * n)()
+    keep = []
+    for k in range(n):
+        f, fh = fs[k], fhats[k]
+        assert f.dtype == torch.float32 and fh.dtype == torch.float32 and f.shape == fh.shape and f.dim() == 3
+        cap = f.numel() if edit_capacities is None else int(edit_capacities[k])
+        out = torch.empty_like(f) if outs is None else outs[k]
+        idx = torch.empty(max(cap, 1), dtype=torch.int32, device=f.device)
+        dl = torch.empty(max(cap, 1), dtype=torch.float32, device=f.device)
+        keep.append((out, idx, dl, cap))
+        tz = 0 if tile_z is None else int(tile_z[k])
+        arr[k] = Field(_dptr(f), _dptr(fh), ctypes.c_float(np.float32(xis[k])), -1, grid_of(f.shape), _dptr(out),
+                       _dptr(idx), _dptr(dl), cap, 0, Stats(), tz, 0)
+    need = int(lib.msz_batch_workspace_size(n, arr, int(max_sweeps)))
+    if need == 0:
+        raise MszError(ERR_INVALID_ARG, "msz_batch_workspace_size")
+    if ws is None:
+        ws = workspace(need, fs[0].device)
+    opt, _ = _options(rule, max_sweeps, dense_min_items, None, 0)
+    log = np.zeros(max(4 * n * log_capacity, 4), dtype=np.int64)
+    st = lib.msz_correct_batch(n, arr, ctypes.byref(opt), log.ctypes.data if log_capacity else None, log_capacity,
+                               _dptr(ws), ws.numel(), _stream(stream))
+    results = []
+    for k in range(n):
+        out, idx, dl, cap = keep[k]
+        fk = arr[k]
+        m = min(int(fk.edit_count), cap)
+        stats = fk.stats.as_dict()
+        nlog = min(stats["sweeps"] + 1, log_capacity)
+        lg = log[4 * k * log_capacity:4 * (k * log_capacity + nlog)].reshape(-1, 4).copy() if log_capacity else \
+            np.zeros((0, 4), np.int64)
+        results.append(CorrectResult(int(fk.status), out, idx[:m], dl[:m], int(fk.edit_count), stats, lg))
+    return BatchResult(int(st), results)

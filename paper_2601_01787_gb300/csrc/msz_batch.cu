@@ -1,0 +1,561 @@
+// msz_batch.cu -- many fields of uneven sizes corrected by one cooperative
+// persistent launch (msz_correct_batch).
+//
+// The fields sit side by side in one virtual index space (field k owns
+// vertices [base_k, base_k + n_k), bases aligned to 1024 vertices).  The
+// workspace bitmaps and codes span that space; each field's FieldView holds
+// windows into them, so the per-field phases of msz_phases.cuh run unchanged.
+//   - codes pass: one tile queue over every field's tiles;
+//   - every later phase walks the shared bitmaps; a set bit is mapped to its
+//     field by binary search over the bases;
+//   - each (sweep, field) pair gets its own record (worklist, distorted,
+//     targets, changed), accumulated in shared memory per block;
+//   - a field stops taking part once it is done (no distortion), stuck or
+//     capped; the launch ends when every field has stopped;
+//   - the edit list is split per field into the caller's arrays.
+// Every field's sweeps are the same Jacobi sweeps as a separate msz_correct
+// call, so its g, edit list and per-sweep records are identical.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <mutex>
+#include <vector>
+
+#include "msz.h"
+#include "msz_device.cuh"
+#include "msz_phases.cuh"
+#include "msz_tile.cuh"
+#include "msz_workspace.h"
+
+namespace msz {
+namespace {
+
+constexpr int kThreads = tile::THREADS;
+constexpr int kMinBlocksB = 3;
+constexpr uint32_t kDenseFactorB = 6;
+
+struct FieldDev {
+    FieldView F;
+    uint32_t base;       // first vertex in the shared index space (multiple of 1024)
+    uint32_t tile_base;  // first tile in the shared tile queue
+    uint32_t *edit_idx;
+    float *edit_delta;
+    unsigned long long edit_cap;
+};
+
+struct BatchRec {
+    uint32_t worklist, distorted, targets, changed;
+    uint32_t dense;  // the detection of this sweep scanned every uncertified vertex
+    uint32_t pad[3];
+};
+
+struct FieldRes {
+    unsigned long long edit_count;
+    uint32_t error;
+    uint32_t pad;
+};
+
+struct BatchProblem {
+    const FieldDev *fields;
+    uint32_t nfields;
+    uint32_t ntiles;
+    GridDev all;  // the shared index space (only n, words used)
+    Ctrl *ctrl;
+    BatchRec *log;  // [sweep][field]
+    FieldRes *res;
+    uint32_t *bsum;
+    uint32_t max_sweeps;
+    long long dense_min;
+    uint32_t *tb, *dm[2], *eb, *ub;  // shared bitmaps (global words)
+};
+
+struct BatchLayout {
+    size_t ctrl, fields, log, res, bsum, tb, d0, d1, eb, ub, codes, total, zero_bytes;
+};
+
+BatchLayout batch_layout(uint32_t nfields, uint64_t ntot, uint32_t max_sweeps) {
+    BatchLayout L{};
+    const uint64_t words = ntot / 32;
+    size_t o = 0;
+    L.ctrl = o;   o = align_up(o + sizeof(Ctrl));
+    L.res = o;    o = align_up(o + nfields * sizeof(FieldRes));
+    L.log = o;    o = align_up(o + (size_t)(max_sweeps + 2) * nfields * sizeof(BatchRec));
+    L.bsum = o;   o = align_up(o + kMaxBlocks * sizeof(uint32_t));
+    L.tb = o;     o = align_up(o + words * 4);
+    L.d0 = o;     o = align_up(o + words * 4);
+    L.d1 = o;     o = align_up(o + words * 4);
+    L.eb = o;     o = align_up(o + words * 4);
+    L.ub = o;     o = align_up(o + words * 4);
+    L.zero_bytes = o;
+    L.fields = o; o = align_up(o + nfields * sizeof(FieldDev));
+    L.codes = o;  o = align_up(o + ntot);
+    L.total = o;
+    return L;
+}
+
+// Field of a vertex (or tile) of the shared space: the last k with tab[k] <= v.
+__device__ __forceinline__ uint32_t find_field(const uint32_t *tab, uint32_t n, uint32_t v) {
+    uint32_t lo = 0, hi = n;  // tab[lo] <= v < tab[hi]
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (tab[mid] <= v) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Block-local per-field counters, flushed to the (sweep, field) record.
+__device__ __forceinline__ void flush_counts(uint32_t (*cnt)[4], uint32_t nf, BatchRec *rec) {
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < nf * 4; i += blockDim.x) {
+        const uint32_t k = i >> 2, c = i & 3;
+        const uint32_t v = cnt[k][c];
+        if (v) {
+            uint32_t *dst = c == 0 ? &rec[k].worklist : c == 1 ? &rec[k].distorted : c == 2 ? &rec[k].targets
+                                                                                        : &rec[k].changed;
+            atomicAdd(dst, v);
+            cnt[k][c] = 0;
+        }
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant__ const BatchProblem P) {
+    extern __shared__ __align__(16) float smem[];
+    __shared__ uint32_t s_base[MSZ_BATCH_MAX_FIELDS + 1];
+    __shared__ uint32_t s_tile[MSZ_BATCH_MAX_FIELDS + 1];
+    __shared__ uint32_t s_cnt[MSZ_BATCH_MAX_FIELDS][4];
+    __shared__ uint32_t s_alive[(MSZ_BATCH_MAX_FIELDS + 31) / 32];
+    __shared__ uint32_t s_next;
+    __shared__ unsigned long long s_sum;
+    __shared__ uint32_t sm[40];
+    const uint32_t nf = P.nfields;
+    Ctrl *C = P.ctrl;
+    const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+    for (uint32_t k = threadIdx.x; k <= nf; k += blockDim.x) {
+        s_base[k] = k < nf ? P.fields[k].base : P.all.n;
+        s_tile[k] = k < nf ? P.fields[k].tile_base : P.ntiles;
+    }
+    for (uint32_t i = threadIdx.x; i < nf * 4; i += blockDim.x) s_cnt[i >> 2][i & 3] = 0;
+    for (uint32_t i = threadIdx.x; i < (nf + 31) / 32; i += blockDim.x) s_alive[i] = 0xffffffffu;
+    __syncthreads();
+    if (leader) C->t_start = global_ns();
+    auto alive = [&](uint32_t k) { return (s_alive[k >> 5] >> (k & 31u)) & 1u; };
+
+    // ---- codes of every field, one shared tile queue
+    {
+        bool bad = false;
+        for (;;) {
+            __syncthreads();
+            if (threadIdx.x == 0) s_next = atomicAdd(&C->flag, 1u);
+            __syncthreads();
+            const uint32_t t = s_next;
+            if (t >= P.ntiles) break;
+            const uint32_t k = find_field(s_tile, nf, t);
+            const FieldView &F = P.fields[k].F;
+            const tile::TileGeom tg = tile::tile_geom(F.G.nx, F.G.ny, F.G.nz, F.tile_z);
+            const uint32_t lt = t - s_tile[k];
+            const uint32_t txi = lt % tg.tx, tyi = (lt / tg.tx) % tg.ty, tzi = lt / (tg.tx * tg.ty);
+            const int zb = (int)(tzi * tg.bz);
+            bool fb = false;
+            first_tile(F, (int)(txi * tile::BX), (int)(tyi * tile::BY), zb, min(zb + (int)tg.bz, (int)F.G.nz), smem,
+                       fb);
+            if (fb) atomicOr(&P.res[k].error, kErrInput);
+            bad = bad || fb;
+        }
+        if (bad) atomicOr(&C->error, kErrInput);
+    }
+    bool ok = grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
+    if (leader) C->t_codes = global_ns();
+
+    // ---- detection of sweep 0 over the uncertified vertices of every field
+    if (ok) {
+        uint32_t seen = 0;
+        walk_bits<false>(P.ub, nullptr, P.all, seen, [&](bool has, uint32_t v) {
+            uint32_t k = 0;
+            if (has) k = find_field(s_base, nf, v);
+            const FieldView &F = P.fields[k].F;
+            Emitter E{F.dm[1], 0};
+            detect_vertex<3>(F, E, has, has ? v - s_base[k] : 0u);
+            if (E.distorted) atomicAdd(&s_cnt[k][1], 1u);
+        });
+        flush_counts(s_cnt, nf, P.log);
+    }
+    ok = ok && grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
+    uint32_t k = 0;
+    while (ok) {
+        BatchRec *rec = P.log + (size_t)k * nf;
+        // every block derives the same verdicts from the same records
+        if (threadIdx.x == 0) s_sum = 0;
+        __syncthreads();
+        unsigned long long m_all = 0;
+        for (uint32_t f = threadIdx.x; f < nf; f += blockDim.x) {
+            if (!alive(f)) continue;
+            const uint32_t m = ld_relaxed(&rec[f].distorted);
+            if (m == 0) atomicAnd(&s_alive[f >> 5], ~(1u << (f & 31u)));  // done
+            m_all += m;
+        }
+        if (m_all) atomicAdd(&s_sum, m_all);
+        __syncthreads();
+        const unsigned long long m_tot = s_sum;
+        __syncthreads();
+        if (m_tot == 0) {
+            if (leader) { C->status = MSZ_OK; C->sweeps = k; }
+            break;
+        }
+        if (k >= P.max_sweeps) {
+            uint32_t nt = 0;
+            walk_bits<true>(P.tb, nullptr, P.all, nt, [&](bool has, uint32_t t) {
+                if (has) {
+                    const uint32_t f = find_field(s_base, nf, t);
+                    if (alive(f)) atomicAdd(&s_cnt[f][2], 1u);
+                }
+            });
+            flush_counts(s_cnt, nf, rec);
+            if (leader) { C->status = MSZ_ERR_MAX_SWEEPS; C->sweeps = k; }
+            ok = grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
+            break;
+        }
+        const bool dense_next = P.dense_min >= 0 && m_tot * kDenseFactorB >= (unsigned long long)P.dense_min;
+        // ---- edit phase of sweep k
+        {
+            uint32_t targets = 0;
+            walk_bits<true>(P.tb, nullptr, P.all, targets, [&](bool has, uint32_t t) {
+                if (!has) return;
+                const uint32_t f = find_field(s_base, nf, t);
+                if (!alive(f)) return;
+                const FieldView &F = P.fields[f].F;
+                atomicAdd(&s_cnt[f][2], 1u);
+                if (apply_target<3>(F, t - s_base[f], dense_next, F.dm[(k + 1) & 1])) atomicAdd(&s_cnt[f][3], 1u);
+            });
+            (void)targets;
+            flush_counts(s_cnt, nf, rec);
+        }
+        ok = grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
+        if (!ok) break;
+        // fields whose targets were all at their floor are stuck
+        uint32_t any_changed = 0;
+        for (uint32_t f = threadIdx.x; f < nf; f += blockDim.x) {
+            if (!alive(f)) continue;
+            if (ld_relaxed(&rec[f].changed) == 0) atomicAnd(&s_alive[f >> 5], ~(1u << (f & 31u)));
+            else any_changed = 1;
+        }
+        if (!__syncthreads_or(any_changed)) {
+            if (leader) { C->status = MSZ_STUCK; C->sweeps = k + 1; }
+            break;
+        }
+        // ---- detection phase of sweep k + 1
+        const uint32_t k1 = k + 1;
+        BatchRec *rec1 = P.log + (size_t)k1 * nf;
+        uint32_t *dcur = P.dm[k1 & 1];
+        if (dense_next) {
+            const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+            for (uint32_t w = gtid; w < P.all.words; w += stride) dcur[w] = 0;
+            for (uint32_t f = gtid; f < nf; f += stride)
+                if (alive(f)) {
+                    rec1[f].worklist = P.fields[f].F.G.n;
+                    rec1[f].dense = 1;
+                }
+            uint32_t seen = 0;
+            walk_bits<false>(P.ub, nullptr, P.all, seen, [&](bool has, uint32_t v) {
+                uint32_t f = 0;
+                if (has) f = find_field(s_base, nf, v);
+                const bool live = has && alive(f);
+                const FieldView &F = P.fields[f].F;
+                Emitter E{F.dm[(k1 + 1) & 1], 0};
+                detect_vertex<3>(F, E, live, live ? v - s_base[f] : 0u);
+                if (E.distorted) atomicAdd(&s_cnt[f][1], 1u);
+            });
+        } else {
+            const uint32_t lane = lane_id();
+            const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+            const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+            // worklist sizes per field (each bitmap word belongs to one field)
+            for (uint32_t base = gw * 32u; base < P.all.words; base += nw * 32u) {
+                const uint32_t wi = base + lane;
+                const uint32_t bits = wi < P.all.words ? dcur[wi] : 0u;
+                if (bits) {
+                    const uint32_t f = find_field(s_base, nf, wi * 32u);
+                    if (alive(f)) atomicAdd(&s_cnt[f][0], (uint32_t)__popc(bits));
+                }
+            }
+            uint32_t seen = 0;
+            walk_bits<true>(dcur, P.ub, P.all, seen, [&](bool has, uint32_t v) {
+                uint32_t f = 0;
+                if (has) f = find_field(s_base, nf, v);
+                const bool live = has && alive(f);
+                const FieldView &F = P.fields[f].F;
+                Emitter E{F.dm[(k1 + 1) & 1], 0};
+                detect_vertex<3>(F, E, live, live ? v - s_base[f] : 0u);
+                if (E.distorted) atomicAdd(&s_cnt[f][1], 1u);
+            });
+        }
+        flush_counts(s_cnt, nf, rec1);
+        ok = grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
+        k = k1;
+    }
+    if (!ok) return;
+
+    // ---- edit lists, split per field, ascending index
+    const uint32_t W = P.all.words;
+    const uint32_t per = (W + gridDim.x - 1) / gridDim.x;
+    const uint32_t w0 = min(blockIdx.x * per, W), w1 = min(w0 + per, W);
+    uint32_t cnt = 0;
+    for (uint32_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) {
+        const uint32_t c = __popc(P.eb[w]);
+        cnt += c;
+        if (c) atomicAdd(&s_cnt[find_field(s_base, nf, w * 32u)][0], c);
+    }
+    uint32_t tot;
+    block_exclusive_scan(cnt, sm, tot);
+    if (threadIdx.x == 0) P.bsum[blockIdx.x] = tot;
+    __syncthreads();
+    for (uint32_t f = threadIdx.x; f < nf; f += blockDim.x)
+        if (s_cnt[f][0]) {
+            atomicAdd(&P.res[f].edit_count, (unsigned long long)s_cnt[f][0]);
+            s_cnt[f][0] = 0;
+        }
+    if (!grid_barrier(&C->bar_count, &C->bar_gen, &C->error)) return;
+    uint32_t pre = 0;
+    for (uint32_t b = threadIdx.x; b < blockIdx.x; b += blockDim.x) pre += ld_relaxed(&P.bsum[b]);
+    uint32_t prefix;
+    block_exclusive_scan(pre, sm, prefix);
+    // s_tile reused: exclusive prefix of the per-field edit counts
+    if (threadIdx.x == 0) {
+        unsigned long long acc = 0;
+        for (uint32_t f = 0; f < nf; ++f) {
+            s_tile[f] = (uint32_t)acc;
+            acc += ((volatile FieldRes *)P.res)[f].edit_count;
+        }
+    }
+    __syncthreads();
+    for (uint32_t r = w0; r < w1; r += blockDim.x) {
+        const uint32_t w = r + threadIdx.x;
+        const uint32_t word = w < w1 ? P.eb[w] : 0u;
+        uint32_t rt;
+        const uint32_t ex = block_exclusive_scan((uint32_t)__popc(word), sm, rt);
+        if (word) {
+            const uint32_t f = find_field(s_base, nf, w * 32u);
+            const FieldDev &D = P.fields[f];
+            unsigned long long pos = (unsigned long long)(prefix + ex) - s_tile[f];
+            uint32_t bits = word;
+            while (bits) {
+                const uint32_t b = (uint32_t)(__ffs(bits) - 1);
+                bits &= bits - 1;
+                const uint32_t i = w * 32u + b - s_base[f];
+                if (pos < D.edit_cap) {
+                    D.edit_idx[pos] = i;
+                    D.edit_delta[pos] = __fsub_rn(D.F.g[i], __ldg(&D.F.fhat[i]));
+                }
+                ++pos;
+            }
+        }
+        prefix += rt;
+    }
+    if (!grid_barrier(&C->bar_count, &C->bar_gen, &C->error)) return;
+    if (leader) C->t_end = global_ns();
+}
+
+std::mutex g_batch_mu;
+
+msz_status batch_blocks(const DeviceInfo &d, int &blocks) {
+    static int cache[64];
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    if (!cache[d.device]) {
+        const size_t sm = tile::kRingBytes;
+        if (cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+            return MSZ_ERR_CUDA;
+        int per = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch, kThreads, sm) != cudaSuccess)
+            return MSZ_ERR_CUDA;
+        if (per < 1) return MSZ_ERR_UNSUPPORTED;
+        int b = per * d.sms;
+        if (b > (int)kMaxBlocks) b = (int)kMaxBlocks;
+        cache[d.device] = b;
+    }
+    blocks = cache[d.device];
+    return MSZ_OK;
+}
+
+// Shared index space of the fields: per-field base (1024-aligned) and total.
+uint32_t field_tile_z(const msz_field &f, const msz_options *opt) {
+    if (f.tile_z > 0) return (uint32_t)f.tile_z;
+    if (opt && opt->tile_z > 0) return (uint32_t)opt->tile_z;
+    return kTileZ;
+}
+
+bool plan(int32_t n, const msz_field *fields, const msz_options *opt, std::vector<GridDev> &grids,
+          std::vector<uint32_t> &bases, uint64_t &ntot, uint32_t &ntiles, std::vector<uint32_t> &tile_bases) {
+    grids.resize(n);
+    bases.resize(n);
+    tile_bases.resize(n);
+    ntot = 0;
+    uint64_t tiles = 0;
+    for (int32_t k = 0; k < n; ++k) {
+        if (fields[k].grid.ndim != 3 || make_grid(fields[k].grid, grids[k]) != MSZ_OK) return false;
+        bases[k] = (uint32_t)ntot;
+        ntot += ((uint64_t)grids[k].n + 1023) / 1024 * 1024;
+        tile_bases[k] = (uint32_t)tiles;
+        const uint32_t tz = field_tile_z(fields[k], opt);
+        if (tz < 1 || tz > 1024) return false;
+        tiles += tile::tile_geom(grids[k].nx, grids[k].ny, grids[k].nz, tz).count;
+        if (ntot > (uint64_t)MSZ_MAX_VERTICES || tiles > 0xffffffffull) return false;
+    }
+    ntiles = (uint32_t)tiles;
+    return true;
+}
+
+}  // namespace
+}  // namespace msz
+
+using namespace msz;
+
+extern "C" size_t msz_batch_workspace_size(int32_t n, const msz_field *fields, int64_t max_sweeps) {
+    if (n < 1 || n > MSZ_BATCH_MAX_FIELDS || !fields) return 0;
+    if (max_sweeps <= 0) max_sweeps = MSZ_BATCH_MAX_SWEEPS;
+    if (max_sweeps > MSZ_BATCH_MAX_SWEEPS) return 0;
+    std::vector<GridDev> grids;
+    std::vector<uint32_t> bases, tile_bases;
+    uint64_t ntot;
+    uint32_t ntiles;
+    if (!plan(n, fields, nullptr, grids, bases, ntot, ntiles, tile_bases)) return 0;
+    return batch_layout((uint32_t)n, ntot, (uint32_t)max_sweeps).total;
+}
+
+extern "C" msz_status msz_correct_batch(int32_t n, msz_field *fields, const msz_options *opt,
+                                        int64_t *h_sweep_log, int64_t log_capacity, void *d_workspace,
+                                        size_t workspace_bytes, msz_stream_t stream) {
+    if (n < 1 || n > MSZ_BATCH_MAX_FIELDS || !fields) return MSZ_ERR_INVALID_ARG;
+    msz_options o{};
+    if (opt) o = *opt;
+    if (o.rule != MSZ_RULE_HALVE && o.rule != MSZ_RULE_SNAP) return MSZ_ERR_INVALID_ARG;
+    if (o.d_g_init || o.max_sweeps > MSZ_BATCH_MAX_SWEEPS || o.dense_min_items < -1 || log_capacity < 0 ||
+        (log_capacity > 0 && !h_sweep_log))
+        return MSZ_ERR_INVALID_ARG;
+    const uint32_t max_sweeps = o.max_sweeps <= 0 ? (uint32_t)MSZ_BATCH_MAX_SWEEPS : (uint32_t)o.max_sweeps;
+    for (int32_t k = 0; k < n; ++k) {
+        const msz_field &F = fields[k];
+        if (!F.d_f || !F.d_fhat || !F.d_out || F.edit_capacity < 0 ||
+            (F.edit_capacity > 0 && (!F.d_edit_idx || !F.d_edit_delta)) || !(F.xi >= 0.0f) || isinf(F.xi))
+            return MSZ_ERR_INVALID_ARG;
+    }
+    std::vector<GridDev> grids;
+    std::vector<uint32_t> bases, tile_bases;
+    uint64_t ntot;
+    uint32_t ntiles;
+    if (!plan(n, fields, &o, grids, bases, ntot, ntiles, tile_bases)) return MSZ_ERR_INVALID_ARG;
+    const BatchLayout L = batch_layout((uint32_t)n, ntot, max_sweeps);
+    if (!d_workspace || workspace_bytes < L.total) return MSZ_ERR_WORKSPACE;
+    if ((uintptr_t)d_workspace % kAlign) return MSZ_ERR_INVALID_ARG;
+    DeviceInfo dev;
+    msz_status st = current_device(dev);
+    if (st != MSZ_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    char *ws = (char *)d_workspace;
+
+    std::vector<FieldDev> tab(n);
+    for (int32_t k = 0; k < n; ++k) {
+        FieldDev &D = tab[k];
+        memset(&D, 0, sizeof D);
+        FieldView &F = D.F;
+        const uint32_t wb = bases[k] / 32;
+        F.G = grids[k];
+        F.f = fields[k].d_f;
+        F.fhat = fields[k].d_fhat;
+        F.ginit = nullptr;
+        F.g = fields[k].d_out;
+        F.codes_f = (uint8_t *)(ws + L.codes) + bases[k];
+        F.tb = (uint32_t *)(ws + L.tb) + wb;
+        F.dm[0] = (uint32_t *)(ws + L.d0) + wb;
+        F.dm[1] = (uint32_t *)(ws + L.d1) + wb;
+        F.eb = (uint32_t *)(ws + L.eb) + wb;
+        F.ub = (uint32_t *)(ws + L.ub) + wb;
+        F.xi = fields[k].xi;
+        F.two_xi = 2.0f * fields[k].xi;
+        F.rule = o.rule;
+        F.tile_z = field_tile_z(fields[k], &o);
+        D.base = bases[k];
+        D.tile_base = tile_bases[k];
+        D.edit_idx = fields[k].d_edit_idx;
+        D.edit_delta = fields[k].d_edit_delta;
+        D.edit_cap = (unsigned long long)fields[k].edit_capacity;
+    }
+    BatchProblem P{};
+    P.fields = (const FieldDev *)(ws + L.fields);
+    P.nfields = (uint32_t)n;
+    P.ntiles = ntiles;
+    P.all.n = (uint32_t)ntot;
+    P.all.words = (uint32_t)(ntot / 32);
+    P.ctrl = (Ctrl *)(ws + L.ctrl);
+    P.log = (BatchRec *)(ws + L.log);
+    P.res = (FieldRes *)(ws + L.res);
+    P.bsum = (uint32_t *)(ws + L.bsum);
+    P.max_sweeps = max_sweeps;
+    P.dense_min = o.dense_min_items == 0 ? (long long)(ntot / 16 > 0 ? ntot / 16 : 1) : (long long)o.dense_min_items;
+    P.tb = (uint32_t *)(ws + L.tb);
+    P.dm[0] = (uint32_t *)(ws + L.d0);
+    P.dm[1] = (uint32_t *)(ws + L.d1);
+    P.eb = (uint32_t *)(ws + L.eb);
+    P.ub = (uint32_t *)(ws + L.ub);
+
+    if (cudaMemsetAsync(ws, 0, L.zero_bytes, s) != cudaSuccess) return MSZ_ERR_CUDA;
+    if (cudaMemcpyAsync(ws + L.fields, tab.data(), n * sizeof(FieldDev), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return MSZ_ERR_CUDA;
+    int blocks = 0;
+    if ((st = batch_blocks(dev, blocks)) != MSZ_OK) return st;
+    void *args[] = {(void *)&P};
+    if (cudaLaunchCooperativeKernel((const void *)k_batch, dim3(blocks), dim3(kThreads), args, tile::kRingBytes, s) !=
+        cudaSuccess)
+        return MSZ_ERR_CUDA;
+    Ctrl hc;
+    std::vector<FieldRes> res(n);
+    if (cudaMemcpyAsync(&hc, ws + L.ctrl, sizeof hc, cudaMemcpyDeviceToHost, s) != cudaSuccess) return MSZ_ERR_CUDA;
+    if (cudaMemcpyAsync(res.data(), ws + L.res, n * sizeof(FieldRes), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return MSZ_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return MSZ_ERR_CUDA;
+    if (hc.error & kErrTimeout) return MSZ_ERR_TIMEOUT;
+    if (hc.error & kErrInput) {
+        for (int32_t k = 0; k < n; ++k) fields[k].status = res[k].error ? MSZ_ERR_INPUT_BOUND : MSZ_ERR_INVALID_ARG;
+        return MSZ_ERR_INPUT_BOUND;
+    }
+    // per-field records, then each field's own termination rule
+    const uint32_t S = hc.sweeps;  // last sweep index the launch reached
+    std::vector<BatchRec> log((size_t)(S + 1) * n);
+    if (cudaMemcpy(log.data(), ws + L.log, log.size() * sizeof(BatchRec), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return MSZ_ERR_CUDA;
+    const int64_t kernel_ns = hc.t_end > hc.t_start ? (int64_t)(hc.t_end - hc.t_start) : 0;
+    const int64_t codes_ns = hc.t_codes > hc.t_start ? (int64_t)(hc.t_codes - hc.t_start) : 0;
+    for (int32_t k = 0; k < n; ++k) {
+        msz_field &F = fields[k];
+        msz_stats &stt = F.stats;
+        memset(&stt, 0, sizeof stt);
+        stt.first_distorted = log[k].distorted;
+        stt.kernel_ns = kernel_ns;
+        stt.codes_ns = codes_ns;
+        msz_status fs = MSZ_ERR_MAX_SWEEPS;
+        for (uint32_t q = 0; q <= S; ++q) {
+            const BatchRec &r = log[(size_t)q * n + k];
+            const int64_t wl = q == 0 ? (int64_t)grids[k].n : (int64_t)r.worklist;
+            stt.examined += wl;
+            stt.dense_sweeps += (q == 0 || r.dense) ? 1 : 0;
+            if (h_sweep_log && q < (uint64_t)log_capacity) {
+                int64_t *row = h_sweep_log + 4 * ((size_t)k * log_capacity + q);
+                row[0] = wl;
+                row[1] = r.distorted;
+                row[2] = r.targets;
+                row[3] = r.changed;
+            }
+            if (r.distorted == 0) { fs = MSZ_OK; stt.sweeps = q; break; }
+            if (q >= max_sweeps) { fs = MSZ_ERR_MAX_SWEEPS; stt.sweeps = q; stt.left = r.distorted; break; }
+            if (r.changed == 0) { fs = MSZ_STUCK; stt.sweeps = q + 1; stt.left = r.distorted; break; }
+            stt.edits += r.changed;
+        }
+        F.edit_count = (int64_t)res[k].edit_count;
+        stt.edited = F.edit_count;
+        if (fs == MSZ_OK && F.edit_count > F.edit_capacity) fs = MSZ_ERR_CAPACITY;
+        F.status = fs;
+    }
+    return MSZ_OK;
+}

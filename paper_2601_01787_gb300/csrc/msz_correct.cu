@@ -26,319 +26,37 @@
 
 #include "msz.h"
 #include "msz_device.cuh"
+#include "msz_phases.cuh"
 #include "msz_tile.cuh"
 #include "msz_workspace.h"
 
 namespace msz {
 
 constexpr int kThreads = tile::THREADS;  // 256 per block of the persistent kernel
-constexpr uint32_t kTileZ = 32;          // planes per tile of a whole-grid pass
 #ifndef MSZ_MIN_BLOCKS
 #define MSZ_MIN_BLOCKS 3
 #endif
 constexpr int kMinBlocks = MSZ_MIN_BLOCKS;  // resident blocks per SM the register budget aims at
 constexpr uint32_t kDenseFactor = 6;        // worklist estimate: 6 x distorted vertices
-constexpr int kDenseWord = 6;               // set bits from which a bitmap word is walked by the whole warp
 
 struct Problem {
-    GridDev G;
-    const float *f;
-    const float *fhat;
-    const float *ginit;
-    float *g;
-    uint8_t *codes_f;
-    uint32_t *tb;      // targets of the current sweep
-    uint32_t *dm[2];   // worklist of a sweep, by sweep parity
-    uint32_t *eb;      // edited vertices
-    uint32_t *ub;      // uncertified vertices: the only ones that can ever be distorted
+    FieldView F;
     Ctrl *ctrl;
     SweepRec *log;
     uint32_t *bsum;
     uint32_t *edit_idx;
     float *edit_delta;
     unsigned long long edit_cap;
-    float xi;
-    float two_xi;      // 2 xi rounded up: the certification margin
-    int rule;
     uint32_t max_sweeps;
     long long dense_min;  // < 0: never scan densely after sweep 0
 };
-
-// Where a detection phase records: the targets (P.tb) and the worklist of the
-// next sweep (dnext); distorted vertices are counted per thread and added to
-// the sweep's record when the phase ends.
-struct Emitter {
-    uint32_t *dnext;
-    uint32_t distorted;
-};
-
-// Warp-collective: vertex v (valid lanes) with codes cf in f and cg in g; a
-// distorted vertex marks its targets and, unless the caller marks whole words
-// itself (self_marked), itself for the next worklist.
-__device__ __forceinline__ bool report(const Problem &P, Emitter &E, bool valid, uint32_t v, uint32_t cf,
-                                       uint32_t cg, bool self_marked = false) {
-    const bool dist = valid && cf != cg;
-    if (!__any_sync(kFull, dist)) return false;
-    if (dist) {
-        uint32_t t0, t1;
-        const int nt = targets_of(P.G, v, (uint8_t)cf, (uint8_t)cg, t0, t1);
-        red_or(&P.tb[t0 >> 5], 1u << (t0 & 31u));
-        if (nt > 1) red_or(&P.tb[t1 >> 5], 1u << (t1 & 31u));
-        if (!self_marked) red_or(&E.dnext[v >> 5], 1u << (v & 31u));
-        E.distorted += 1;
-    }
-    return dist;
-}
-
-// Warp-collective walk over the set bits of a bitmap: each warp takes 32
-// consecutive words (1024 vertices) at a time, grid-stride.  CLEAR zeroes the
-// visited words; `seen` counts their set bits; a non-null filter restricts the
-// calls to the vertices also set there.  fn(valid, v) runs once per round
-// with one vertex per lane.
-template <bool CLEAR, class F>
-__device__ __forceinline__ void walk_bits(uint32_t *bm, const uint32_t *filter, const GridDev &G, uint32_t &seen,
-                                          F &&fn) {
-    const uint32_t lane = lane_id();
-    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t base = gw * 32u; base < G.words; base += nw * 32u) {
-        const uint32_t wi = base + lane;
-        uint32_t bits = 0;
-        if (wi < G.words) {
-            bits = bm[wi];
-            if (CLEAR && bits) bm[wi] = 0u;
-            seen += (uint32_t)__popc(bits);
-            if (filter && bits) bits &= filter[wi];
-        }
-        // words with many set bits: the whole warp takes one word at a time,
-        // lane l on vertex 32*word + l, so neighbour loads coalesce
-        const bool dense = __popc(bits) >= kDenseWord;
-        uint32_t dm = __ballot_sync(kFull, dense);
-        while (dm) {
-            const int j = __ffs(dm) - 1;
-            dm &= dm - 1u;
-            const uint32_t word = __shfl_sync(kFull, bits, j);
-            fn(((word >> lane) & 1u) != 0u, (base + (uint32_t)j) * 32u + lane);
-        }
-        if (dense) bits = 0u;
-        // the remaining sparse words: each lane walks its own word's bits
-        while (__any_sync(kFull, bits != 0u)) {
-            const bool has = bits != 0u;
-            uint32_t v = 0;
-            if (has) {
-                v = wi * 32u + (uint32_t)(__ffs(bits) - 1);
-                bits &= bits - 1u;
-            }
-            fn(has, v);
-        }
-    }
-}
-
-// Detection of one vertex in the current g (warp-collective).
-template <int NDIM>
-__device__ __forceinline__ void detect_vertex(const Problem &P, Emitter &E, bool has, uint32_t v) {
-    uint32_t cf = 0, cg = 0;
-    if (has) {
-        uint32_t x, y, z;
-        coords_of(P.G, v, x, y, z);
-        cg = code_global<NDIM>(P.g, P.G, v, x, y, z);
-        cf = __ldg(&P.codes_f[v]);
-    }
-    report(P, E, has, v, cf, cg);
-}
-
-// ------------------------------------------------ generic (2D) codes of f
-template <int NDIM>
-__device__ void first_generic(const Problem &P) {
-    const GridDev &G = P.G;
-    const uint32_t lane = lane_id();
-    const uint32_t stride = gridDim.x * blockDim.x;
-    bool bad = false;
-    for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < G.n; base += stride) {
-        const uint32_t i = base + lane;
-        const bool valid = i < G.n;
-        bool differs = false, uncert = false;
-        if (valid) {
-            uint32_t x, y, z;
-            coords_of(G, i, x, y, z);
-            const float fi = P.f[i], fh = P.fhat[i];
-            const float gs = P.ginit ? P.ginit[i] : fh;
-            const float L = floor_bound(fi, P.xi), U = ceil_bound(fi, P.xi);
-            bad = bad || !(isfinite(fi) && isfinite(fh) && fh >= L && fh <= U);
-            if (P.ginit) {
-                bad = bad || !(isfinite(gs) && gs >= L && gs <= U);
-                differs = __float_as_uint(gs) != __float_as_uint(fh);
-            }
-            bool cert;
-            P.codes_f[i] = code_global_cert<NDIM>(P.f, G, i, x, y, z, P.two_xi, cert);
-            uncert = !cert;
-            P.g[i] = gs;
-        }
-        // base is a multiple of 32: this warp owns whole bitmap words
-        const uint32_t um = __ballot_sync(kFull, uncert);
-        if (lane == 0) P.ub[base >> 5] = um;
-        if (P.ginit) {
-            const uint32_t m = __ballot_sync(kFull, differs);
-            if (lane == 0 && m) P.eb[base >> 5] = m;
-        }
-    }
-    if (bad) atomicOr(&P.ctrl->error, kErrInput);
-}
-
-// ------------------------------------------------ tiled (3D) codes of f
-// Codes of f with their certification, g = start value, bound check.
-__device__ void first_tiled(const Problem &P, uint32_t *tile_next, float *smem) {
-    using namespace tile;
-    const GridDev &G = P.G;
-    const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
-    const TileGeom tg = tile_geom(G.nx, G.ny, G.nz, kTileZ);
-    __shared__ uint32_t s_tile;
-    bool bad = false;
-    for (;;) {
-        __syncthreads();
-        if (tid == 0) s_tile = atomicAdd(tile_next, 1u);
-        __syncthreads();
-        const uint32_t t = s_tile;
-        if (t >= tg.count) break;
-        const uint32_t txi = t % tg.tx, tyi = (t / tg.tx) % tg.ty, tzi = t / (tg.tx * tg.ty);
-        const int x0 = (int)(txi * BX), y0 = (int)(tyi * BY);
-        const int zb = (int)(tzi * tg.bz);
-        const int ze = min(zb + (int)tg.bz, (int)G.nz);
-
-        // copy slots of this thread: element e = tid + j*THREADS of the
-        // ROWS x LOADW staged region; bit j of inm / ownm = in the grid / in
-        // the tile interior.
-        uint32_t inm = 0, ownm = 0;
-#pragma unroll
-        for (int j = 0; j < PER_THREAD; ++j) {
-            const int e = (int)tid + j * THREADS;
-            const int r = e / LOADW, c = e - r * LOADW;
-            const int gx = x0 - 1 + c, gy = y0 - 1 + r;
-            const bool in = e < ELEMS && gx >= 0 && gx < (int)G.nx && gy >= 0 && gy < (int)G.ny;
-            inm |= (uint32_t)in << j;
-            ownm |= (uint32_t)(in && r >= 1 && r <= BY && c >= 1 && c <= BX) << j;
-        }
-        const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
-        const int gbase = (y0 - 1) * (int)G.nx + (x0 - 1);  // plane offset of staged element 0
-        const float qnan = __int_as_float(0x7fffffff);
-        // Positions outside the grid hold NaN: a NaN candidate never wins a
-        // comparison, so the codes need no domain masks (it only withholds the
-        // certification of vertices on the grid boundary, which is safe).
-#pragma unroll
-        for (int j = 0; j < PER_THREAD; ++j) {
-            const int e = (int)tid + j * THREADS;
-            if (e >= ELEMS || (inm >> j & 1u)) continue;
-            const int r = e / LOADW, c = e - r * LOADW;
-            for (int sl = 0; sl < NSLOT; ++sl) smem[sl * SLOT + r * PW + c + 3] = qnan;
-        }
-        // asynchronous copy of plane p (f over the staged region, fhat over the
-        // owned region) into its ring slot; planes outside the grid become NaN
-        auto issue = [&](int p) {
-            if (p >= 0 && p <= ze) {
-                const int slot = (p - zb + 1) % NSLOT;
-                const bool inside = p < (int)G.nz;
-                const size_t pb = (size_t)p * G.nxy;
-#pragma unroll
-                for (int j = 0; j < PER_THREAD; ++j) {
-                    if (!(inm >> j & 1u)) continue;
-                    const int e = (int)tid + j * THREADS;
-                    const int r = e / LOADW, c = e - r * LOADW;
-                    const uint32_t so = (uint32_t)(slot * SLOT + r * PW + c + 3);
-                    if (!inside) {
-                        smem[so] = qnan;
-                        continue;
-                    }
-                    const size_t gi = pb + (size_t)(gbase + r * (int)G.nx + c);
-                    cp_async4(sbase + 4u * so, P.f + gi);
-                    if (ownm >> j & 1u) cp_async4(sbase + 4u * (so + (uint32_t)PLANE), P.fhat + gi);
-                }
-            } else if (p < 0) {
-                const int slot = (p - zb + 1) % NSLOT;
-#pragma unroll
-                for (int j = 0; j < PER_THREAD; ++j) {
-                    if (!(inm >> j & 1u)) continue;
-                    const int e = (int)tid + j * THREADS;
-                    const int r = e / LOADW, c = e - r * LOADW;
-                    smem[slot * SLOT + r * PW + c + 3] = qnan;
-                }
-            }
-            cp_async_commit();
-        };
-        // owned vertices of plane p: bound check and g = start value
-        auto own = [&](int p) {
-            const int slot = (p - zb + 1) % NSLOT;
-            const size_t pb = (size_t)p * G.nxy;
-#pragma unroll
-            for (int j = 0; j < PER_THREAD; ++j) {
-                if (!(ownm >> j & 1u)) continue;
-                const int e = (int)tid + j * THREADS;
-                const int r = e / LOADW, c = e - r * LOADW;
-                const int so = slot * SLOT + r * PW + c + 3;
-                const float fi = smem[so], fh = smem[so + PLANE];
-                const size_t gi = pb + (size_t)(gbase + r * (int)G.nx + c);
-                const float gs = P.ginit ? P.ginit[gi] : fh;
-                const float L = floor_bound(fi, P.xi), U = ceil_bound(fi, P.xi);
-                bool ok = isfinite(fi) && isfinite(fh) && fh >= L && fh <= U;
-                if (P.ginit) {
-                    ok = ok && isfinite(gs) && gs >= L && gs <= U;
-                    if (__float_as_uint(fh) != __float_as_uint(gs)) red_or(&P.eb[gi >> 5], 1u << (gi & 31u));
-                }
-                bad = bad || !ok;
-                P.g[gi] = gs;
-            }
-        };
-        issue(zb - 1);
-        issue(zb);
-        issue(zb + 1);
-        issue(zb + 2);
-        const int y = y0 + (int)warp, r = (int)warp + 1;
-        const int xl = x0 + 4 * (int)lane;
-        for (int z = zb; z < ze; ++z) {
-            cp_async_wait<1>();  // planes up to z+1 of this thread have landed (z+2 may be in flight)
-            __syncthreads();     // ... of every thread; the slot of z-2 is free
-            issue(z + 3);
-            own(z);
-            if (y >= (int)G.ny) continue;
-            auto plane = [&](int p) { return smem + ((p - zb + 1) % NSLOT) * SLOT; };
-            uint32_t cf[4], cert;
-            tile::codes4_cert(plane(z - 1), plane(z), plane(z + 1), r, lane, P.two_xi, cf, cert);
-            const size_t rowbase = (size_t)z * G.nxy + (size_t)y * G.nx;
-            const size_t i0 = rowbase + xl;
-            if (xl + 3 < (int)G.nx && (i0 & 3) == 0) {
-                *reinterpret_cast<uint32_t *>(P.codes_f + i0) = cf[0] | cf[1] << 8 | cf[2] << 16 | cf[3] << 24;
-            } else {
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    if (xl + e < (int)G.nx) P.codes_f[i0 + e] = (uint8_t)cf[e];
-            }
-            // uncertified bits of this lane's vertices (outside the grid: 0)
-            uint32_t nib = 0;
-#pragma unroll
-            for (int e = 0; e < 4; ++e) nib |= (uint32_t)(xl + e < (int)G.nx && !((cert >> e) & 1u)) << e;
-            const bool words_ok = ((rowbase + (size_t)x0) & 31u) == 0 && x0 + BX <= (int)G.nx;
-            if (words_ok) {
-                // the warp's 128 vertices are 4 whole bitmap words
-                uint32_t w = nib << (4u * (lane & 7u));
-                w |= __shfl_xor_sync(kFull, w, 1);
-                w |= __shfl_xor_sync(kFull, w, 2);
-                w |= __shfl_xor_sync(kFull, w, 4);
-                if ((lane & 7u) == 0) P.ub[(i0) >> 5] = w;
-            } else {
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    if ((nib >> e) & 1u) red_or(&P.ub[(i0 + e) >> 5], 1u << ((i0 + e) & 31u));
-            }
-        }
-        cp_async_wait<0>();
-    }
-    if (bad) atomicOr(&P.ctrl->error, kErrInput);
-}
 
 // ------------------------------------------------------ the persistent kernel
 template <int NDIM>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constant__ const Problem P) {
     extern __shared__ __align__(16) float smem[];
-    const GridDev &G = P.G;
+    const FieldView &F = P.F;
+    const GridDev &G = F.G;
     Ctrl *C = P.ctrl;
     __shared__ uint32_t sm[40];
     const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -347,15 +65,15 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
     if (leader) C->t_start = global_ns();
 
     // ---- sweep 0: codes of f with their certification, g = start, bound check
-    if (NDIM == 3) first_tiled(P, &P.log[0].tile_next, smem);
-    else first_generic<NDIM>(P);
+    if (NDIM == 3) first_tiled(F, &P.log[0].tile_next, smem, &C->error);
+    else first_generic<NDIM>(F, &C->error);
     bool ok = grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
     if (leader) C->t_codes = global_ns();
     // ---- detection of sweep 0: only uncertified vertices can be distorted
     if (ok) {
-        Emitter E{P.dm[1], 0};
+        Emitter E{F.dm[1], 0};
         uint32_t seen = 0;
-        walk_bits<false>(P.ub, nullptr, G, seen, [&](bool has, uint32_t v) { detect_vertex<NDIM>(P, E, has, v); });
+        walk_bits<false>(F.ub, nullptr, G, seen, [&](bool has, uint32_t v) { detect_vertex<NDIM>(F, E, has, v); });
         warp_add(E.distorted, &P.log[0].distorted);
     }
     if (leader) {
@@ -375,7 +93,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
         if (k >= P.max_sweeps) {
             // count the distinct targets this sweep found, for the record
             uint32_t nt = 0;
-            walk_bits<true>(P.tb, nullptr, G, nt, [&](bool, uint32_t) {});
+            walk_bits<true>(F.tb, nullptr, G, nt, [&](bool, uint32_t) {});
             warp_add(nt, &P.log[k].targets);
             if (leader) { C->status = MSZ_ERR_MAX_SWEEPS; C->sweeps = k; C->left = m; }
             ok = grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
@@ -385,28 +103,10 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
             P.dense_min >= 0 && (unsigned long long)m * kDenseFactor >= (unsigned long long)P.dense_min;
         // ---- edit phase of sweep k (Eq. 1), one application per distinct target
         {
-            uint32_t *dnext = P.dm[(k + 1) & 1];
+            uint32_t *dnext = F.dm[(k + 1) & 1];
             uint32_t targets = 0, changed_here = 0;
-            walk_bits<true>(P.tb, nullptr, G, targets, [&](bool has, uint32_t t) {
-                if (!has) return;
-                const float gt = P.g[t];
-                const float L = floor_bound(__ldg(&P.f[t]), P.xi);
-                float h;
-                if (!edit_value(gt, L, P.rule, h)) return;
-                P.g[t] = h;
-                ++changed_here;
-                red_or(&P.eb[t >> 5], 1u << (t & 31u));
-                if (dense_next) return;
-                red_or(&dnext[t >> 5], 1u << (t & 31u));
-                uint32_t x, y, z;
-                coords_of(G, t, x, y, z);
-                constexpr int ns = NDIM == 2 ? 6 : 14;
-#pragma unroll
-                for (int s = 0; s < ns; ++s) {
-                    if (!slot_in_domain(G, s, x, y, z)) continue;
-                    const uint32_t j = (uint32_t)((int64_t)t + G.off[s]);
-                    red_or(&dnext[j >> 5], 1u << (j & 31u));
-                }
+            walk_bits<true>(F.tb, nullptr, G, targets, [&](bool has, uint32_t t) {
+                if (has && apply_target<NDIM>(F, t, dense_next, dnext)) ++changed_here;
             });
             warp_add(targets, &P.log[k].targets);
             warp_add(changed_here, &P.log[k].changed);
@@ -422,8 +122,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
         if (leader) C->edits += changed_k;
         // ---- detection phase of sweep k + 1
         const uint32_t k1 = k + 1;
-        Emitter E{P.dm[(k1 + 1) & 1], 0};
-        uint32_t *dcur = P.dm[k1 & 1];
+        Emitter E{F.dm[(k1 + 1) & 1], 0};
+        uint32_t *dcur = F.dm[k1 & 1];
         uint32_t seen = 0;
         if (dense_next) {
             // whole grid: every uncertified vertex
@@ -433,10 +133,10 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
                 C->dense_sweeps += 1;
             }
             for (uint32_t w = gtid; w < G.words; w += stride) dcur[w] = 0;
-            walk_bits<false>(P.ub, nullptr, G, seen, [&](bool has, uint32_t v) { detect_vertex<NDIM>(P, E, has, v); });
+            walk_bits<false>(F.ub, nullptr, G, seen, [&](bool has, uint32_t v) { detect_vertex<NDIM>(F, E, has, v); });
         } else {
             // the worklist, restricted to uncertified vertices
-            walk_bits<true>(dcur, P.ub, G, seen, [&](bool has, uint32_t v) { detect_vertex<NDIM>(P, E, has, v); });
+            walk_bits<true>(dcur, F.ub, G, seen, [&](bool has, uint32_t v) { detect_vertex<NDIM>(F, E, has, v); });
             warp_add(seen, &P.log[k1].worklist);
         }
         warp_add(E.distorted, &P.log[k1].distorted);
@@ -454,7 +154,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
     const uint32_t per = (W + gridDim.x - 1) / gridDim.x;
     const uint32_t w0 = min(blockIdx.x * per, W), w1 = min(w0 + per, W);
     uint32_t cnt = 0;
-    for (uint32_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) cnt += __popc(P.eb[w]);
+    for (uint32_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) cnt += __popc(F.eb[w]);
     uint32_t tot;
     block_exclusive_scan(cnt, sm, tot);
     if (threadIdx.x == 0) P.bsum[blockIdx.x] = tot;
@@ -471,7 +171,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
     if (leader) C->edit_count = all;
     for (uint32_t r = w0; r < w1; r += blockDim.x) {
         const uint32_t w = r + threadIdx.x;
-        const uint32_t word = w < w1 ? P.eb[w] : 0u;
+        const uint32_t word = w < w1 ? F.eb[w] : 0u;
         uint32_t rt;
         const uint32_t ex = block_exclusive_scan((uint32_t)__popc(word), sm, rt);
         unsigned long long pos = (unsigned long long)prefix + ex;
@@ -482,7 +182,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
             const uint32_t i = w * 32u + b;
             if (pos < P.edit_cap) {
                 P.edit_idx[pos] = i;
-                P.edit_delta[pos] = __fsub_rn(P.g[i], __ldg(&P.fhat[i]));
+                P.edit_delta[pos] = __fsub_rn(F.g[i], __ldg(&F.fhat[i]));
             }
             ++pos;
         }
@@ -602,7 +302,8 @@ extern "C" msz_status msz_correct(const float *d_f, const float *d_fhat, float x
     msz_options o{};
     if (opt) o = *opt;
     if (o.rule != MSZ_RULE_HALVE && o.rule != MSZ_RULE_SNAP) return MSZ_ERR_INVALID_ARG;
-    if (o.max_sweeps > MSZ_MAX_SWEEPS_LIMIT || o.dense_min_items < -1 || o.log_capacity < 0 ||
+    if (o.max_sweeps > MSZ_MAX_SWEEPS_LIMIT || o.dense_min_items < -1 || o.log_capacity < 0 || o.tile_z < 0 ||
+        o.tile_z > 1024 ||
         (o.log_capacity > 0 && !o.h_sweep_log))
         return MSZ_ERR_INVALID_ARG;
     const Layout L = layout_for(G.n);
@@ -614,26 +315,28 @@ extern "C" msz_status msz_correct(const float *d_f, const float *d_fhat, float x
 
     char *ws = (char *)d_workspace;
     Problem P{};
-    P.G = G;
-    P.f = d_f;
-    P.fhat = d_fhat;
-    P.ginit = o.d_g_init;
-    P.g = d_out;
-    P.codes_f = (uint8_t *)(ws + L.codes);
-    P.tb = (uint32_t *)(ws + L.tb);
-    P.dm[0] = (uint32_t *)(ws + L.d0);
-    P.dm[1] = (uint32_t *)(ws + L.d1);
-    P.eb = (uint32_t *)(ws + L.eb);
-    P.ub = (uint32_t *)(ws + L.ub);
+    FieldView &F = P.F;
+    F.G = G;
+    F.f = d_f;
+    F.fhat = d_fhat;
+    F.ginit = o.d_g_init;
+    F.g = d_out;
+    F.codes_f = (uint8_t *)(ws + L.codes);
+    F.tb = (uint32_t *)(ws + L.tb);
+    F.dm[0] = (uint32_t *)(ws + L.d0);
+    F.dm[1] = (uint32_t *)(ws + L.d1);
+    F.eb = (uint32_t *)(ws + L.eb);
+    F.ub = (uint32_t *)(ws + L.ub);
+    F.xi = xi;
+    F.two_xi = 2.0f * xi;  // exact (power-of-two scaling), +inf on overflow
+    F.rule = o.rule;
+    F.tile_z = o.tile_z > 0 ? (uint32_t)o.tile_z : kTileZ;
     P.ctrl = (Ctrl *)(ws + L.ctrl);
     P.log = (SweepRec *)(ws + L.log);
     P.bsum = (uint32_t *)(ws + L.bsum);
     P.edit_idx = d_edit_idx;
     P.edit_delta = d_edit_delta;
     P.edit_cap = (unsigned long long)edit_capacity;
-    P.xi = xi;
-    P.two_xi = 2.0f * xi;  // exact (power-of-two scaling), +inf on overflow
-    P.rule = o.rule;
     P.max_sweeps = o.max_sweeps <= 0 ? (uint32_t)MSZ_MAX_SWEEPS_LIMIT : (uint32_t)o.max_sweeps;
     P.dense_min = o.dense_min_items == 0 ? (long long)(G.n / 16 > 0 ? G.n / 16 : 1) : (long long)o.dense_min_items;
 

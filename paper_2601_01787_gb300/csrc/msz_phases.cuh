@@ -1,0 +1,342 @@
+// msz_phases.cuh -- the phases of the correction loop for one field,
+// shared by the single-field and the batched persistent kernels.
+//
+// A FieldView is one field's slice of the work: its grid, data pointers, and
+// its windows into the workspace bitmaps (targets, worklists, edited,
+// uncertified) and codes, all indexed by the field's own linear index.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "msz.h"
+#include "msz_device.cuh"
+#include "msz_tile.cuh"
+#include "msz_workspace.h"
+
+namespace msz {
+
+constexpr uint32_t kTileZ = 32;  // default planes per tile of the code pass
+constexpr int kDenseWord = 6;    // set bits from which a bitmap word is walked by the whole warp
+
+struct FieldView {
+    GridDev G;
+    const float *f;
+    const float *fhat;
+    const float *ginit;
+    float *g;
+    uint8_t *codes_f;
+    uint32_t *tb;      // targets of the current sweep
+    uint32_t *dm[2];   // worklist of a sweep, by sweep parity
+    uint32_t *eb;      // edited vertices
+    uint32_t *ub;      // uncertified vertices: the only ones that can ever be distorted
+    float xi;
+    float two_xi;      // 2 xi (exact): the certification margin
+    int rule;
+    uint32_t tile_z;   // planes per tile of the code pass
+};
+
+// Where a detection phase records: the targets (P.tb) and the worklist of the
+// next sweep (dnext); distorted vertices are counted per thread and added to
+// the sweep's record when the phase ends.
+struct Emitter {
+    uint32_t *dnext;
+    uint32_t distorted;
+};
+
+// Warp-collective: vertex v (valid lanes) with codes cf in f and cg in g; a
+// distorted vertex marks its targets and, unless the caller marks whole words
+// itself (self_marked), itself for the next worklist.
+__device__ __forceinline__ bool report(const FieldView &P, Emitter &E, bool valid, uint32_t v, uint32_t cf,
+                                       uint32_t cg, bool self_marked = false) {
+    const bool dist = valid && cf != cg;
+    if (!__any_sync(kFull, dist)) return false;
+    if (dist) {
+        uint32_t t0, t1;
+        const int nt = targets_of(P.G, v, (uint8_t)cf, (uint8_t)cg, t0, t1);
+        red_or(&P.tb[t0 >> 5], 1u << (t0 & 31u));
+        if (nt > 1) red_or(&P.tb[t1 >> 5], 1u << (t1 & 31u));
+        if (!self_marked) red_or(&E.dnext[v >> 5], 1u << (v & 31u));
+        E.distorted += 1;
+    }
+    return dist;
+}
+
+// Warp-collective walk over the set bits of a bitmap: each warp takes 32
+// consecutive words (1024 vertices) at a time, grid-stride.  CLEAR zeroes the
+// visited words; `seen` counts their set bits; a non-null filter restricts the
+// calls to the vertices also set there.  fn(valid, v) runs once per round
+// with one vertex per lane.
+template <bool CLEAR, class F>
+__device__ __forceinline__ void walk_bits(uint32_t *bm, const uint32_t *filter, const GridDev &G, uint32_t &seen,
+                                          F &&fn) {
+    const uint32_t lane = lane_id();
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t base = gw * 32u; base < G.words; base += nw * 32u) {
+        const uint32_t wi = base + lane;
+        uint32_t bits = 0;
+        if (wi < G.words) {
+            bits = bm[wi];
+            if (CLEAR && bits) bm[wi] = 0u;
+            seen += (uint32_t)__popc(bits);
+            if (filter && bits) bits &= filter[wi];
+        }
+        // words with many set bits: the whole warp takes one word at a time,
+        // lane l on vertex 32*word + l, so neighbour loads coalesce
+        const bool dense = __popc(bits) >= kDenseWord;
+        uint32_t dm = __ballot_sync(kFull, dense);
+        while (dm) {
+            const int j = __ffs(dm) - 1;
+            dm &= dm - 1u;
+            const uint32_t word = __shfl_sync(kFull, bits, j);
+            fn(((word >> lane) & 1u) != 0u, (base + (uint32_t)j) * 32u + lane);
+        }
+        if (dense) bits = 0u;
+        // the remaining sparse words: each lane walks its own word's bits
+        while (__any_sync(kFull, bits != 0u)) {
+            const bool has = bits != 0u;
+            uint32_t v = 0;
+            if (has) {
+                v = wi * 32u + (uint32_t)(__ffs(bits) - 1);
+                bits &= bits - 1u;
+            }
+            fn(has, v);
+        }
+    }
+}
+
+// Detection of one vertex in the current g (warp-collective).
+template <int NDIM>
+__device__ __forceinline__ void detect_vertex(const FieldView &P, Emitter &E, bool has, uint32_t v) {
+    uint32_t cf = 0, cg = 0;
+    if (has) {
+        uint32_t x, y, z;
+        coords_of(P.G, v, x, y, z);
+        cg = code_global<NDIM>(P.g, P.G, v, x, y, z);
+        cf = __ldg(&P.codes_f[v]);
+    }
+    report(P, E, has, v, cf, cg);
+}
+
+// ------------------------------------------------ generic (2D) codes of f
+template <int NDIM>
+__device__ void first_generic(const FieldView &P, uint32_t *err) {
+    const GridDev &G = P.G;
+    const uint32_t lane = lane_id();
+    const uint32_t stride = gridDim.x * blockDim.x;
+    bool bad = false;
+    for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < G.n; base += stride) {
+        const uint32_t i = base + lane;
+        const bool valid = i < G.n;
+        bool differs = false, uncert = false;
+        if (valid) {
+            uint32_t x, y, z;
+            coords_of(G, i, x, y, z);
+            const float fi = P.f[i], fh = P.fhat[i];
+            const float gs = P.ginit ? P.ginit[i] : fh;
+            const float L = floor_bound(fi, P.xi), U = ceil_bound(fi, P.xi);
+            bad = bad || !(isfinite(fi) && isfinite(fh) && fh >= L && fh <= U);
+            if (P.ginit) {
+                bad = bad || !(isfinite(gs) && gs >= L && gs <= U);
+                differs = __float_as_uint(gs) != __float_as_uint(fh);
+            }
+            bool cert;
+            P.codes_f[i] = code_global_cert<NDIM>(P.f, G, i, x, y, z, P.two_xi, cert);
+            uncert = !cert;
+            P.g[i] = gs;
+        }
+        // base is a multiple of 32: this warp owns whole bitmap words
+        const uint32_t um = __ballot_sync(kFull, uncert);
+        if (lane == 0) P.ub[base >> 5] = um;
+        if (P.ginit) {
+            const uint32_t m = __ballot_sync(kFull, differs);
+            if (lane == 0 && m) P.eb[base >> 5] = m;
+        }
+    }
+    if (bad) atomicOr(err, kErrInput);
+}
+
+// ------------------------------------------------ tiled (3D) codes of f
+// One tile (x0, y0, planes zb .. ze-1) of field P: codes of f with their
+// certification, g = start value, bound check (bad is set on a violation).
+// Block-collective; the caller synchronizes the block before the next tile.
+__device__ __forceinline__ void first_tile(const FieldView &P, int x0, int y0, int zb, int ze, float *smem,
+                                           bool &bad) {
+    using namespace tile;
+    const GridDev &G = P.G;
+    const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+    // copy slots of this thread: element e = tid + j*THREADS of the
+    // ROWS x LOADW staged region; bit j of inm / ownm = in the grid / in
+    // the tile interior.
+    uint32_t inm = 0, ownm = 0;
+#pragma unroll
+    for (int j = 0; j < PER_THREAD; ++j) {
+        const int e = (int)tid + j * THREADS;
+        const int r = e / LOADW, c = e - r * LOADW;
+        const int gx = x0 - 1 + c, gy = y0 - 1 + r;
+        const bool in = e < ELEMS && gx >= 0 && gx < (int)G.nx && gy >= 0 && gy < (int)G.ny;
+        inm |= (uint32_t)in << j;
+        ownm |= (uint32_t)(in && r >= 1 && r <= BY && c >= 1 && c <= BX) << j;
+    }
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
+    const int gbase = (y0 - 1) * (int)G.nx + (x0 - 1);  // plane offset of staged element 0
+    const float qnan = __int_as_float(0x7fffffff);
+    // Positions outside the grid hold NaN: a NaN candidate never wins a
+    // comparison, so the codes need no domain masks (it only withholds the
+    // certification of vertices on the grid boundary, which is safe).
+#pragma unroll
+    for (int j = 0; j < PER_THREAD; ++j) {
+        const int e = (int)tid + j * THREADS;
+        if (e >= ELEMS || (inm >> j & 1u)) continue;
+        const int r = e / LOADW, c = e - r * LOADW;
+        for (int sl = 0; sl < NSLOT; ++sl) smem[sl * SLOT + r * PW + c + 3] = qnan;
+    }
+    // asynchronous copy of plane p (f over the staged region, fhat over the
+    // owned region) into its ring slot; planes outside the grid become NaN
+    auto issue = [&](int p) {
+        if (p >= 0 && p <= ze) {
+            const int slot = (p - zb + 1) % NSLOT;
+            const bool inside = p < (int)G.nz;
+            const size_t pb = (size_t)p * G.nxy;
+#pragma unroll
+            for (int j = 0; j < PER_THREAD; ++j) {
+                if (!(inm >> j & 1u)) continue;
+                const int e = (int)tid + j * THREADS;
+                const int r = e / LOADW, c = e - r * LOADW;
+                const uint32_t so = (uint32_t)(slot * SLOT + r * PW + c + 3);
+                if (!inside) {
+                    smem[so] = qnan;
+                    continue;
+                }
+                const size_t gi = pb + (size_t)(gbase + r * (int)G.nx + c);
+                cp_async4(sbase + 4u * so, P.f + gi);
+                if (ownm >> j & 1u) cp_async4(sbase + 4u * (so + (uint32_t)PLANE), P.fhat + gi);
+            }
+        } else if (p < 0) {
+            const int slot = (p - zb + 1) % NSLOT;
+#pragma unroll
+            for (int j = 0; j < PER_THREAD; ++j) {
+                if (!(inm >> j & 1u)) continue;
+                const int e = (int)tid + j * THREADS;
+                const int r = e / LOADW, c = e - r * LOADW;
+                smem[slot * SLOT + r * PW + c + 3] = qnan;
+            }
+        }
+        cp_async_commit();
+    };
+    // owned vertices of plane p: bound check and g = start value
+    auto own = [&](int p) {
+        const int slot = (p - zb + 1) % NSLOT;
+        const size_t pb = (size_t)p * G.nxy;
+#pragma unroll
+        for (int j = 0; j < PER_THREAD; ++j) {
+            if (!(ownm >> j & 1u)) continue;
+            const int e = (int)tid + j * THREADS;
+            const int r = e / LOADW, c = e - r * LOADW;
+            const int so = slot * SLOT + r * PW + c + 3;
+            const float fi = smem[so], fh = smem[so + PLANE];
+            const size_t gi = pb + (size_t)(gbase + r * (int)G.nx + c);
+            const float gs = P.ginit ? P.ginit[gi] : fh;
+            const float L = floor_bound(fi, P.xi), U = ceil_bound(fi, P.xi);
+            bool ok = isfinite(fi) && isfinite(fh) && fh >= L && fh <= U;
+            if (P.ginit) {
+                ok = ok && isfinite(gs) && gs >= L && gs <= U;
+                if (__float_as_uint(fh) != __float_as_uint(gs)) red_or(&P.eb[gi >> 5], 1u << (gi & 31u));
+            }
+            bad = bad || !ok;
+            P.g[gi] = gs;
+        }
+    };
+    issue(zb - 1);
+    issue(zb);
+    issue(zb + 1);
+    issue(zb + 2);
+    const int y = y0 + (int)warp, r = (int)warp + 1;
+    const int xl = x0 + 4 * (int)lane;
+    for (int z = zb; z < ze; ++z) {
+        cp_async_wait<1>();  // planes up to z+1 of this thread have landed (z+2 may be in flight)
+        __syncthreads();     // ... of every thread; the slot of z-2 is free
+        issue(z + 3);
+        own(z);
+        if (y >= (int)G.ny) continue;
+        auto plane = [&](int p) { return smem + ((p - zb + 1) % NSLOT) * SLOT; };
+        uint32_t cf[4], cert;
+        tile::codes4_cert(plane(z - 1), plane(z), plane(z + 1), r, lane, P.two_xi, cf, cert);
+        const size_t rowbase = (size_t)z * G.nxy + (size_t)y * G.nx;
+        const size_t i0 = rowbase + xl;
+        if (xl + 3 < (int)G.nx && (i0 & 3) == 0) {
+            *reinterpret_cast<uint32_t *>(P.codes_f + i0) = cf[0] | cf[1] << 8 | cf[2] << 16 | cf[3] << 24;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (xl + e < (int)G.nx) P.codes_f[i0 + e] = (uint8_t)cf[e];
+        }
+        // uncertified bits of this lane's vertices (outside the grid: 0)
+        uint32_t nib = 0;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) nib |= (uint32_t)(xl + e < (int)G.nx && !((cert >> e) & 1u)) << e;
+        const bool words_ok = ((rowbase + (size_t)x0) & 31u) == 0 && x0 + BX <= (int)G.nx;
+        if (words_ok) {
+            // the warp's 128 vertices are 4 whole bitmap words
+            uint32_t w = nib << (4u * (lane & 7u));
+            w |= __shfl_xor_sync(kFull, w, 1);
+            w |= __shfl_xor_sync(kFull, w, 2);
+            w |= __shfl_xor_sync(kFull, w, 4);
+            if ((lane & 7u) == 0) P.ub[(i0) >> 5] = w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if ((nib >> e) & 1u) red_or(&P.ub[(i0 + e) >> 5], 1u << ((i0 + e) & 31u));
+        }
+    }
+    cp_async_wait<0>();
+}
+
+// Tiles of one field handed out by an atomic counter (block-collective).
+static __device__ void first_tiled(const FieldView &P, uint32_t *tile_next, float *smem, uint32_t *err) {
+    using namespace tile;
+    const GridDev &G = P.G;
+    const TileGeom tg = tile_geom(G.nx, G.ny, G.nz, P.tile_z);
+    __shared__ uint32_t s_tile;
+    bool bad = false;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_tile = atomicAdd(tile_next, 1u);
+        __syncthreads();
+        const uint32_t t = s_tile;
+        if (t >= tg.count) break;
+        const uint32_t txi = t % tg.tx, tyi = (t / tg.tx) % tg.ty, tzi = t / (tg.tx * tg.ty);
+        const int zb = (int)(tzi * tg.bz);
+        first_tile(P, (int)(txi * BX), (int)(tyi * BY), zb, min(zb + (int)tg.bz, (int)G.nz), smem, bad);
+    }
+    if (bad) atomicOr(err, kErrInput);
+}
+
+// Eq. 1 on target t of field P (once per sweep); a changed target marks the
+// edited bitmap and, unless the next sweep scans densely, its closed
+// neighbourhood in the next worklist.  Returns whether g_t decreased.
+template <int NDIM>
+__device__ __forceinline__ bool apply_target(const FieldView &P, uint32_t t, bool dense_next, uint32_t *dnext) {
+    const float gt = P.g[t];
+    const float L = floor_bound(__ldg(&P.f[t]), P.xi);
+    float h;
+    if (!edit_value(gt, L, P.rule, h)) return false;
+    P.g[t] = h;
+    red_or(&P.eb[t >> 5], 1u << (t & 31u));
+    if (dense_next) return true;
+    red_or(&dnext[t >> 5], 1u << (t & 31u));
+    uint32_t x, y, z;
+    coords_of(P.G, t, x, y, z);
+    constexpr int ns = NDIM == 2 ? 6 : 14;
+#pragma unroll
+    for (int s = 0; s < ns; ++s) {
+        if (!slot_in_domain(P.G, s, x, y, z)) continue;
+        const uint32_t j = (uint32_t)((int64_t)t + P.G.off[s]);
+        red_or(&dnext[j >> 5], 1u << (j & 31u));
+    }
+    return true;
+}
+
+}  // namespace msz

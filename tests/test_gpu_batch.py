@@ -1,0 +1,103 @@
+"""msz_correct_batch: every field of one persistent launch gets exactly what a
+separate correction gives -- checked against the oracle (small uneven batch)
+and against msz_correct plus the GPU verifier (the full 64-field batch)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2601_01787_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    assert torch.cuda.is_available()
+    from paper_2601_01787_gb300 import api as a
+    a.load()
+    return a
+
+
+def _bits(t):
+    a = t.detach().cpu().numpy() if isinstance(t, torch.Tensor) else t
+    return np.ascontiguousarray(a).view(np.uint32)
+
+
+def _small_batch():
+    fields = []
+    for k, (shape, eb) in enumerate([((33, 47, 61), 1e-4), ((20, 20, 20), 1e-3), ((64, 40, 70), 1e-5),
+                                     ((7, 130, 9), 1e-3), ((45, 33, 129), 1e-4)]):
+        fields.append(synth.perlin3d_prequant(shape, seed=900 + k, eb_rel=eb, octaves=4))
+    fields.append(synth.peaks3d((24, 31, 40), seed=950, eb_rel=1e-3, npeaks=12))
+    return fields
+
+
+@pytest.mark.parametrize("dense_min", [-1, 0, 1])
+def test_batch_matches_oracle_per_field(api, dense_min):
+    fields = _small_batch()
+    fs = [torch.from_numpy(fl.f).cuda() for fl in fields]
+    fhs = [torch.from_numpy(fl.fhat).cuda() for fl in fields]
+    res = api.correct_batch(fs, fhs, [fl.xi for fl in fields], dense_min_items=dense_min, log_capacity=4096)
+    assert res.status == api.OK
+    for fl, r in zip(fields, res.fields):
+        ref = oracle.correct(fl.f, fl.fhat, fl.xi, log_capacity=4096)
+        assert r.status == ref.status
+        assert np.array_equal(_bits(r.out), _bits(ref.g))
+        assert r.edit_count == ref.edit_count
+        assert np.array_equal(r.edit_idx.cpu().numpy().view(np.uint32), ref.edit_idx)
+        assert np.array_equal(_bits(r.edit_delta), _bits(ref.edit_delta))
+        st = r.stats
+        assert (st["sweeps"], st["edits"], st["edited"], st["first_distorted"], st["left"]) == \
+            (ref.sweeps, ref.edits, ref.edited, ref.first_distorted, ref.left)
+        assert np.array_equal(r.sweep_log[:, 1:], ref.sweep_log[:, 1:])
+        if dense_min == -1:
+            assert np.array_equal(r.sweep_log[:, 0], ref.sweep_log[:, 0])
+            assert st["examined"] == ref.examined
+
+
+def test_batch_with_done_and_stuck_fields(api):
+    good = synth.perlin3d_prequant((30, 30, 30), seed=960, eb_rel=1e-4)
+    f_st = np.array([[[1.0000001, 1.0]]], dtype=np.float32)
+    xi_st = np.float32(1e8)
+    lo = np.array([oracle.floor_bound(v, xi_st) for v in f_st.reshape(-1)], dtype=np.float32).reshape(f_st.shape)
+    cases = [(good.f, good.fhat, good.xi), (good.f, good.f.copy(), good.xi), (f_st, lo, xi_st)]
+    res = api.correct_batch([torch.from_numpy(a).cuda() for a, _, _ in cases],
+                            [torch.from_numpy(b).cuda() for _, b, _ in cases], [c for _, _, c in cases])
+    assert res.status == api.OK
+    for (f, fh, xi), r in zip(cases, res.fields):
+        ref = oracle.correct(f, fh, xi)
+        assert r.status == ref.status
+        assert np.array_equal(_bits(r.out), _bits(ref.g))
+        assert r.stats["sweeps"] == ref.sweeps and r.stats["left"] == ref.left
+
+
+def test_batch_input_bound_is_reported_per_field(api):
+    a = synth.perlin3d_prequant((16, 16, 16), seed=970, eb_rel=1e-3)
+    b = synth.perlin3d_prequant((16, 17, 18), seed=971, eb_rel=1e-3)
+    bad = b.fhat.copy()
+    bad[3, 4, 5] = b.f[3, 4, 5] + np.float32(4) * b.xi
+    res = api.correct_batch([torch.from_numpy(a.f).cuda(), torch.from_numpy(b.f).cuda()],
+                            [torch.from_numpy(a.fhat).cuda(), torch.from_numpy(bad).cuda()], [a.xi, b.xi])
+    assert res.status == api.ERR_INPUT_BOUND
+    assert res.fields[1].status == api.ERR_INPUT_BOUND
+
+
+def test_full_uneven_batch_matches_single_corrections(api):
+    """The 64-field batch (axes uniform in 64..384, eb_rel in {1e-3,1e-4,1e-5},
+    prequantized Perlin): each field equals its own msz_correct call, which the
+    parity tests tie to the oracle, and verifies on the GPU."""
+    fields = synth.batch(64)
+    fs = [torch.from_numpy(fl.f).cuda() for fl in fields]
+    fhs = [torch.from_numpy(fl.fhat).cuda() for fl in fields]
+    res = api.correct_batch(fs, fhs, [fl.xi for fl in fields], edit_capacities=[fl.n // 4 for fl in fields])
+    assert res.status == api.OK
+    for fl, f, fh, r in zip(fields, fs, fhs, res.fields):
+        one = api.correct(f, fh, fl.xi, edit_capacity=fl.n // 4)
+        assert r.status == one.status == api.OK
+        assert torch.equal(r.out.view(torch.int32), one.out.view(torch.int32))
+        assert torch.equal(r.edit_idx, one.edit_idx)
+        for key in ("sweeps", "edits", "edited", "first_distorted"):
+            assert r.stats[key] == one.stats[key], key
+        v = api.verify(f, r.out)
+        assert v["codes_equal"] and v["wrong_labels"] == 0
