@@ -204,8 +204,8 @@ typedef struct {
  * cap (max_sweeps <= 0: MSZ_BATCH_MAX_SWEEPS); 0 for an invalid batch. */
 size_t msz_batch_workspace_size(int32_t n, const msz_field *fields, int64_t max_sweeps);
 
-/* Batched form of msz_correct (the benchmark spec's batching direction; the paper has
- * no batched form): n 3D fields of any sizes, each with its own xi, corrected
+/* Batched form of msz_correct (an extension: the paper corrects one field per
+ * run): n 3D fields of any sizes, each with its own xi, corrected
  * by one cooperative persistent launch.  The fields share one tile queue for
  * the code pass and one set of sweeps; each field stops taking part when it is
  * done, stuck or capped, and every field gets exactly the g, edit list,
@@ -218,6 +218,73 @@ size_t msz_batch_workspace_size(int32_t n, const msz_field *fields, int64_t max_
  * Synchronizes `stream`. */
 msz_status msz_correct_batch(int32_t n, msz_field *fields, const msz_options *opt, int64_t *h_sweep_log,
                              int64_t log_capacity, void *d_workspace, size_t workspace_bytes, msz_stream_t stream);
+
+/* ---- Learned initial-edit proposal (an extension: the paper has no learned
+ * component).  A 4-layer 3D conv net (3x3x3 cross-correlations, zero
+ * padding, channels 8 -> 32 -> 32 -> 32 -> 16, ReLU between) classifies each
+ * vertex by k = 0..15, the number of HALVE edits the plain loop applies to it
+ * (15: fifteen or more).  The start g0 = fhat edited k times by that rule goes
+ * to msz_correct as d_g_init and the exact loop finishes from there, so every
+ * invariant still holds; a right class reproduces the plain loop's value bit
+ * for bit.  Tensors: channels-last BF16 ([z][y][x][C], C = 16 or 32; uint16_t
+ * storage), 16-byte aligned; 3D grids only; weights w[o][cout][cin] FP32 with
+ * kernel offset o = (dz+1)*9 + (dy+1)*3 + (dx+1) applied to input voxel
+ * (x+dx, y+dy, z+dz).  All calls are asynchronous on `stream`. */
+
+/* The 8 input channels (BF16, padded with zeros to 16): (fhat - f)/xi, the
+ * forward differences of f along x, y, z divided by 4 xi (clamped to [-1, 1]),
+ * f's maximum and minimum flags, and whether fhat's ascending / descending
+ * code differs from f's.  d_codes_f / d_codes_fhat: msz_directions of f / fhat. */
+msz_status msz_learned_features(const float *d_f, const float *d_fhat, float xi, msz_grid grid,
+                                const uint8_t *d_codes_f, const uint8_t *d_codes_fhat, uint16_t *d_x,
+                                msz_stream_t stream);
+
+/* BF16 weight image of a conv with cin input and cout output channels (16 or
+ * 32 each) from FP32 weights d_w[27][cout_real][cin_real], zero-padded;
+ * mirror != 0: the image of the backward-data conv (input = gradient of the
+ * forward output, weights of the mirrored offset, channels swapped).  d_img:
+ * msz_learned_weight_image_size(cin, cout) bytes. */
+size_t msz_learned_weight_image_size(int32_t cin, int32_t cout);
+msz_status msz_learned_weight_image(const float *d_w, int32_t cout_real, int32_t cin_real, int32_t cin,
+                                    int32_t cout, int32_t mirror, uint16_t *d_img, msz_stream_t stream);
+
+/* One 3x3x3 conv layer on tcgen05 tensor cores (BF16 x BF16 -> FP32 in TMEM).
+ * mode 0 (ReLU):  d_out_bf16 = max(0, conv(d_x) + d_bias)       cin 16|32, cout 32
+ * mode 1 (head):  k = argmax_c (conv(d_x)[c] + d_bias[c]) (lowest c on ties);
+ *                 a nonzero k becomes clamp(k + shift, 1, 15); d_out_f32 (may
+ *                 be NULL) = k; if d_g0: d_g0 = fhat edited k times by HALVE
+ *                 with floor L of d_f, xi                         cin 32, cout 16
+ * mode 2 (dgrad): d_out_bf16 = conv(d_x) where d_mask > 0, else 0 (the input
+ *                 gradient through a ReLU; d_x = output gradient)  cin 16|32, cout 32
+ * mode 3 (raw):   d_out_f32 = conv(d_x) (+ d_bias if not NULL)    any of the above
+ * d_err: a device word that gets bit 0 when a bounded wait ran out. */
+msz_status msz_learned_conv(const uint16_t *d_x, int32_t cin, int32_t cout, int32_t mode, msz_grid grid,
+                            const uint16_t *d_img, const float *d_bias, uint16_t *d_out_bf16, float *d_out_f32,
+                            const uint16_t *d_mask, const float *d_f, const float *d_fhat, float xi, int32_t shift,
+                            float *d_g0, uint32_t *d_err, msz_stream_t stream);
+
+/* Training loss head: d_z holds the 16 head logits per vertex (the raw head
+ * conv with its bias), d_target the class k per vertex (as float).
+ * *d_loss_sum += sum of the softmax cross-entropies logsumexp(z) - z_k
+ * (double); d_dz16 = scale (softmax(z) - onehot(k)), 16 BF16 per vertex. */
+msz_status msz_learned_head_grad(const float *d_z, const float *d_target, int64_t n, float scale,
+                                 uint16_t *d_dz16, double *d_loss_sum, msz_stream_t stream);
+
+/* Training classes: d_target[i] = the number of HALVE edits (capped at 15)
+ * that take fhat_i to g_i, g the corrected field of msz_correct from fhat. */
+msz_status msz_learned_target(const float *d_f, const float *d_fhat, const float *d_g, float xi, int64_t n,
+                              float *d_target, msz_stream_t stream);
+
+/* Weight and bias gradients of one layer (FP32, accumulated into d_dw
+ * [27][cout_real][cin_real] and d_db[cout_real]): dw[o][co][ci] += sum_v
+ * dz[v][co] x[v + d_o][ci].  d_x: the layer's input (cin channels), d_dz: the
+ * gradient of its pre-activation output (cout channels). */
+msz_status msz_learned_wgrad(const uint16_t *d_x, int32_t cin, const uint16_t *d_dz, int32_t cout, msz_grid grid,
+                             int32_t cin_real, int32_t cout_real, float *d_dw, float *d_db, msz_stream_t stream);
+
+/* One Adam step on n FP32 parameters (bias-corrected; step >= 1). */
+msz_status msz_learned_adam(float *d_p, const float *d_g, float *d_m, float *d_v, int64_t n, float lr, float beta1,
+                            float beta2, float eps, int64_t step, msz_stream_t stream);
 
 /* msz_correct for callers that cannot allocate device memory.  (The paper has
  * no counterpart: this entry point exists for how callers use the library.)
