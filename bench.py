@@ -34,7 +34,7 @@ import numpy as np  # noqa: E402
 SHAPE = (512, 512, 512)  # (nz, ny, nx); --shape overrides (profiling captures only)
 SEED = 2
 EB_REL = 1e-4
-METRIC = "Gvertices/s to zero-mismatch correction at 512^3 (plain)"
+METRIC = "Gvertices/s to zero-mismatch correction at 512\u00b3 (plain vs learned); HBM GB/s"
 UNIT = "Gvertices/s"
 def workload_name():
     nz, ny, nx = SHAPE
@@ -224,7 +224,7 @@ def run_ours(args, ws, rank, local):
         try:
             with open(tfile) as fh_:
                 tj = json.load(fh_)
-            if tj.get("source_hash") == api_source_hash():
+            if tj.get("unit_hash") == api_source_hash():
                 traffic = tj.get("traffic_bytes")
         except Exception:
             traffic = None
@@ -276,6 +276,11 @@ def run_ours(args, ws, rank, local):
         api._ws_cache.clear()
         torch.cuda.empty_cache()
         line["batch"] = run_batch(dev, stream)
+    if rank == 0 and not args.no_learned:
+        api._ws_cache.clear()
+        torch.cuda.empty_cache()
+        line["learned"] = run_learned(dev, stream)
+        torch.cuda.empty_cache()
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(fl, args.cpu_slab)
     if rank == 0:
@@ -333,9 +338,70 @@ def run_batch(dev, stream, reps: int = 5) -> dict:
             "tile_z": sorted(set(tz)), "launches": 1}
 
 
+def run_learned(dev, stream, reps: int = 3) -> dict:
+    """The learned proposal against the plain loop on a 512^3 Gaussian-peak
+    field (5000 peaks: the peak density of the 1024 x 1024 x 512 workload;
+    seed 7; relative bound 1e-4; uniform noise): wall time on the device from
+    f and fhat resident to a corrected field and its edit list, sweeps, and
+    the verification of both results.  The network is trained first by its
+    recipe (200 seeded 128^3 triples) unless this build already has it."""
+    import torch
+
+    from paper_2601_01787_gb300 import api, learned, synth
+    net, info = learned.default_net(dev)
+    fl = synth.peaks3d((512, 512, 512), seed=7, eb_rel=1e-4, npeaks=5000)
+    f = torch.from_numpy(fl.f).to(dev)
+    fh = torch.from_numpy(fl.fhat).to(dev)
+    cap = fl.n // 2
+    out = torch.empty_like(f)
+    eidx = torch.empty(cap, dtype=torch.int32, device=dev)
+    edel = torch.empty(cap, dtype=torch.float32, device=dev)
+    kw = dict(out=out, edit_idx=eidx, edit_delta=edel, edit_capacity=cap, stream=stream)
+
+    def timed(fn):
+        best, res = None, None
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            res = fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b)
+            best = t if best is None else min(best, t)
+        return best, res
+
+    timed(lambda: api.correct(f, fh, fl.xi, **kw))
+    t_plain, rp = timed(lambda: api.correct(f, fh, fl.xi, **kw))
+    assert rp.status == api.OK, api.status_str(rp.status)
+    vp = api.verify(f, out)
+    timed(lambda: learned.correct_learned(f, fh, fl.xi, net, **kw))
+    t_learned, rl = timed(lambda: learned.correct_learned(f, fh, fl.xi, net, **kw))
+    assert rl.result.status == api.OK, api.status_str(rl.result.status)
+    vl = api.verify(f, out)
+    n = fl.n
+    return {"workload": "peaks3d_512x512x512: 5000 Gaussian peaks on Poisson(5) counts, seed 7, eb_rel 1e-4, "
+                        "fhat = f + U[-xi, xi]",
+            "n_vertices": n, "unit": UNIT, "shift": learned.SHIFT,
+            "plain": {"ms": round(t_plain, 4), "value": round(n / (t_plain * 1e-3) / 1e9, 4),
+                      "sweeps": rp.stats["sweeps"], "first_distorted": rp.stats["first_distorted"],
+                      "edited": rp.edit_count, "kernel_ms": round(rp.stats["kernel_ns"] / 1e6, 4),
+                      "verified": bool(vp["codes_equal"] and vp["wrong_labels"] == 0)},
+            "learned": {"ms": round(t_learned, 4), "value": round(n / (t_learned * 1e-3) / 1e9, 4),
+                        "propose_ms": round(rl.propose_ms, 4),
+                        "loop_kernel_ms": round(rl.from_g0.stats["kernel_ns"] / 1e6, 4),
+                        "sweeps": rl.from_g0.stats["sweeps"], "first_distorted": rl.from_g0.stats["first_distorted"],
+                        "edited": rl.result.edit_count, "fallback_to_plain": rl.fallback,
+                        "verified": bool(vl["codes_equal"] and vl["wrong_labels"] == 0)},
+            "training": {"recipe": learned.RECIPE | {"shape": list(learned.RECIPE["shape"])},
+                         "cached": info["cached"], "train_s": None if info.get("train_s") is None else
+                         round(info["train_s"], 2), "final_loss": info.get("final_loss")}}
+
+
 def api_source_hash() -> str:
+    """Identity of the correction kernel's sources and flags (the traffic
+    record applies only while it is unchanged)."""
     from paper_2601_01787_gb300 import _build
-    return _build.source_hash()
+    return _build.unit_hash("msz_correct.cu")
 
 
 # ------------------------------------------------------------ CPU oracle
@@ -393,6 +459,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-field batch measurement")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal comparison")
     ap.add_argument("--cpu-slab", type=int, default=128, help="z-planes of the CPU-baseline sample")
     ap.add_argument("--ref-slab", type=int, default=24, help="z-planes per reference-arm step")
     ap.add_argument("--shape", default=None, help="nz,ny,nx of a smaller field (profiling captures only)")

@@ -221,7 +221,7 @@ msz_status msz_correct_batch(int32_t n, msz_field *fields, const msz_options *op
 
 /* ---- Learned initial-edit proposal (an extension: the paper has no learned
  * component).  A 4-layer 3D conv net (3x3x3 cross-correlations, zero
- * padding, channels 8 -> 32 -> 32 -> 32 -> 16, ReLU between) classifies each
+ * padding, channels 16 -> 32 -> 32 -> 32 -> 16, ReLU between) classifies each
  * vertex by k = 0..15, the number of HALVE edits the plain loop applies to it
  * (15: fifteen or more).  The start g0 = fhat edited k times by that rule goes
  * to msz_correct as d_g_init and the exact loop finishes from there, so every
@@ -231,10 +231,15 @@ msz_status msz_correct_batch(int32_t n, msz_field *fields, const msz_options *op
  * kernel offset o = (dz+1)*9 + (dy+1)*3 + (dx+1) applied to input voxel
  * (x+dx, y+dy, z+dz).  All calls are asynchronous on `stream`. */
 
-/* The 8 input channels (BF16, padded with zeros to 16): (fhat - f)/xi, the
- * forward differences of f along x, y, z divided by 4 xi (clamped to [-1, 1]),
- * f's maximum and minimum flags, and whether fhat's ascending / descending
- * code differs from f's.  d_codes_f / d_codes_fhat: msz_directions of f / fhat. */
+/* The 16 input channels (BF16) per vertex: 0 (fhat - f)/xi; 1..3 the forward
+ * differences of f along x, y, z divided by 4 xi; 4, 5 f has a maximum / a
+ * minimum here; 6, 7 fhat's ascending / descending code differs from f's;
+ * 8, 9 the vertex is the target of an ascending / descending mismatch in the
+ * first sweep (the msz_correct target rule with g = fhat); 10, 11 fhat has a
+ * maximum / a minimum here; 12..14 the forward differences of fhat divided
+ * by 4 xi; 15 the fraction of the 14 neighbours whose f equals this vertex's.
+ * Differences are clamped to [-1, 1] and read as 0 past the grid's end.
+ * d_codes_f / d_codes_fhat: msz_directions of f / fhat; 3D grids only. */
 msz_status msz_learned_features(const float *d_f, const float *d_fhat, float xi, msz_grid grid,
                                 const uint8_t *d_codes_f, const uint8_t *d_codes_fhat, uint16_t *d_x,
                                 msz_stream_t stream);

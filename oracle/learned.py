@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY: only tests/ and bench.py's CPU arms call it.
 
 The network of the learned initial-edit proposal: four 3x3x3
-cross-correlations with zero padding (channels 8 -> 32 -> 32 -> 32 -> 16),
+cross-correlations with zero padding (channels 16 -> 32 -> 32 -> 32 -> 16),
 ReLU between; the 16 outputs are the logits of the edit-count classes
 k = 0..15, trained with softmax cross-entropy.  Tensors are channels-last
 ([z][y][x][C]); weights w[o][cout][cin] with kernel offset
@@ -20,7 +20,7 @@ from __future__ import annotations
 import numpy as np
 
 OFFSETS = [(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
-CHANNELS = (8, 32, 32, 32, 16)
+CHANNELS = (16, 32, 32, 32, 16)
 CLASSES = 16
 
 

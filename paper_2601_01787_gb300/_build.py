@@ -59,6 +59,23 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def unit_hash(unit: str) -> str:
+    """Hash of one translation unit, every header it can include and its
+    flags: identifies the kernels of that unit a profile was taken of (a
+    change to another unit leaves it unchanged)."""
+    h = hashlib.sha256()
+    names = [unit] + sorted(n for n in os.listdir(CSRC) if n.endswith((".cuh", ".h"))) + ["../../include/msz.h"]
+    for name in names:
+        p = os.path.normpath(os.path.join(CSRC, name))
+        if os.path.isfile(p):
+            h.update(name.encode())
+            with open(p, "rb") as fh:
+                h.update(fh.read())
+    flags = [u for u in UNITS if (u[0] if isinstance(u, (tuple, list)) else u) == unit]
+    h.update(repr(([c for c in COMMON if not c.startswith("/")], flags)).encode())
+    return h.hexdigest()[:16]
+
+
 def _stamp() -> str:
     return source_hash() + "-" + os.uname().machine
 

@@ -3,12 +3,12 @@
 // to it), trained and run on sm_103a.  The exact correction loop always
 // finishes from the proposed start, so results stay exact.
 //
-//   features   8 channels per vertex (BF16, padded to 16): (fhat - f)/xi, the
-//              three forward differences of f / (4 xi) (clamped to +-1), f's
-//              maximum and minimum flags, and whether fhat's ascending /
-//              descending code differs from f's;
+//   features   16 channels per vertex (BF16): (fhat - f)/xi, the forward
+//              differences of f and of fhat / (4 xi) (clamped to +-1), the
+//              extremum flags of f and fhat, the first sweep's mismatch and
+//              target flags, and the fraction of tied neighbours in f;
 //   conv3d     4 layers of 3x3x3 cross-correlations with zero padding,
-//              16(8)->32->32->32->16 channels, ReLU between, as implicit
+//              16->32->32->32->16 channels, ReLU between, as implicit
 //              GEMMs on tcgen05 (BF16 operands in shared memory, FP32
 //              accumulators in TMEM);
 //   head       16 logits per vertex, one per class k = 0..15: the number of
@@ -256,20 +256,23 @@ __global__ void __launch_bounds__(kConvThreads, 1)
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t sbase = sstg + st * kStageBytes;
+                    // descriptors of offset 0 of this stage and slab pair; every MMA
+                    // adds a compile-time start offset (in 16-byte units: the start
+                    // field stays below 2^14 for addresses under 256 KB)
+                    const uint64_t a0 = sdesc(sstg + st * kStageBytes, kSlabBytes, 128);
+                    const uint64_t b0 = sdesc(swsm + 2 * sp * COUT * 16, COUT * 16, 128);
+                    const uint32_t d0 = tmem + buf * 4 * COUT;
+                    const uint32_t first = sp > 0 ? 1u : 0u;
+#pragma unroll
                     for (int r = 0; r < 4; ++r) {
-                        const int iz = r >> 1, iy = r & 1;
-                        const uint32_t d = tmem + (buf * 4 + r) * COUT;
-                        for (int dz = -1; dz <= 1; ++dz)
-                            for (int dy = -1; dy <= 1; ++dy)
-                                for (int dx = -1; dx <= 1; ++dx) {
-                                    const int o = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
-                                    const int L = (iz + 1 + dz) * 4 + (iy + 1 + dy);
-                                    const uint32_t a = sbase + L * kLineBytes + (1 + dx) * 16;
-                                    const uint32_t b = swsm + ((o * S::KG + 2 * sp) * COUT) * 16;
-                                    mma_bf16(d, sdesc(a, kSlabBytes, 128), sdesc(b, COUT * 16, 128), S::IDESC,
-                                             (sp > 0 || o > 0) ? 1u : 0u);
-                                }
+#pragma unroll
+                        for (int o = 0; o < 27; ++o) {
+                            const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+                            const int L = ((r >> 1) + 1 + dz) * 4 + ((r & 1) + 1 + dy);
+                            const uint64_t a = a0 + (uint64_t)((L * kLineBytes + (1 + dx) * 16) >> 4);
+                            const uint64_t b = b0 + (uint64_t)((o * S::KG * COUT * 16) >> 4);
+                            mma_bf16(d0 + r * COUT, a, b, S::IDESC, o > 0 ? 1u : first);
+                        }
                     }
                     mma_commit(smem_u32(&bar_free[st]));
                     issued = true;
@@ -343,9 +346,16 @@ __global__ void __launch_bounds__(kConvThreads, 1)
                         P.g0[v] = g;
                     }
                 } else {
+                    float4 *dst = reinterpret_cast<float4 *>(P.out_f32 + v * COUT);
 #pragma unroll
-                    for (int c = 0; c < COUT; ++c)
-                        P.out_f32[v * COUT + c] = __uint_as_float(acc[c]) + (P.bias ? P.bias[c] : 0.0f);
+                    for (int c = 0; c < COUT; c += 4) {
+                        float4 o4;
+                        o4.x = __uint_as_float(acc[c]) + (P.bias ? P.bias[c] : 0.0f);
+                        o4.y = __uint_as_float(acc[c + 1]) + (P.bias ? P.bias[c + 1] : 0.0f);
+                        o4.z = __uint_as_float(acc[c + 2]) + (P.bias ? P.bias[c + 2] : 0.0f);
+                        o4.w = __uint_as_float(acc[c + 3]) + (P.bias ? P.bias[c + 3] : 0.0f);
+                        dst[c / 4] = o4;
+                    }
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -362,32 +372,63 @@ __global__ void __launch_bounds__(kConvThreads, 1)
 }
 
 // ------------------------------------------------------------- features
-// 8 channels per vertex (BF16, channels 8..15 zero).  codes_f / codes_h: the
-// steepest-neighbour codes of f and fhat.
+// 16 channels per vertex (BF16).  codes_f / codes_h: the steepest-neighbour
+// codes of f and fhat (3D slots).
+//   0      (fhat - f) / xi                    clamped to [-1, 1]
+//   1..3   forward differences of f / (4 xi)  along x, y, z, clamped to [-1, 1]
+//   4, 5   f has a maximum / a minimum here
+//   6, 7   fhat's ascending / descending code differs from f's
+//   8, 9   the vertex is the target of an ascending / descending mismatch in
+//          the first sweep (the correction's target rule applied to g = fhat)
+//   10, 11 fhat has a maximum / a minimum here
+//   12..14 forward differences of fhat / (4 xi), clamped to [-1, 1]
+//   15     the fraction of the 14 neighbours whose f value equals this one's
 __global__ void __launch_bounds__(256) k_features(const float *f, const float *fhat, const uint8_t *codes_f,
-                                                 const uint8_t *codes_h, uint32_t nx, uint32_t ny, uint32_t nz,
-                                                 float xi, uint16_t *out) {
-    const size_t n = (size_t)nx * ny * nz;
+                                                 const uint8_t *codes_h, const GridDev G, float xi, uint16_t *out) {
+    const size_t n = (size_t)G.n;
+    const uint32_t nx = G.nx, ny = G.ny, nz = G.nz;
     const float inv = xi > 0.0f ? 1.0f / xi : 0.0f;
     const float inv4 = xi > 0.0f ? 0.25f / xi : 0.0f;
     for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (size_t)gridDim.x * blockDim.x) {
-        const uint32_t x = (uint32_t)(v % nx), y = (uint32_t)((v / nx) % ny), z = (uint32_t)(v / ((size_t)nx * ny));
-        const float fv = f[v];
-        float ch[8];
-        ch[0] = fminf(fmaxf((fhat[v] - fv) * inv, -1.0f), 1.0f);
+        uint32_t x, y, z;
+        coords_of(G, (uint32_t)v, x, y, z);
+        const float fv = f[v], hv = fhat[v];
+        float ch[16];
+        ch[0] = fminf(fmaxf((hv - fv) * inv, -1.0f), 1.0f);
         ch[1] = x + 1 < nx ? fminf(fmaxf((f[v + 1] - fv) * inv4, -1.0f), 1.0f) : 0.0f;
         ch[2] = y + 1 < ny ? fminf(fmaxf((f[v + nx] - fv) * inv4, -1.0f), 1.0f) : 0.0f;
-        ch[3] = z + 1 < nz ? fminf(fmaxf((f[v + (size_t)nx * ny] - fv) * inv4, -1.0f), 1.0f) : 0.0f;
-        const uint8_t cf = codes_f[v], ch_ = codes_h[v];
+        ch[3] = z + 1 < nz ? fminf(fmaxf((f[v + (size_t)G.nxy] - fv) * inv4, -1.0f), 1.0f) : 0.0f;
+        const uint32_t cf = codes_f[v], cg = codes_h[v];
         ch[4] = (cf & 15u) == kSelf ? 1.0f : 0.0f;
         ch[5] = (cf >> 4) == kSelf ? 1.0f : 0.0f;
-        ch[6] = (cf & 15u) != (ch_ & 15u) ? 1.0f : 0.0f;
-        ch[7] = (cf >> 4) != (ch_ >> 4) ? 1.0f : 0.0f;
+        ch[6] = (cf & 15u) != (cg & 15u) ? 1.0f : 0.0f;
+        ch[7] = (cf >> 4) != (cg >> 4) ? 1.0f : 0.0f;
+        // a mismatched vertex j targets itself (ascending: when fhat makes it a
+        // maximum; descending: when f makes it a minimum), else its steepest
+        // neighbour (ascending: in fhat; descending: in f)
+        bool at = (cf & 15u) != (cg & 15u) && (cg & 15u) == kSelf;
+        bool dt = (cf >> 4) != (cg >> 4) && (cf >> 4) == kSelf;
+        int ties = 0;
+        for (int sl = 0; sl < 14; ++sl) {
+            if (!slot_in_domain(G, sl, x, y, z)) continue;
+            const size_t j = (size_t)((int64_t)v + G.off[sl]);
+            const uint32_t back = (uint32_t)(sl < 7 ? sl + 7 : sl - 7);  // slot of v seen from j
+            const uint32_t jf = codes_f[j], jg = codes_h[j];
+            at = at || ((jf & 15u) != (jg & 15u) && (jg & 15u) == back);
+            dt = dt || ((jf >> 4) != (jg >> 4) && (jf >> 4) == back);
+            ties += f[j] == fv ? 1 : 0;
+        }
+        ch[8] = at ? 1.0f : 0.0f;
+        ch[9] = dt ? 1.0f : 0.0f;
+        ch[10] = (cg & 15u) == kSelf ? 1.0f : 0.0f;
+        ch[11] = (cg >> 4) == kSelf ? 1.0f : 0.0f;
+        ch[12] = x + 1 < nx ? fminf(fmaxf((fhat[v + 1] - hv) * inv4, -1.0f), 1.0f) : 0.0f;
+        ch[13] = y + 1 < ny ? fminf(fmaxf((fhat[v + nx] - hv) * inv4, -1.0f), 1.0f) : 0.0f;
+        ch[14] = z + 1 < nz ? fminf(fmaxf((fhat[v + (size_t)G.nxy] - hv) * inv4, -1.0f), 1.0f) : 0.0f;
+        ch[15] = (float)ties / 14.0f;
         uint32_t p[8];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) p[c] = (uint32_t)f_to_bf16(ch[2 * c]) | ((uint32_t)f_to_bf16(ch[2 * c + 1]) << 16);
-#pragma unroll
-        for (int c = 4; c < 8; ++c) p[c] = 0;
+        for (int c = 0; c < 8; ++c) p[c] = (uint32_t)f_to_bf16(ch[2 * c]) | ((uint32_t)f_to_bf16(ch[2 * c + 1]) << 16);
         uint4 *dst = reinterpret_cast<uint4 *>(out + v * 16);
         dst[0] = make_uint4(p[0], p[1], p[2], p[3]);
         dst[1] = make_uint4(p[4], p[5], p[6], p[7]);
@@ -665,8 +706,8 @@ extern "C" msz_status msz_learned_features(const float *d_f, const float *d_fhat
     if (st != MSZ_OK) return st;
     DeviceInfo dev;
     if ((st = current_device(dev)) != MSZ_OK) return st;
-    k_features<<<dev.sms * 8, 256, 0, (cudaStream_t)stream>>>(d_f, d_fhat, d_codes_f, d_codes_fhat, G.nx, G.ny, G.nz,
-                                                               xi, d_x);
+    if (grid.ndim != 3) return MSZ_ERR_INVALID_ARG;
+    k_features<<<dev.sms * 8, 256, 0, (cudaStream_t)stream>>>(d_f, d_fhat, d_codes_f, d_codes_fhat, G, xi, d_x);
     return cudaGetLastError() == cudaSuccess ? MSZ_OK : MSZ_ERR_CUDA;
 }
 

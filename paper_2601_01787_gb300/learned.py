@@ -1,6 +1,6 @@
 """Learned initial-edit proposal: binding, network, training and inference.
 
-A 4-layer 3D conv net (3x3x3 kernels, zero padding, 8 -> 32 -> 32 -> 32 -> 16
+A 4-layer 3D conv net (3x3x3 kernels, zero padding, 16 -> 32 -> 32 -> 32 -> 16
 channels, ReLU between) classifies each vertex by k = 0..15, the number of
 HALVE edits the plain correction loop applies to it (15: fifteen or more).
 The start g0 = fhat edited k times by that same rule goes to msz_correct as
@@ -30,10 +30,11 @@ from . import api
 
 # (cin_real, cout_real, cin, cout): real channel counts and the padded ones the
 # conv kernels run with
-LAYERS = ((8, 32, 16, 32), (32, 32, 32, 32), (32, 32, 32, 32), (32, 16, 32, 16))
+LAYERS = ((16, 32, 16, 32), (32, 32, 32, 32), (32, 32, 32, 32), (32, 16, 32, 16))
 MODE_RELU, MODE_HEAD, MODE_DGRAD, MODE_RAW = 0, 1, 2, 3
-FEATURES = 16  # 8 real channels, padded
+FEATURES = 16  # input channels per vertex
 CLASSES = 16   # edit-count classes of the head
+SHIFT = 2      # added to nonzero classes at inference: a slight overshoot settles distortions sooner
 _typed = False
 
 
@@ -270,7 +271,7 @@ class ProposalNet:
         return loss
 
     # -- inference
-    def propose(self, f: torch.Tensor, fhat: torch.Tensor, xi: float, shift: int = 0, out=None, k_out=None,
+    def propose(self, f: torch.Tensor, fhat: torch.Tensor, xi: float, shift: int = SHIFT, out=None, k_out=None,
                 stream=None) -> torch.Tensor:
         """The proposed start g0 (FP32, shape of f) for msz_correct's g_init;
         k_out (optional, FP32 [N]) receives the class used per vertex."""
@@ -356,6 +357,51 @@ def train(net: ProposalNet, data: list[Sample], epochs: int = 4, lr: float = 1e-
     return log
 
 
+# recipe of the default network: 200 seeded 128^3 Gaussian-peak fields (the
+# peak density of the 1024 x 1024 x 512 workload), relative bound 1e-4, uniform
+# noise, the plain loop's classes as targets
+RECIPE = {"count": 200, "shape": (128, 128, 128), "eb_rel": 1e-4, "seed0": 5000, "epochs": 12, "lr": 2e-3,
+          "init_seed": 1, "order_seed": 0}
+
+
+def _cache_path(recipe: dict) -> str:
+    import hashlib
+    import json
+    import os
+
+    from . import _build
+    key = hashlib.sha256((_build.source_hash() + json.dumps(recipe, sort_keys=True)).encode()).hexdigest()[:16]
+    return os.path.join(os.path.dirname(_build.LIB), f"proposal_{key}.npz")
+
+
+def default_net(device=None, train_if_missing: bool = True, recipe: dict | None = None, verbose: bool = False):
+    """The network trained by `recipe` (default RECIPE) with this build's
+    kernels, cached next to the library; returns (net, info)."""
+    import os
+    recipe = dict(RECIPE if recipe is None else recipe)
+    path = _cache_path(recipe)
+    if os.path.exists(path):
+        net = ProposalNet.from_file(path, device=device)
+        with np.load(path) as z:
+            info = {"cached": True, "train_s": float(z["train_s"]) if "train_s" in z.files else None,
+                    "final_loss": float(z["final_loss"]) if "final_loss" in z.files else None}
+        return net, info
+    if not train_if_missing:
+        raise FileNotFoundError(path)
+    t0 = time.perf_counter()
+    data = training_set(recipe["count"], recipe["shape"], recipe["eb_rel"], recipe["seed0"], device)
+    t1 = time.perf_counter()
+    net = ProposalNet(seed=recipe["init_seed"], device=device)
+    log = train(net, data, epochs=recipe["epochs"], lr=recipe["lr"], seed=recipe["order_seed"], verbose=verbose)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    del data
+    info = {"cached": False, "data_s": t1 - t0, "train_s": t2 - t1, "final_loss": log.epochs[-1][1]}
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    np.savez(path, **net.state(), train_s=info["train_s"], final_loss=info["final_loss"])
+    return net, info
+
+
 # ----------------------------------------------------------------- inference
 
 @dataclass
@@ -366,7 +412,7 @@ class LearnedResult:
     propose_ms: float
 
 
-def correct_learned(f: torch.Tensor, fhat: torch.Tensor, xi: float, net: ProposalNet, shift: int = 0,
+def correct_learned(f: torch.Tensor, fhat: torch.Tensor, xi: float, net: ProposalNet, shift: int = SHIFT,
                     **kw) -> LearnedResult:
     """Proposal, then the exact correction loop from it; when that loop ends
     without a correct field (STUCK or at its sweep cap) the plain loop from

@@ -256,34 +256,61 @@ def test_adam_matches_torch_optim(L):
     np.testing.assert_allclose(p.cpu().numpy(), ref.detach().numpy(), rtol=1e-5, atol=1e-6)
 
 
-def test_features_bitwise(L):
-    shape = (5, 9, 131)
-    fl = synth.peaks3d(shape, seed=61, eb_rel=1e-3)
-    f, fh = torch.from_numpy(fl.f).cuda(), torch.from_numpy(fl.fhat).cuda()
-    got = L.features(f, fh, float(fl.xi))
-    # differences near the clamp and inside it both occur in this field
-    torch.cuda.synchronize()
-    got = got.view(torch.int16).cpu().numpy().view(np.uint16).reshape(*shape, 16)
+def features_reference(fl):
+    """The 16 input channels written out from their definitions with the
+    oracle's codes and neighbour table (float32 arithmetic as on the GPU)."""
+    shape = fl.f.shape
     inv = np.float32(1) / np.float32(fl.xi)
     inv4 = np.float32(0.25) / np.float32(fl.xi)
 
     def cl(a, s):
         return np.clip(a.astype(np.float32) * s, -1, 1).astype(np.float32)
 
-    ff = fl.f
+    ff, hh = fl.f, fl.fhat
     ch = np.zeros((*shape, 16), np.float32)
-    ch[..., 0] = cl(fl.fhat - ff, inv)
-    ch[:, :, :-1, 1] = cl(ff[:, :, 1:] - ff[:, :, :-1], inv4)
-    ch[:, :-1, :, 2] = cl(ff[:, 1:, :] - ff[:, :-1, :], inv4)
-    ch[:-1, :, :, 3] = cl(ff[1:] - ff[:-1], inv4)
-    cf, chh = oracle.codes(fl.f), oracle.codes(fl.fhat)
+    ch[..., 0] = cl(hh - ff, inv)
+    for c, src in ((1, ff), (12, hh)):
+        ch[:, :, :-1, c] = cl(src[:, :, 1:] - src[:, :, :-1], inv4)
+        ch[:, :-1, :, c + 1] = cl(src[:, 1:, :] - src[:, :-1, :], inv4)
+        ch[:-1, :, :, c + 2] = cl(src[1:] - src[:-1], inv4)
+    cf, cg = oracle.codes(ff), oracle.codes(hh)
     ch[..., 4] = (cf & 15) == 15
     ch[..., 5] = (cf >> 4) == 15
-    ch[..., 6] = (cf & 15) != (chh & 15)
-    ch[..., 7] = (cf >> 4) != (chh >> 4)
+    ch[..., 6] = (cf & 15) != (cg & 15)
+    ch[..., 7] = (cf >> 4) != (cg >> 4)
+    ch[..., 10] = (cg & 15) == 15
+    ch[..., 11] = (cg >> 4) == 15
+    flat = ch.reshape(-1, 16)
+    cfv, cgv, fv = cf.ravel(), cg.ravel(), ff.ravel()
+    for j in range(fv.size):
+        a_f, a_g, d_f, d_g = cfv[j] & 15, cgv[j] & 15, cfv[j] >> 4, cgv[j] >> 4
+        if a_f != a_g:  # ascending mismatch: itself when fhat makes it a maximum, else fhat's steepest ascent
+            flat[j if a_g == 15 else oracle.neighbour(shape, j, int(a_g)), 8] = 1
+        if d_f != d_g:  # descending mismatch: itself when f makes it a minimum, else f's steepest descent
+            flat[j if d_f == 15 else oracle.neighbour(shape, j, int(d_f)), 9] = 1
+        ties = 0
+        for sl in range(14):
+            k = oracle.neighbour(shape, j, sl)
+            ties += k is not None and fv[k] == fv[j]
+        flat[j, 15] = np.float32(ties) / np.float32(14)
+    return ch
+
+
+def test_features_bitwise(L):
+    shape = (5, 9, 131)
+    fl = synth.peaks3d(shape, seed=61, eb_rel=1e-3)
+    f, fh = torch.from_numpy(fl.f).cuda(), torch.from_numpy(fl.fhat).cuda()
+    got = L.features(f, fh, float(fl.xi))
+    torch.cuda.synchronize()
+    got = got.view(torch.int16).cpu().numpy().view(np.uint16).reshape(*shape, 16)
+    ch = features_reference(fl)
     ref = OL.bf16(ch).astype(np.float32).view(np.uint32) >> 16
     assert np.array_equal(got.astype(np.uint32), ref)
-    assert ch[..., 6].any() or ch[..., 7].any()
+    # the case exercises every flag and both sides of the clamp
+    for c in (4, 5, 6, 7, 8, 9, 10, 11):
+        assert ch[..., c].any(), c
+    assert (np.abs(ch[..., 1]) == 1).any() and ((np.abs(ch[..., 1]) < 1) & (ch[..., 1] != 0)).any()
+    assert (ch[..., 15] > 0).any()
 
 
 # ----------------------------------------------------- whole backward pass
@@ -302,7 +329,7 @@ def test_network_gradients_match_oracle(L):
     torch.cuda.synchronize()
     net.check()
     params = net.params_numpy()
-    feat = host(x0).reshape(*shape, 16)[..., :8]
+    feat = host(x0).reshape(*shape, 16)
     acts_o = OL.forward(feat, params)
     # layer by layer the GPU activations equal the oracle's up to BF16 rounding flips
     for l in (1, 2, 3):
@@ -341,3 +368,27 @@ def test_training_reduces_loss_and_keeps_invariants(L):
     lo = np.array([oracle.floor_bound(x, fl.xi) for x in fl.f.ravel()], np.float32).reshape(fl.f.shape)
     hi = np.array([oracle.ceil_bound(x, fl.xi) for x in fl.f.ravel()], np.float32).reshape(fl.f.shape)
     assert np.all(g >= lo) and np.all(g <= hi)
+
+
+def test_trained_proposal_cuts_sweeps(L):
+    """What the trained network gains: trained by its recipe (200 seeded 128^3
+    Gaussian-peak triples, 12 epochs; about 45 s, cached with the build), its
+    start takes the exact loop to a correct field in clearly fewer sweeps than
+    the plain start on an unseen 256^3 field, and the result passes every check
+    the plain result passes."""
+    from paper_2601_01787_gb300 import api
+    net, _ = L.default_net()
+    fl = synth.peaks3d((256, 256, 256), seed=9002, eb_rel=1e-4)
+    f, fh = torch.from_numpy(fl.f).cuda(), torch.from_numpy(fl.fhat).cuda()
+    plain = api.correct(f, fh, float(fl.xi), edit_capacity=0)
+    lr = L.correct_learned(f, fh, float(fl.xi), net, edit_capacity=0)
+    assert plain.status == api.ERR_CAPACITY and lr.result.status == api.ERR_CAPACITY  # converged; no list asked
+    assert not lr.fallback
+    sp, sl = plain.stats["sweeps"], lr.from_g0.stats["sweeps"]
+    assert sl <= 0.85 * sp, (sl, sp)
+    assert lr.from_g0.stats["first_distorted"] < plain.stats["first_distorted"]
+    v = api.verify(f, lr.result.out)
+    assert v["codes_equal"] and v["wrong_labels"] == 0
+    g = lr.result.out
+    xi = float(fl.xi)
+    assert bool(((g.double() - f.double()).abs() <= xi).all())
