@@ -322,6 +322,16 @@ def run_batch(dev, stream, reps: int = 5) -> dict:
         api.correct_batch(fs, fhs, xis, edit_capacities=caps, outs=outs, tile_z=tz, stream=stream)
     t_batch = timed(lambda: api.correct_batch(fs, fhs, xis, edit_capacities=caps, outs=outs, tile_z=tz,
                                               stream=stream))
+    # the same launch captured once in a CUDA graph and replayed
+    plan = api.BatchPlan(fs, fhs, xis, edit_capacities=caps, outs=outs, tile_z=tz, stream=stream)
+    graph = plan.graph()
+    graph.replay()
+    torch.cuda.synchronize()
+    rg = plan.collect()
+    assert rg.status == api.OK and all(r.status == api.OK for r in rg.fields)
+    assert all(a.edit_count == b.edit_count for a, b in zip(rg.fields, res.fields))
+    t_graph = timed(graph.replay)
+    plan.close()
     ws1 = api.workspace(max(api.workspace_size(f.shape) for f in fs), dev)
 
     def singles():
@@ -332,7 +342,8 @@ def run_batch(dev, stream, reps: int = 5) -> dict:
     t_single = timed(singles)
     return {"workload": "perlin3d_prequant batch of 64, axes U{64..384}, eb_rel in {1e-3,1e-4,1e-5}, seeds 1000+k",
             "n_vertices": n_tot, "unit": UNIT, "value": round(n_tot / (t_batch * 1e-3) / 1e9, 4),
-            "ms": round(t_batch, 4), "separate_calls_ms": round(t_single, 4),
+            "ms": round(t_batch, 4), "graph_replay_ms": round(t_graph, 4),
+            "graph_replay_value": round(n_tot / (t_graph * 1e-3) / 1e9, 4), "separate_calls_ms": round(t_single, 4),
             "separate_calls_value": round(n_tot / (t_single * 1e-3) / 1e9, 4),
             "max_sweeps_over_fields": max(r.stats["sweeps"] for r in res.fields),
             "tile_z": sorted(set(tz)), "launches": 1}

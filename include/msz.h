@@ -219,6 +219,32 @@ size_t msz_batch_workspace_size(int32_t n, const msz_field *fields, int64_t max_
 msz_status msz_correct_batch(int32_t n, msz_field *fields, const msz_options *opt, int64_t *h_sweep_log,
                              int64_t log_capacity, void *d_workspace, size_t workspace_bytes, msz_stream_t stream);
 
+/* msz_correct_batch in three steps, so that the launch can be captured in a
+ * CUDA graph and replayed (the fields' buffers and the workspace must then
+ * stay where they are):
+ *   msz_batch_plan_create   checks the batch as msz_correct_batch does,
+ *                           uploads the field table into the workspace and
+ *                           returns a host-side plan in *plan (synchronizes
+ *                           `stream`; not capturable);
+ *   msz_batch_launch        one memset of the workspace's control block and
+ *                           bitmaps plus the cooperative kernel launch on
+ *                           `stream`: asynchronous, no host synchronization,
+ *                           capturable (on the plan's device);
+ *   msz_batch_collect       synchronizes `stream`, reads the control block,
+ *                           the per-field results and the sweep log, and
+ *                           fills fields[k] (status, edit_count, stats) and
+ *                           h_sweep_log exactly as msz_correct_batch does;
+ *                           the fields array must describe the same batch;
+ *   msz_batch_plan_destroy  frees the plan (host memory only).
+ * The plan owns no device memory. */
+typedef struct msz_batch_plan msz_batch_plan;
+msz_status msz_batch_plan_create(int32_t n, const msz_field *fields, const msz_options *opt, void *d_workspace,
+                                 size_t workspace_bytes, msz_stream_t stream, msz_batch_plan **plan);
+msz_status msz_batch_launch(const msz_batch_plan *plan, msz_stream_t stream);
+msz_status msz_batch_collect(const msz_batch_plan *plan, msz_field *fields, int64_t *h_sweep_log,
+                             int64_t log_capacity, msz_stream_t stream);
+void msz_batch_plan_destroy(msz_batch_plan *plan);
+
 /* ---- Learned initial-edit proposal (an extension: the paper has no learned
  * component).  A 4-layer 3D conv net (3x3x3 cross-correlations, zero
  * padding, channels 16 -> 32 -> 32 -> 32 -> 16, ReLU between) classifies each

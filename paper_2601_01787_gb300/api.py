@@ -105,6 +105,15 @@ def load(build_if_missing: bool = True):
         lib.msz_correct_batch.argtypes = [ctypes.c_int32, ctypes.POINTER(Field), ctypes.POINTER(Options), P, I64, P,
                                           SZ, P]
         lib.msz_correct_batch.restype = st
+        lib.msz_batch_plan_create.argtypes = [ctypes.c_int32, ctypes.POINTER(Field), ctypes.POINTER(Options), P, SZ,
+                                              P, ctypes.POINTER(P)]
+        lib.msz_batch_plan_create.restype = st
+        lib.msz_batch_launch.argtypes = [P, P]
+        lib.msz_batch_launch.restype = st
+        lib.msz_batch_collect.argtypes = [P, ctypes.POINTER(Field), P, I64, P]
+        lib.msz_batch_collect.restype = st
+        lib.msz_batch_plan_destroy.argtypes = [P]
+        lib.msz_batch_plan_destroy.restype = None
         lib.msz_status_str.argtypes = [st]
         lib.msz_status_str.restype = ctypes.c_char_p
         _lib = lib
@@ -311,6 +320,86 @@ def verify(f: torch.Tensor, g: torch.Tensor) -> dict:
 class BatchResult:
     status: int
     fields: list  # CorrectResult per field
+
+
+class BatchPlan:
+    """A prepared batch (msz_batch_plan_create): launch() is asynchronous and
+    can be captured in a CUDA graph; collect() synchronizes and returns the
+    per-field results.  The plan keeps every buffer it points to alive."""
+
+    def __init__(self, fs, fhats, xis, *, rule="halve", max_sweeps: int = 0, dense_min_items: int = 0,
+                 edit_capacities=None, outs=None, ws: torch.Tensor | None = None, stream=None, tile_z=None):
+        lib = load()
+        n = len(fs)
+        arr = (Field * n)()
+        keep = []
+        for k in range(n):
+            f, fh = fs[k], fhats[k]
+            assert f.dtype == torch.float32 and fh.dtype == torch.float32 and f.shape == fh.shape and f.dim() == 3
+            cap = f.numel() if edit_capacities is None else int(edit_capacities[k])
+            out = torch.empty_like(f) if outs is None else outs[k]
+            idx = torch.empty(max(cap, 1), dtype=torch.int32, device=f.device)
+            dl = torch.empty(max(cap, 1), dtype=torch.float32, device=f.device)
+            keep.append((out, idx, dl, cap))
+            tz = 0 if tile_z is None else int(tile_z[k])
+            arr[k] = Field(_dptr(f), _dptr(fh), ctypes.c_float(np.float32(xis[k])), -1, grid_of(f.shape),
+                           _dptr(out), _dptr(idx), _dptr(dl), cap, 0, Stats(), tz, 0)
+        need = int(lib.msz_batch_workspace_size(n, arr, int(max_sweeps)))
+        if need == 0:
+            raise MszError(ERR_INVALID_ARG, "msz_batch_workspace_size")
+        if ws is None:
+            ws = workspace(need, fs[0].device)
+        opt, _ = _options(rule, max_sweeps, dense_min_items, None, 0)
+        handle = ctypes.c_void_p()
+        st = lib.msz_batch_plan_create(n, arr, ctypes.byref(opt), _dptr(ws), ws.numel(), _stream(stream),
+                                       ctypes.byref(handle))
+        if st != OK:
+            raise MszError(st, "msz_batch_plan_create")
+        self._lib, self._h, self.n, self.arr = lib, handle, n, arr
+        self._keep = (list(fs), list(fhats), keep, ws, opt)
+
+    def launch(self, stream=None) -> None:
+        st = self._lib.msz_batch_launch(self._h, _stream(stream))
+        if st != OK:
+            raise MszError(st, "msz_batch_launch")
+
+    def collect(self, log_capacity: int = 0, stream=None) -> "BatchResult":
+        log = np.zeros(max(4 * self.n * log_capacity, 4), dtype=np.int64)
+        st = self._lib.msz_batch_collect(self._h, self.arr, log.ctypes.data if log_capacity else None,
+                                         int(log_capacity), _stream(stream))
+        results = []
+        for k in range(self.n):
+            out, idx, dl, cap = self._keep[2][k]
+            fk = self.arr[k]
+            m = min(int(fk.edit_count), cap)
+            stats = fk.stats.as_dict()
+            nlog = min(stats["sweeps"] + 1, log_capacity)
+            lg = log[4 * k * log_capacity:4 * (k * log_capacity + nlog)].reshape(-1, 4).copy() if log_capacity \
+                else np.zeros((0, 4), np.int64)
+            results.append(CorrectResult(int(fk.status), out, idx[:m], dl[:m], int(fk.edit_count), stats, lg))
+        return BatchResult(int(st), results)
+
+    def graph(self, stream=None) -> "torch.cuda.CUDAGraph":
+        """Capture one launch in a CUDA graph; replay() then reruns the whole
+        batch correction (read the results with collect())."""
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream() if stream is None else stream
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.graph(g, stream=side):
+            self.launch(torch.cuda.current_stream())
+        torch.cuda.current_stream().wait_stream(side)
+        return g
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.msz_batch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def correct_batch(fs, fhats, xis, *, rule="halve", max_sweeps: int = 0, dense_min_items: int = 0,

@@ -21,6 +21,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <new>
 #include <vector>
 
 #include "msz.h"
@@ -407,12 +408,7 @@ bool plan(int32_t n, const msz_field *fields, const msz_options *opt, std::vecto
     return true;
 }
 
-}  // namespace
-}  // namespace msz
-
-using namespace msz;
-
-extern "C" size_t msz_batch_workspace_size(int32_t n, const msz_field *fields, int64_t max_sweeps) {
+size_t batch_workspace_bytes(int32_t n, const msz_field *fields, int64_t max_sweeps) {
     if (n < 1 || n > MSZ_BATCH_MAX_FIELDS || !fields) return 0;
     if (max_sweeps <= 0) max_sweeps = MSZ_BATCH_MAX_SWEEPS;
     if (max_sweeps > MSZ_BATCH_MAX_SWEEPS) return 0;
@@ -424,16 +420,41 @@ extern "C" size_t msz_batch_workspace_size(int32_t n, const msz_field *fields, i
     return batch_layout((uint32_t)n, ntot, (uint32_t)max_sweeps).total;
 }
 
-extern "C" msz_status msz_correct_batch(int32_t n, msz_field *fields, const msz_options *opt,
-                                        int64_t *h_sweep_log, int64_t log_capacity, void *d_workspace,
-                                        size_t workspace_bytes, msz_stream_t stream) {
+// A prepared batch: everything the launch needs, kept on the host.
+struct BatchPlanImpl {
+    int32_t n;
+    uint32_t max_sweeps;
+    int blocks;
+    int device;
+    char *ws;
+    BatchLayout L;
+    BatchProblem P;
+    std::vector<GridDev> grids;
+};
+
+}  // namespace
+}  // namespace msz
+
+struct msz_batch_plan {
+    msz::BatchPlanImpl impl;
+};
+
+using namespace msz;
+
+extern "C" size_t msz_batch_workspace_size(int32_t n, const msz_field *fields, int64_t max_sweeps) {
+    return batch_workspace_bytes(n, fields, max_sweeps);
+}
+
+extern "C" msz_status msz_batch_plan_create(int32_t n, const msz_field *fields, const msz_options *opt,
+                                            void *d_workspace, size_t workspace_bytes, msz_stream_t stream,
+                                            msz_batch_plan **out_plan) {
+    if (!out_plan) return MSZ_ERR_INVALID_ARG;
+    *out_plan = nullptr;
     if (n < 1 || n > MSZ_BATCH_MAX_FIELDS || !fields) return MSZ_ERR_INVALID_ARG;
     msz_options o{};
     if (opt) o = *opt;
     if (o.rule != MSZ_RULE_HALVE && o.rule != MSZ_RULE_SNAP) return MSZ_ERR_INVALID_ARG;
-    if (o.d_g_init || o.max_sweeps > MSZ_BATCH_MAX_SWEEPS || o.dense_min_items < -1 || log_capacity < 0 ||
-        (log_capacity > 0 && !h_sweep_log))
-        return MSZ_ERR_INVALID_ARG;
+    if (o.d_g_init || o.max_sweeps > MSZ_BATCH_MAX_SWEEPS || o.dense_min_items < -1) return MSZ_ERR_INVALID_ARG;
     const uint32_t max_sweeps = o.max_sweeps <= 0 ? (uint32_t)MSZ_BATCH_MAX_SWEEPS : (uint32_t)o.max_sweeps;
     for (int32_t k = 0; k < n; ++k) {
         const msz_field &F = fields[k];
@@ -499,16 +520,57 @@ extern "C" msz_status msz_correct_batch(int32_t n, msz_field *fields, const msz_
     P.dm[1] = (uint32_t *)(ws + L.d1);
     P.eb = (uint32_t *)(ws + L.eb);
     P.ub = (uint32_t *)(ws + L.ub);
-
-    if (cudaMemsetAsync(ws, 0, L.zero_bytes, s) != cudaSuccess) return MSZ_ERR_CUDA;
-    if (cudaMemcpyAsync(ws + L.fields, tab.data(), n * sizeof(FieldDev), cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return MSZ_ERR_CUDA;
     int blocks = 0;
     if ((st = batch_blocks(dev, blocks)) != MSZ_OK) return st;
-    void *args[] = {(void *)&P};
-    if (cudaLaunchCooperativeKernel((const void *)k_batch, dim3(blocks), dim3(kThreads), args, tile::kRingBytes, s) !=
-        cudaSuccess)
+    // the descriptor table is uploaded once; launches only clear the control
+    // block and bitmaps, so a captured launch can be replayed
+    if (cudaMemcpyAsync(ws + L.fields, tab.data(), n * sizeof(FieldDev), cudaMemcpyHostToDevice, s) != cudaSuccess)
         return MSZ_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return MSZ_ERR_CUDA;
+    msz_batch_plan *p = new (std::nothrow) msz_batch_plan;
+    if (!p) return MSZ_ERR_WORKSPACE;
+    p->impl.n = n;
+    p->impl.max_sweeps = max_sweeps;
+    p->impl.blocks = blocks;
+    p->impl.device = dev.device;
+    p->impl.ws = ws;
+    p->impl.L = L;
+    p->impl.P = P;
+    p->impl.grids = std::move(grids);
+    *out_plan = p;
+    return MSZ_OK;
+}
+
+extern "C" msz_status msz_batch_launch(const msz_batch_plan *plan, msz_stream_t stream) {
+    if (!plan) return MSZ_ERR_INVALID_ARG;
+    const BatchPlanImpl &B = plan->impl;
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != B.device) return MSZ_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemsetAsync(B.ws, 0, B.L.zero_bytes, s) != cudaSuccess) return MSZ_ERR_CUDA;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(B.blocks);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = tile::kRingBytes;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    BatchProblem P = B.P;
+    if (cudaLaunchKernelEx(&cfg, k_batch, P) != cudaSuccess) return MSZ_ERR_CUDA;
+    return MSZ_OK;
+}
+
+extern "C" msz_status msz_batch_collect(const msz_batch_plan *plan, msz_field *fields, int64_t *h_sweep_log,
+                                        int64_t log_capacity, msz_stream_t stream) {
+    if (!plan || !fields || log_capacity < 0 || (log_capacity > 0 && !h_sweep_log)) return MSZ_ERR_INVALID_ARG;
+    const BatchPlanImpl &B = plan->impl;
+    const int32_t n = B.n;
+    const BatchLayout &L = B.L;
+    cudaStream_t s = (cudaStream_t)stream;
+    char *ws = B.ws;
     Ctrl hc;
     std::vector<FieldRes> res(n);
     if (cudaMemcpyAsync(&hc, ws + L.ctrl, sizeof hc, cudaMemcpyDeviceToHost, s) != cudaSuccess) return MSZ_ERR_CUDA;
@@ -537,7 +599,7 @@ extern "C" msz_status msz_correct_batch(int32_t n, msz_field *fields, const msz_
         msz_status fs = MSZ_ERR_MAX_SWEEPS;
         for (uint32_t q = 0; q <= S; ++q) {
             const BatchRec &r = log[(size_t)q * n + k];
-            const int64_t wl = q == 0 ? (int64_t)grids[k].n : (int64_t)r.worklist;
+            const int64_t wl = q == 0 ? (int64_t)B.grids[k].n : (int64_t)r.worklist;
             stt.examined += wl;
             stt.dense_sweeps += (q == 0 || r.dense) ? 1 : 0;
             if (h_sweep_log && q < (uint64_t)log_capacity) {
@@ -548,7 +610,7 @@ extern "C" msz_status msz_correct_batch(int32_t n, msz_field *fields, const msz_
                 row[3] = r.changed;
             }
             if (r.distorted == 0) { fs = MSZ_OK; stt.sweeps = q; break; }
-            if (q >= max_sweeps) { fs = MSZ_ERR_MAX_SWEEPS; stt.sweeps = q; stt.left = r.distorted; break; }
+            if (q >= B.max_sweeps) { fs = MSZ_ERR_MAX_SWEEPS; stt.sweeps = q; stt.left = r.distorted; break; }
             if (r.changed == 0) { fs = MSZ_STUCK; stt.sweeps = q + 1; stt.left = r.distorted; break; }
             stt.edits += r.changed;
         }
@@ -558,4 +620,19 @@ extern "C" msz_status msz_correct_batch(int32_t n, msz_field *fields, const msz_
         F.status = fs;
     }
     return MSZ_OK;
+}
+
+extern "C" void msz_batch_plan_destroy(msz_batch_plan *plan) { delete plan; }
+
+extern "C" msz_status msz_correct_batch(int32_t n, msz_field *fields, const msz_options *opt,
+                                        int64_t *h_sweep_log, int64_t log_capacity, void *d_workspace,
+                                        size_t workspace_bytes, msz_stream_t stream) {
+    if (log_capacity < 0 || (log_capacity > 0 && !h_sweep_log)) return MSZ_ERR_INVALID_ARG;
+    msz_batch_plan *plan = nullptr;
+    msz_status st = msz_batch_plan_create(n, fields, opt, d_workspace, workspace_bytes, stream, &plan);
+    if (st != MSZ_OK) return st;
+    st = msz_batch_launch(plan, stream);
+    if (st == MSZ_OK) st = msz_batch_collect(plan, fields, h_sweep_log, log_capacity, stream);
+    msz_batch_plan_destroy(plan);
+    return st;
 }

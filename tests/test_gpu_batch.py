@@ -101,3 +101,46 @@ def test_full_uneven_batch_matches_single_corrections(api):
             assert r.stats[key] == one.stats[key], key
         v = api.verify(f, r.out)
         assert v["codes_equal"] and v["wrong_labels"] == 0
+
+
+def test_batch_graph_replay_matches_oracle(api):
+    """The batch launch captured in a CUDA graph: every replay rebuilds g, the
+    edit lists and the statuses from fhat, equal to the oracle's per field."""
+    fields = _small_batch()
+    fs = [torch.from_numpy(fl.f).cuda() for fl in fields]
+    fhs = [torch.from_numpy(fl.fhat).cuda() for fl in fields]
+    plan = api.BatchPlan(fs, fhs, [fl.xi for fl in fields])
+    graph = plan.graph()
+    refs = [oracle.correct(fl.f, fl.fhat, fl.xi, log_capacity=4096) for fl in fields]
+    for rep in range(3):
+        for r in plan._keep[2]:
+            r[0].fill_(float("nan"))  # the replay must rewrite every output
+        graph.replay()
+        res = plan.collect(log_capacity=4096)
+        assert res.status == api.OK
+        for ref, r in zip(refs, res.fields):
+            assert r.status == ref.status
+            assert np.array_equal(_bits(r.out), _bits(ref.g))
+            assert r.edit_count == ref.edit_count
+            assert np.array_equal(r.edit_idx.cpu().numpy().view(np.uint32), ref.edit_idx)
+            assert np.array_equal(_bits(r.edit_delta), _bits(ref.edit_delta))
+            assert r.stats["sweeps"] == ref.sweeps
+            assert np.array_equal(r.sweep_log[:, 1:], ref.sweep_log[:, 1:])
+    plan.close()
+
+
+def test_batch_plan_launch_matches_one_call(api):
+    fields = _small_batch()
+    fs = [torch.from_numpy(fl.f).cuda() for fl in fields]
+    fhs = [torch.from_numpy(fl.fhat).cuda() for fl in fields]
+    one = api.correct_batch(fs, fhs, [fl.xi for fl in fields], log_capacity=64)
+    plan = api.BatchPlan(fs, fhs, [fl.xi for fl in fields])
+    plan.launch()
+    two = plan.collect(log_capacity=64)
+    assert one.status == two.status == api.OK
+    for a, b in zip(one.fields, two.fields):
+        assert a.status == b.status and a.edit_count == b.edit_count
+        assert np.array_equal(_bits(a.out), _bits(b.out))
+        assert np.array_equal(a.sweep_log, b.sweep_log)
+        assert {k: v for k, v in a.stats.items() if not k.endswith("_ns")} == \
+            {k: v for k, v in b.stats.items() if not k.endswith("_ns")}
