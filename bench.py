@@ -48,6 +48,16 @@ def workload_config(n):
             "l2": "no flush: inputs f+fhat (1.07 GB) exceed the 129 MB L2"}
 
 
+def load_bf16_peak():
+    """Dense BF16 tensor peak: the measured cuBLAS burst figure (a conv layer is
+    timed on its own), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops"]), "measured (burst)"
+    except Exception:
+        return 1900.0, "fallback"
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -390,6 +400,9 @@ def run_learned(dev, stream, reps: int = 3) -> dict:
     assert rl.result.status == api.OK, api.status_str(rl.result.status)
     vl = api.verify(f, out)
     n = fl.n
+    convs = time_convs(net, f, fh, fl.xi, stream)
+    peak = load_bf16_peak()
+    c32 = convs["conv32x32_relu"]
     return {"workload": "peaks3d_512x512x512: 5000 Gaussian peaks on Poisson(5) counts, seed 7, eb_rel 1e-4, "
                         "fhat = f + U[-xi, xi]",
             "n_vertices": n, "unit": UNIT, "shift": learned.SHIFT,
@@ -403,9 +416,69 @@ def run_learned(dev, stream, reps: int = 3) -> dict:
                         "sweeps": rl.from_g0.stats["sweeps"], "first_distorted": rl.from_g0.stats["first_distorted"],
                         "edited": rl.result.edit_count, "fallback_to_plain": rl.fallback,
                         "verified": bool(vl["codes_equal"] and vl["wrong_labels"] == 0)},
+            "convs": convs,
+            "conv_roofline": {"bound": "tensor", "kernel": "k_conv<32,32,RELU>", "achieved": c32["tflops"],
+                              "peak": peak[0], "unit": "TFLOP/s", "frac": round(c32["tflops"] / peak[0], 4),
+                              "peak_kind": peak[1], "flops_per_voxel": conv_flops_per_voxel(32, 32)},
             "training": {"recipe": learned.RECIPE | {"shape": list(learned.RECIPE["shape"])},
                          "cached": info["cached"], "train_s": None if info.get("train_s") is None else
                          round(info["train_s"], 2), "final_loss": info.get("final_loss")}}
+
+
+def conv_flops_per_voxel(cin: int, cout: int) -> int:
+    """Dense FLOPs of one 3x3x3 conv layer per output voxel (padded channels)."""
+    return 2 * 27 * cin * cout
+
+
+def time_convs(net, f, fh, xi, stream, reps: int = 5) -> dict:
+    """Device time of each conv layer of the proposal on this field (CUDA
+    events on the launching stream, after one warm-up launch each)."""
+    import torch
+
+    from paper_2601_01787_gb300 import learned
+    n = f.numel()
+    x0 = learned.features(f, fh, xi, stream=stream)
+    net.build_images(stream=stream)
+    a = torch.empty(n, 32, dtype=torch.bfloat16, device=f.device)
+    b = torch.empty_like(a)
+    g0 = torch.empty_like(f)
+    layers = [("conv16x32_relu", lambda: learned.conv(x0, 16, 32, learned.MODE_RELU, f.shape, net._img[0], net.err,
+                                                      bias=net.b[0], out_bf16=a, stream=stream), 16, 32),
+              ("conv32x32_relu", lambda: learned.conv(a, 32, 32, learned.MODE_RELU, f.shape, net._img[1], net.err,
+                                                      bias=net.b[1], out_bf16=b, stream=stream), 32, 32),
+              ("conv32x16_head", lambda: learned.conv(b, 32, 16, learned.MODE_HEAD, f.shape, net._img[3], net.err,
+                                                      bias=net.b[3], f=f, fhat=fh, xi=xi, g0=g0, stream=stream),
+               32, 16)]
+    out = {}
+    for name, fn, cin, cout in layers:
+        fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"ms": round(ms, 4), "tflops": round(n * conv_flops_per_voxel(cin, cout) / (ms * 1e-3) / 1e12, 2)}
+    net.check()
+    return out
+
+
+def profile_conv(args) -> None:
+    """Profiling case (captures only): two proposals on a small Gaussian-peak
+    field with an untrained network (the weights do not change the work)."""
+    import torch
+
+    from paper_2601_01787_gb300 import learned, synth
+    fl = synth.peaks3d(SHAPE, seed=7, eb_rel=1e-4)
+    f = torch.from_numpy(fl.f).cuda()
+    fh = torch.from_numpy(fl.fhat).cuda()
+    net = learned.ProposalNet(seed=1)
+    for _ in range(2):
+        net.propose(f, fh, fl.xi)
+    torch.cuda.synchronize()
+    net.check()
+    print(json.dumps({"profile_conv": list(SHAPE)}))
 
 
 def api_source_hash() -> str:
@@ -474,12 +547,17 @@ def main(argv=None):
     ap.add_argument("--cpu-slab", type=int, default=128, help="z-planes of the CPU-baseline sample")
     ap.add_argument("--ref-slab", type=int, default=24, help="z-planes per reference-arm step")
     ap.add_argument("--shape", default=None, help="nz,ny,nx of a smaller field (profiling captures only)")
+    ap.add_argument("--profile-conv", action="store_true",
+                    help="run two learned proposals on a --shape peak field and exit (profiling captures only)")
     args = ap.parse_args(argv)
     if args.shape:
         global SHAPE
         SHAPE = tuple(int(v) for v in args.shape.split(","))
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.profile_conv:
+        profile_conv(args)
+        return
     ws, rank, local = dist_info()
     if ws > 1:
         import torch.distributed as dist
