@@ -81,10 +81,14 @@ typedef enum { MSZ_RULE_HALVE = 0, MSZ_RULE_SNAP = 1 } msz_rule;
 
 typedef struct {
     int32_t rule;             /* msz_rule; default HALVE */
-    int32_t reserved;         /* 0 */
+    int32_t test_fault;       /* 0.  Test hook of the bounded waits: 1 makes block 0 of the
+                                 correction kernel wait at its first grid barrier without
+                                 arriving, so every block's wait (shortened to 0.25 s) runs
+                                 out and the call returns MSZ_ERR_TIMEOUT with no output */
     int64_t max_sweeps;       /* <= 0: MSZ_MAX_SWEEPS_LIMIT; else 1..MSZ_MAX_SWEEPS_LIMIT */
-    int64_t dense_min_items;  /* next sweep scans the whole grid when 8*targets + distorted
-                                 >= this; 0: N/16 (default); -1: always use the worklist */
+    int64_t dense_min_items;  /* next sweep scans the whole grid when 6 x (vertices distorted
+                                 in this sweep) >= this; 0: N/16 (default); -1: always use
+                                 the worklist.  Affects speed only, never results */
     const float *d_g_init;    /* NULL: start from fhat.  Else N floats, each in [L_i, U_i]: a
                                  proposed start (the learned proposal); edits are still
                                  reported against fhat */

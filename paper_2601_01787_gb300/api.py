@@ -36,7 +36,7 @@ class Grid(ctypes.Structure):
 
 
 class Options(ctypes.Structure):
-    _fields_ = [("rule", ctypes.c_int32), ("reserved", ctypes.c_int32), ("max_sweeps", ctypes.c_int64),
+    _fields_ = [("rule", ctypes.c_int32), ("test_fault", ctypes.c_int32), ("max_sweeps", ctypes.c_int64),
                 ("dense_min_items", ctypes.c_int64), ("d_g_init", ctypes.c_void_p),
                 ("h_sweep_log", ctypes.c_void_p), ("log_capacity", ctypes.c_int64),
                 ("h_timeline", ctypes.c_void_p), ("tile_z", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
@@ -195,10 +195,11 @@ class CorrectResult:
         return self.status == OK
 
 
-def _options(rule, max_sweeps, dense_min_items, g_init, log_capacity, tile_z=0):
+def _options(rule, max_sweeps, dense_min_items, g_init, log_capacity, tile_z=0, test_fault=0):
     log = np.zeros(max(4 * log_capacity, 4), dtype=np.int64)
     tl = np.full(max(2 * log_capacity, 2), -1, dtype=np.int64)
-    opt = Options(RULES[rule] if isinstance(rule, str) else int(rule), 0, int(max_sweeps), int(dense_min_items),
+    opt = Options(RULES[rule] if isinstance(rule, str) else int(rule), int(test_fault), int(max_sweeps),
+                  int(dense_min_items),
                   _dptr(g_init), log.ctypes.data if log_capacity else None, int(log_capacity),
                   tl.ctypes.data if log_capacity else None, int(tile_z), 0)
     opt._keep = (log, tl)
@@ -209,7 +210,7 @@ def correct(f: torch.Tensor, fhat: torch.Tensor, xi: float, *, rule="halve", max
             dense_min_items: int = 0, g_init: torch.Tensor | None = None, edit_capacity: int | None = None,
             log_capacity: int = 0, out: torch.Tensor | None = None, edit_idx: torch.Tensor | None = None,
             edit_delta: torch.Tensor | None = None, ws: torch.Tensor | None = None, stream=None,
-            check: bool = False, tile_z: int = 0) -> CorrectResult:
+            check: bool = False, tile_z: int = 0, test_fault: int = 0) -> CorrectResult:
     """Run the correction loop on device tensors (msz_correct)."""
     assert f.dtype == torch.float32 and fhat.dtype == torch.float32 and f.shape == fhat.shape
     lib = load()
@@ -225,7 +226,7 @@ def correct(f: torch.Tensor, fhat: torch.Tensor, xi: float, *, rule="halve", max
     need = int(lib.msz_workspace_size(g))
     if ws is None:
         ws = workspace(need, f.device)
-    opt, log = _options(rule, max_sweeps, dense_min_items, g_init, log_capacity, tile_z)
+    opt, log = _options(rule, max_sweeps, dense_min_items, g_init, log_capacity, tile_z, test_fault)
     stats = Stats()
     count = ctypes.c_int64()
     st = lib.msz_correct(_dptr(f), _dptr(fhat), ctypes.c_float(np.float32(xi)), g, _dptr(out),

@@ -454,7 +454,8 @@ extern "C" msz_status msz_batch_plan_create(int32_t n, const msz_field *fields, 
     msz_options o{};
     if (opt) o = *opt;
     if (o.rule != MSZ_RULE_HALVE && o.rule != MSZ_RULE_SNAP) return MSZ_ERR_INVALID_ARG;
-    if (o.d_g_init || o.max_sweeps > MSZ_BATCH_MAX_SWEEPS || o.dense_min_items < -1) return MSZ_ERR_INVALID_ARG;
+    if (o.d_g_init || o.test_fault || o.max_sweeps > MSZ_BATCH_MAX_SWEEPS || o.dense_min_items < -1)
+        return MSZ_ERR_INVALID_ARG;
     const uint32_t max_sweeps = o.max_sweeps <= 0 ? (uint32_t)MSZ_BATCH_MAX_SWEEPS : (uint32_t)o.max_sweeps;
     for (int32_t k = 0; k < n; ++k) {
         const msz_field &F = fields[k];

@@ -49,6 +49,7 @@ struct Problem {
     unsigned long long edit_cap;
     uint32_t max_sweeps;
     long long dense_min;  // < 0: never scan densely after sweep 0
+    uint32_t test_fault;  // test hook: block 0 does not arrive at the first grid barrier
 };
 
 // ------------------------------------------------------ the persistent kernel
@@ -67,7 +68,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
     // ---- sweep 0: codes of f with their certification, g = start, bound check
     if (NDIM == 3) first_tiled(F, &P.log[0].tile_next, smem, &C->error);
     else first_generic<NDIM>(F, &C->error);
-    bool ok = grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
+    bool ok = P.test_fault ? grid_barrier(&C->bar_count, &C->bar_gen, &C->error, kTestBarrierNs, blockIdx.x == 0)
+                           : grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
     if (leader) C->t_codes = global_ns();
     // ---- detection of sweep 0: only uncertified vertices can be distorted
     if (ok) {
@@ -302,6 +304,7 @@ extern "C" msz_status msz_correct(const float *d_f, const float *d_fhat, float x
     msz_options o{};
     if (opt) o = *opt;
     if (o.rule != MSZ_RULE_HALVE && o.rule != MSZ_RULE_SNAP) return MSZ_ERR_INVALID_ARG;
+    if (o.test_fault != 0 && o.test_fault != 1) return MSZ_ERR_INVALID_ARG;
     if (o.max_sweeps > MSZ_MAX_SWEEPS_LIMIT || o.dense_min_items < -1 || o.log_capacity < 0 || o.tile_z < 0 ||
         o.tile_z > 1024 ||
         (o.log_capacity > 0 && !o.h_sweep_log))
@@ -339,6 +342,7 @@ extern "C" msz_status msz_correct(const float *d_f, const float *d_fhat, float x
     P.edit_cap = (unsigned long long)edit_capacity;
     P.max_sweeps = o.max_sweeps <= 0 ? (uint32_t)MSZ_MAX_SWEEPS_LIMIT : (uint32_t)o.max_sweeps;
     P.dense_min = o.dense_min_items == 0 ? (long long)(G.n / 16 > 0 ? G.n / 16 : 1) : (long long)o.dense_min_items;
+    P.test_fault = (uint32_t)o.test_fault;
 
     if (cudaMemsetAsync(ws, 0, L.zero_bytes, s) != cudaSuccess) return MSZ_ERR_CUDA;
     st = G.ndim == 3 ? run_correct<3>(P, dev, s) : run_correct<2>(P, dev, s);

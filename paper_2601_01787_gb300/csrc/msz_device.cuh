@@ -317,17 +317,21 @@ __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
 
 // Grid-wide barrier for a cooperative launch (all blocks co-resident).  The
 // wait is bounded: after timeout_ns the block records kErrTimeout and leaves.
-// Returns false when any block has recorded an error.
-constexpr uint64_t kBarrierTimeoutNs = 4000000000ull;  // 4 s
+// Returns false when any block has recorded an error.  skip_arrival (a test
+// hook) makes this block wait without arriving, so that every block's wait
+// runs out and every block returns false.
+constexpr uint64_t kBarrierTimeoutNs = 4000000000ull;   // 4 s
+constexpr uint64_t kTestBarrierNs = 250000000ull;       // 0.25 s, under the test hook
 
-__device__ __forceinline__ bool grid_barrier(uint32_t *count, uint32_t *gen, uint32_t *err) {
+__device__ __forceinline__ bool grid_barrier(uint32_t *count, uint32_t *gen, uint32_t *err,
+                                             uint64_t timeout_ns = kBarrierTimeoutNs, bool skip_arrival = false) {
     __shared__ uint32_t s_err;  // block-uniform verdict
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
         const uint32_t g0 = ld_acquire(gen);
-        const uint32_t arrived = atomicAdd(count, 1u);
-        if (arrived == gridDim.x - 1) {
+        const uint32_t arrived = skip_arrival ? 0u : atomicAdd(count, 1u);
+        if (!skip_arrival && arrived == gridDim.x - 1) {
             *count = 0;
             __threadfence();
             st_release(gen, g0 + 1);
@@ -335,7 +339,7 @@ __device__ __forceinline__ bool grid_barrier(uint32_t *count, uint32_t *gen, uin
             const uint64_t t0 = global_ns();
             while (ld_acquire(gen) == g0) {
                 __nanosleep(32);
-                if (global_ns() - t0 > kBarrierTimeoutNs) {
+                if (global_ns() - t0 > timeout_ns) {
                     atomicOr(err, kErrTimeout);
                     break;
                 }
