@@ -132,7 +132,7 @@ class ClockSampler:
 
 # --------------------------------------------------------------- roofline
 def algorithmic_bytes(n: int, log: np.ndarray, edited: int) -> int:
-    """Compulsory HBM bytes of one correction (see DESIGN.md):
+    """Compulsory HBM bytes of one correction:
     sweep 0 reads f, fhat and writes codes_f, g (13 B/vertex); a later sweep
     reads g and codes_f of every examined vertex (5 B each: the whole grid for
     dense sweeps, the worklist otherwise); every distinct target reads f and g
@@ -144,6 +144,31 @@ def algorithmic_bytes(n: int, log: np.ndarray, edited: int) -> int:
     total += 12 * int(log[:, 2].sum())
     total += n // 8 + 8 * edited
     return total
+
+
+# ALU operations of one steepest-neighbour code over the 14 neighbours and
+# the vertex itself: per candidate and direction a compare, a value select and
+# a slot select (3 ops); the certification of sweep 0 adds the runner-up value
+# (a select and a min/max: 2 ops) per candidate and direction.
+ALU_OPS_CODE = 14 * 2 * 3
+ALU_OPS_CODE_CERT = 14 * 2 * 5
+
+
+def algorithmic_alu_ops(n: int, log: np.ndarray, uncertified: int) -> int:
+    """ALU operations of one correction: the certified codes of f at every
+    vertex, the codes of g at the uncertified vertices in sweep 0 and at every
+    vertex examined by a later sweep (dense sweeps examine the uncertified
+    ones)."""
+    total = ALU_OPS_CODE_CERT * n + ALU_OPS_CODE * uncertified
+    for k in range(1, log.shape[0]):
+        total += ALU_OPS_CODE * min(int(log[k, 0]), uncertified)
+    return total
+
+
+def alu_peak(sm_mhz: float) -> float:
+    """ALU-pipe peak of a GB300 in operations/s: 152 SMs x 4 sub-partitions x
+    16 lanes (a warp instruction every 2 cycles) x the SM clock."""
+    return 152 * 4 * 16 * sm_mhz * 1e6
 
 
 def dist_info():
@@ -239,6 +264,28 @@ def run_ours(args, ws, rank, local):
         except Exception:
             traffic = None
 
+    # the same kernel against the ALU-pipe peak (the pipe that bounds it)
+    alu_ops = algorithmic_alu_ops(n, log, first.stats["uncertified"])
+    alu_pk = alu_peak(clk.get("sm_mhz") or 2070.0) / 1e9
+    alu_ach = alu_ops / (ms_local * 1e-3) / 1e9
+
+    # verification of the result (codes, labels by pointer jumping, counts)
+    # and the SNAP edit rule on the same field
+    def timed_ms(fn, reps=3):
+        fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            res = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps, res
+
+    verify_ms, ver = timed_ms(lambda: api.verify(f, out))
+    snap_ms, snap = timed_ms(lambda: api.correct(f, fh, fl.xi, rule="snap", out=out, edit_idx=eidx, edit_delta=edel,
+                                                 edit_capacity=cap, ws=ws_buf, stream=stream))
+    step()  # leave the HALVE result in out
+
     # end to end through the host-buffer entry point (pinned buffers)
     hf = torch.from_numpy(fl.f).pin_memory()
     hfh = torch.from_numpy(fl.fhat).pin_memory()
@@ -272,6 +319,15 @@ def run_ours(args, ws, rank, local):
                      "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
                      "algorithmic_bytes": alg, "kernel": "k_correct<3>",
                      "kernel_ms_device": round(kernel_ms, 5)},
+        "roofline_alu": {"bound": "alu", "achieved": round(alu_ach, 1), "peak": round(alu_pk, 1), "unit": "Gop/s",
+                         "frac": round(alu_ach / alu_pk, 4), "ops": alu_ops, "uncertified": first.stats["uncertified"],
+                         "peak_kind": "derived: 152 SMs x 64 ALU lanes x median SM clock"},
+        "verify": {"ms": round(verify_ms, 4), "codes_equal": ver["codes_equal"], "wrong_labels": ver["wrong_labels"],
+                   "false_extrema": ver["fp_max"] + ver["fn_max"] + ver["fp_min"] + ver["fn_min"]},
+        "rules": {"halve": {"ms": round(ms, 4), "sweeps": first.stats["sweeps"], "edits": first.stats["edits"],
+                            "edited": first.edit_count},
+                  "snap": {"ms": round(snap_ms, 4), "sweeps": snap.stats["sweeps"], "edits": snap.stats["edits"],
+                           "edited": snap.edit_count, "status": api.status_str(snap.status)}},
         "e2e": {"value": round(e2e_value, 4), "unit": UNIT, "h2d_bytes_per_step": 8 * n,
                 "d2h_bytes_per_step": 4 * n + 8 * hr.edit_count, "ms_per_step": round(e2e_ms, 4)},
         "gpu_launches": args.steps,

@@ -86,9 +86,11 @@ typedef struct {
                                  arriving, so every block's wait (shortened to 0.25 s) runs
                                  out and the call returns MSZ_ERR_TIMEOUT with no output */
     int64_t max_sweeps;       /* <= 0: MSZ_MAX_SWEEPS_LIMIT; else 1..MSZ_MAX_SWEEPS_LIMIT */
-    int64_t dense_min_items;  /* next sweep scans the whole grid when 6 x (vertices distorted
-                                 in this sweep) >= this; 0: N/16 (default); -1: always use
-                                 the worklist.  Affects speed only, never results */
+    int64_t dense_min_items;  /* > 0: the next sweep scans every uncertified vertex instead of
+                                 the worklist when 6 x (vertices distorted in this sweep) >=
+                                 this; 0 (default): always the worklist in msz_correct, N/16
+                                 in msz_correct_batch (N: all fields' vertices); -1: always the
+                                 worklist.  Affects speed only, never results */
     const float *d_g_init;    /* NULL: start from fhat.  Else N floats, each in [L_i, U_i]: a
                                  proposed start (the learned proposal); edits are still
                                  reported against fhat */
@@ -113,6 +115,8 @@ typedef struct {
     int64_t dense_sweeps;     /* sweeps run as whole-grid scans, sweep 0 included */
     int64_t kernel_ns;        /* device time of the correction kernel (globaltimer) */
     int64_t codes_ns;         /* ... of its first phase: the codes of f and their certification */
+    int64_t uncertified;      /* vertices sweep 0 could not certify (only these can ever be
+                                 distorted); 0 in msz_correct_batch results */
 } msz_stats;
 
 /* Bytes of device workspace msz_correct needs for this grid (about 13.5 bytes

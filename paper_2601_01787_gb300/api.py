@@ -44,7 +44,8 @@ class Options(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("sweeps", "edits", "edited", "first_distorted", "left",
-                                              "examined", "dense_sweeps", "kernel_ns", "codes_ns")]
+                                              "examined", "dense_sweeps", "kernel_ns", "codes_ns",
+                                              "uncertified")]
 
     def as_dict(self) -> dict:
         return {n: int(getattr(self, n)) for n, _ in self._fields_}

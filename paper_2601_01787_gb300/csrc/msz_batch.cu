@@ -123,6 +123,31 @@ __device__ __forceinline__ void flush_counts(uint32_t (*cnt)[4], uint32_t nf, Ba
     __syncthreads();
 }
 
+// Detection of two vertices per lane of the shared index space (each may lie
+// in a different field): the neighbour loads of both are issued before either
+// code is formed; distorted vertices are counted per field in s_cnt[f][1].
+template <class Alive>
+__device__ __forceinline__ void detect_pair(const BatchProblem &P, const uint32_t *s_base, uint32_t nf,
+                                            uint32_t (*s_cnt)[4], uint32_t next_parity, Alive &&alive, bool h1,
+                                            uint32_t v1, bool h2, uint32_t v2) {
+    const uint32_t f1 = h1 ? find_field(s_base, nf, v1) : 0u, f2 = h2 ? find_field(s_base, nf, v2) : 0u;
+    const bool l1 = h1 && alive(f1), l2 = h2 && alive(f2);
+    const FieldView &F1 = P.fields[f1].F;
+    const FieldView &F2 = P.fields[f2].F;
+    const uint32_t i1 = l1 ? v1 - s_base[f1] : 0u, i2 = l2 ? v2 - s_base[f2] : 0u;
+    float a[15], b[15];
+    gather_closed<3>(F1.g, F1.G, l1, i1, a);
+    gather_closed<3>(F2.g, F2.G, l2, i2, b);
+    const uint32_t cf1 = l1 ? __ldg(&F1.codes_f[i1]) : 0u;
+    const uint32_t cf2 = l2 ? __ldg(&F2.codes_f[i2]) : 0u;
+    Emitter E1{F1.dm[next_parity], 0};
+    report(F1, E1, l1, i1, cf1, code_of_closed<3>(a));
+    if (E1.distorted) atomicAdd(&s_cnt[f1][1], 1u);
+    Emitter E2{F2.dm[next_parity], 0};
+    report(F2, E2, l2, i2, cf2, code_of_closed<3>(b));
+    if (E2.distorted) atomicAdd(&s_cnt[f2][1], 1u);
+}
+
 __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant__ const BatchProblem P) {
     extern __shared__ __align__(16) float smem[];
     __shared__ uint32_t s_base[MSZ_BATCH_MAX_FIELDS + 1];
@@ -174,13 +199,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
     // ---- detection of sweep 0 over the uncertified vertices of every field
     if (ok) {
         uint32_t seen = 0;
-        walk_bits<false>(P.ub, nullptr, P.all, seen, [&](bool has, uint32_t v) {
-            uint32_t k = 0;
-            if (has) k = find_field(s_base, nf, v);
-            const FieldView &F = P.fields[k].F;
-            Emitter E{F.dm[1], 0};
-            detect_vertex<3>(F, E, has, has ? v - s_base[k] : 0u);
-            if (E.distorted) atomicAdd(&s_cnt[k][1], 1u);
+        walk_bits_pairs<false>(P.ub, nullptr, P.all, seen, [&](bool h1, uint32_t v1, bool h2, uint32_t v2) {
+            detect_pair(P, s_base, nf, s_cnt, 1u, [](uint32_t) { return true; }, h1, v1, h2, v2);
         });
         flush_counts(s_cnt, nf, P.log);
     }
@@ -260,14 +280,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
                     rec1[f].dense = 1;
                 }
             uint32_t seen = 0;
-            walk_bits<false>(P.ub, nullptr, P.all, seen, [&](bool has, uint32_t v) {
-                uint32_t f = 0;
-                if (has) f = find_field(s_base, nf, v);
-                const bool live = has && alive(f);
-                const FieldView &F = P.fields[f].F;
-                Emitter E{F.dm[(k1 + 1) & 1], 0};
-                detect_vertex<3>(F, E, live, live ? v - s_base[f] : 0u);
-                if (E.distorted) atomicAdd(&s_cnt[f][1], 1u);
+            walk_bits_pairs<false>(P.ub, nullptr, P.all, seen, [&](bool h1, uint32_t v1, bool h2, uint32_t v2) {
+                detect_pair(P, s_base, nf, s_cnt, (k1 + 1) & 1, alive, h1, v1, h2, v2);
             });
         } else {
             const uint32_t lane = lane_id();
@@ -283,14 +297,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
                 }
             }
             uint32_t seen = 0;
-            walk_bits<true>(dcur, P.ub, P.all, seen, [&](bool has, uint32_t v) {
-                uint32_t f = 0;
-                if (has) f = find_field(s_base, nf, v);
-                const bool live = has && alive(f);
-                const FieldView &F = P.fields[f].F;
-                Emitter E{F.dm[(k1 + 1) & 1], 0};
-                detect_vertex<3>(F, E, live, live ? v - s_base[f] : 0u);
-                if (E.distorted) atomicAdd(&s_cnt[f][1], 1u);
+            walk_bits_pairs<true>(dcur, P.ub, P.all, seen, [&](bool h1, uint32_t v1, bool h2, uint32_t v2) {
+                detect_pair(P, s_base, nf, s_cnt, (k1 + 1) & 1, alive, h1, v1, h2, v2);
             });
         }
         flush_counts(s_cnt, nf, rec1);
@@ -515,6 +523,8 @@ extern "C" msz_status msz_batch_plan_create(int32_t n, const msz_field *fields, 
     P.res = (FieldRes *)(ws + L.res);
     P.bsum = (uint32_t *)(ws + L.bsum);
     P.max_sweeps = max_sweeps;
+    // default: whole-grid scans while 6 x distorted >= N/16 (measured faster
+    // than the worklist for the many small fields of a batch)
     P.dense_min = o.dense_min_items == 0 ? (long long)(ntot / 16 > 0 ? ntot / 16 : 1) : (long long)o.dense_min_items;
     P.tb = (uint32_t *)(ws + L.tb);
     P.dm[0] = (uint32_t *)(ws + L.d0);

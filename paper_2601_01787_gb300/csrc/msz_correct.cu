@@ -75,7 +75,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
     if (ok) {
         Emitter E{F.dm[1], 0};
         uint32_t seen = 0;
-        walk_bits<false>(F.ub, nullptr, G, seen, [&](bool has, uint32_t v) { detect_vertex<NDIM>(F, E, has, v); });
+        walk_bits_pairs<false>(F.ub, nullptr, G, seen, [&](bool h1, uint32_t v1, bool h2, uint32_t v2) {
+            detect_vertex2<NDIM>(F, E, h1, v1, h2, v2);
+        });
         warp_add(E.distorted, &P.log[0].distorted);
     }
     if (leader) {
@@ -135,10 +137,14 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
                 C->dense_sweeps += 1;
             }
             for (uint32_t w = gtid; w < G.words; w += stride) dcur[w] = 0;
-            walk_bits<false>(F.ub, nullptr, G, seen, [&](bool has, uint32_t v) { detect_vertex<NDIM>(F, E, has, v); });
+            walk_bits_pairs<false>(F.ub, nullptr, G, seen, [&](bool h1, uint32_t v1, bool h2, uint32_t v2) {
+                detect_vertex2<NDIM>(F, E, h1, v1, h2, v2);
+            });
         } else {
             // the worklist, restricted to uncertified vertices
-            walk_bits<true>(dcur, F.ub, G, seen, [&](bool has, uint32_t v) { detect_vertex<NDIM>(F, E, has, v); });
+            walk_bits_pairs<true>(dcur, F.ub, G, seen, [&](bool h1, uint32_t v1, bool h2, uint32_t v2) {
+                detect_vertex2<NDIM>(F, E, h1, v1, h2, v2);
+            });
             warp_add(seen, &P.log[k1].worklist);
         }
         warp_add(E.distorted, &P.log[k1].distorted);
@@ -155,8 +161,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
     const uint32_t W = G.words;
     const uint32_t per = (W + gridDim.x - 1) / gridDim.x;
     const uint32_t w0 = min(blockIdx.x * per, W), w1 = min(w0 + per, W);
-    uint32_t cnt = 0;
-    for (uint32_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) cnt += __popc(F.eb[w]);
+    uint32_t cnt = 0, unc = 0;
+    for (uint32_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) {
+        cnt += __popc(F.eb[w]);
+        unc += __popc(F.ub[w]);
+    }
+    warp_add(unc, &C->uncertified);
     uint32_t tot;
     block_exclusive_scan(cnt, sm, tot);
     if (threadIdx.x == 0) P.bsum[blockIdx.x] = tot;
@@ -341,7 +351,9 @@ extern "C" msz_status msz_correct(const float *d_f, const float *d_fhat, float x
     P.edit_delta = d_edit_delta;
     P.edit_cap = (unsigned long long)edit_capacity;
     P.max_sweeps = o.max_sweeps <= 0 ? (uint32_t)MSZ_MAX_SWEEPS_LIMIT : (uint32_t)o.max_sweeps;
-    P.dense_min = o.dense_min_items == 0 ? (long long)(G.n / 16 > 0 ? G.n / 16 : 1) : (long long)o.dense_min_items;
+    // default: the worklist after sweep 0 (measured faster than whole-grid
+    // scans on every workload once detection gathers two vertices per lane)
+    P.dense_min = o.dense_min_items == 0 ? -1LL : (long long)o.dense_min_items;
     P.test_fault = (uint32_t)o.test_fault;
 
     if (cudaMemsetAsync(ws, 0, L.zero_bytes, s) != cudaSuccess) return MSZ_ERR_CUDA;
@@ -385,6 +397,7 @@ extern "C" msz_status msz_correct(const float *d_f, const float *d_fhat, float x
         h_stats->dense_sweeps = hc.dense_sweeps;
         h_stats->kernel_ns = hc.t_end > hc.t_start ? (int64_t)(hc.t_end - hc.t_start) : 0;
         h_stats->codes_ns = hc.t_codes > hc.t_start ? (int64_t)(hc.t_codes - hc.t_start) : 0;
+        h_stats->uncertified = hc.uncertified;
     }
     const msz_status loop = (msz_status)hc.status;
     if (loop == MSZ_OK && (int64_t)hc.edit_count > edit_capacity) return MSZ_ERR_CAPACITY;

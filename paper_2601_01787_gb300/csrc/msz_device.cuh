@@ -21,6 +21,28 @@ constexpr uint32_t kFull = 0xffffffffu;
 constexpr uint32_t kErrInput = 1u;    // a value not finite or outside [L, U]
 constexpr uint32_t kErrTimeout = 2u;  // a bounded wait ran out
 
+// Division of an index n < 2^31 by a fixed d >= 1 without a divide: for d a
+// power of two, n >> s; otherwise with s = ceil(log2 d) and
+// m = ceil(2^(31+s) / d) < 2^32, floor(n / d) = umulhi(n, m) >> (s - 1),
+// because n m / 2^(31+s) exceeds n / d by less than n / 2^(31+s) < 1/d, too
+// little to reach the next integer.  m = 0 marks the power-of-two case.
+struct FastDiv {
+    uint32_t m, sh;
+};
+
+__host__ __device__ inline FastDiv fast_div(uint32_t d) {
+    FastDiv f{0u, 0u};
+    if ((d & (d - 1u)) == 0u) {
+        while ((1u << f.sh) < d) ++f.sh;
+        return f;
+    }
+    uint32_t s = 0;
+    while (s < 32u && (1ull << s) < (unsigned long long)d) ++s;
+    f.m = (uint32_t)(((1ull << (31u + s)) + d - 1ull) / d);
+    f.sh = s - 1u;
+    return f;
+}
+
 struct GridDev {
     int32_t ndim;
     uint32_t nx, ny, nz;
@@ -29,7 +51,12 @@ struct GridDev {
     uint32_t words;   // ceil(n / 32): bitmap words
     uint32_t blocks;  // ceil(n / 1024): top-level bits
     int32_t off[16];  // linear offset of each neighbour slot (14, 15 unused)
+    FastDiv dx, dxy;  // division by nx and by nx * ny
 };
+
+__device__ __forceinline__ uint32_t div_fast(uint32_t n, FastDiv f) {
+    return f.m ? (__umulhi(n, f.m) >> f.sh) : (n >> f.sh);
+}
 
 // Slot table (x, y, z) of the public header: positive offsets, then negatives.
 __host__ __device__ __forceinline__ void slot_delta(int ndim, int s, int &dx, int &dy, int &dz) {
@@ -56,9 +83,9 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 }
 
 __device__ __forceinline__ void coords_of(const GridDev &G, uint32_t i, uint32_t &x, uint32_t &y, uint32_t &z) {
-    z = i / G.nxy;
+    z = div_fast(i, G.dxy);
     const uint32_t r = i - z * G.nxy;
-    y = r / G.nx;
+    y = div_fast(r, G.dx);
     x = r - y * G.nx;
 }
 
@@ -88,6 +115,66 @@ struct Extremes {
     }
     __device__ __forceinline__ uint8_t code() const { return (uint8_t)(hs | (ls << 4)); }
 };
+
+// The 15 candidates of vertex i in ascending linear index order (3D; 7 in
+// 2D), NaN where the neighbour is outside the grid or the lane has no vertex:
+// a NaN candidate never wins a comparison.  Loads only, so that a caller can
+// issue the loads of several vertices before using any of them.
+template <int NDIM>
+__device__ __forceinline__ void gather_closed(const float *v, const GridDev &G, bool has, uint32_t i, float (&w)[15]) {
+    const float nan = __int_as_float(0x7fffffff);
+#pragma unroll
+    for (int k = 0; k < 15; ++k) w[k] = nan;
+    if (!has) return;
+    uint32_t x, y, z;
+    coords_of(G, i, x, y, z);
+    const bool xm = x > 0, xp = x + 1 < G.nx, ym = y > 0, yp = y + 1 < G.ny;
+    const uint32_t nx = G.nx;
+    if (NDIM == 3) {
+        const bool zm = z > 0, zp = z + 1 < G.nz;
+        const uint32_t nxy = G.nxy;
+        if (xm && ym && zm) w[0] = v[i - 1 - nx - nxy];
+        if (ym && zm) w[1] = v[i - nx - nxy];
+        if (xm && zm) w[2] = v[i - 1 - nxy];
+        if (zm) w[3] = v[i - nxy];
+        if (xm && ym) w[4] = v[i - 1 - nx];
+        if (ym) w[5] = v[i - nx];
+        if (xm) w[6] = v[i - 1];
+        w[7] = v[i];
+        if (xp) w[8] = v[i + 1];
+        if (yp) w[9] = v[i + nx];
+        if (xp && yp) w[10] = v[i + 1 + nx];
+        if (zp) w[11] = v[i + nxy];
+        if (xp && zp) w[12] = v[i + 1 + nxy];
+        if (yp && zp) w[13] = v[i + nx + nxy];
+        if (xp && yp && zp) w[14] = v[i + 1 + nx + nxy];
+    } else {
+        if (xm && ym) w[0] = v[i - 1 - nx];
+        if (ym) w[1] = v[i - nx];
+        if (xm) w[2] = v[i - 1];
+        w[3] = v[i];
+        if (xp) w[4] = v[i + 1];
+        if (yp) w[5] = v[i + nx];
+        if (xp && yp) w[6] = v[i + 1 + nx];
+    }
+}
+
+// Code from the candidates of gather_closed (slots in the same order).
+template <int NDIM>
+__device__ __forceinline__ uint8_t code_of_closed(const float (&w)[15]) {
+    Extremes e;
+    e.init();
+    if (NDIM == 3) {
+        constexpr uint8_t slot[15] = {13, 12, 11, 9, 10, 8, 7, kSelf, 0, 1, 3, 2, 4, 5, 6};
+#pragma unroll
+        for (int k = 0; k < 15; ++k) e.take(w[k], slot[k]);
+    } else {
+        constexpr uint8_t slot[7] = {5, 4, 3, kSelf, 0, 1, 2};
+#pragma unroll
+        for (int k = 0; k < 7; ++k) e.take(w[k], slot[k]);
+    }
+    return e.code();
+}
 
 // Code of vertex i (at x, y, z) of field v, reading neighbours from global
 // memory with bounds checks.  v is read through the coherent path (no

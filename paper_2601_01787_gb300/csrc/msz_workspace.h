@@ -38,7 +38,8 @@ struct Ctrl {
     unsigned long long counts[8]; // compare counters
     unsigned long long t_start, t_end;  // %globaltimer at kernel start / edit list written
     unsigned long long t_codes;         // ... when the codes of f were complete
-    uint32_t pad[16];
+    uint32_t uncertified;               // vertices that sweep 0 could not certify
+    uint32_t pad[15];
 };
 
 constexpr size_t kAlign = 256;
@@ -94,6 +95,8 @@ inline msz_status make_grid(const msz_grid &g, GridDev &G) {
         if (s < ns) slot_delta(g.ndim, s, dx, dy, dz);
         G.off[s] = (int32_t)((int64_t)dx + (int64_t)G.nx * dy + (int64_t)G.nxy * dz);
     }
+    G.dx = fast_div(G.nx);
+    G.dxy = fast_div(G.nxy);
     return MSZ_OK;
 }
 

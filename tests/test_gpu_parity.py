@@ -100,6 +100,13 @@ def test_correct_always_dense_bit_exact(api, case):
     assert res.stats["dense_sweeps"] == res.stats["sweeps"] + 1
 
 
+def test_correct_mixed_dense_then_worklist_bit_exact(api, case):
+    """Whole-grid scans while many vertices are distorted, then the worklist."""
+    fl, ref = case
+    res = api.correct(dev(fl.f), dev(fl.fhat), fl.xi, dense_min_items=max(1, fl.n // 16), log_capacity=100000)
+    _check_against(res, ref, fl, worklist_column=False)
+
+
 def test_correct_is_deterministic_across_calls(api, case):
     fl, ref = case
     f, fh = dev(fl.f), dev(fl.fhat)
