@@ -260,11 +260,19 @@ def test_segment_rejects_codes_outside_grid(api):
 
 
 # ------------------------------------------------------- host buffers
-def test_correct_host_matches_device(api):
-    fl = synth.perlin3d_prequant((31, 47, 70), seed=60, eb_rel=1e-4)
+@pytest.mark.parametrize("memory", ["pinned", "pageable"])
+@pytest.mark.parametrize("shape", [(31, 47, 70), (53, 91)])
+def test_correct_host_matches_oracle(api, memory, shape):
+    """Host entry point with pinned and with pageable host buffers: both give
+    the oracle's result."""
+    fl = synth.perlin3d_prequant(shape, seed=60, eb_rel=1e-4) if len(shape) == 3 else \
+        synth.perlin2d(shape, seed=61)
     ref = oracle.correct(fl.f, fl.fhat, fl.xi)
-    f = torch.from_numpy(fl.f).pin_memory()
-    fh = torch.from_numpy(fl.fhat).pin_memory()
+    if memory == "pinned":
+        f = torch.from_numpy(fl.f).pin_memory()
+        fh = torch.from_numpy(fl.fhat).pin_memory()
+    else:
+        f, fh = fl.f.copy(), fl.fhat.copy()
     res = api.correct_host(f, fh, fl.xi)
     assert res.status == ref.status
     assert np.array_equal(bits(res.out), bits(ref.g))
