@@ -315,13 +315,16 @@ def run_ours(args, ws, rank, local):
         "warmup": args.warmup, "ms_per_step": round(ms, 5), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(n) | {"parallelism": f"independent fields x{ws}" if ws > 1 else "single"},
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
-                     "algorithmic_bytes": alg, "kernel": "k_correct<3>",
+        # the kernel is bound by its ALU pipe (compare / select / min-max of
+        # the codes); the HBM figures are reported beside it
+        "roofline": {"bound": "alu", "achieved": round(alu_ach, 1), "peak": round(alu_pk, 1), "unit": "Gop/s",
+                     "frac": round(alu_ach / alu_pk, 4), "traffic": traffic, "kernel": "k_correct<3>",
+                     "ops": alu_ops, "uncertified": first.stats["uncertified"],
+                     "peak_kind": "derived: 152 SMs x 64 ALU lanes x median SM clock",
                      "kernel_ms_device": round(kernel_ms, 5)},
-        "roofline_alu": {"bound": "alu", "achieved": round(alu_ach, 1), "peak": round(alu_pk, 1), "unit": "Gop/s",
-                         "frac": round(alu_ach / alu_pk, 4), "ops": alu_ops, "uncertified": first.stats["uncertified"],
-                         "peak_kind": "derived: 152 SMs x 64 ALU lanes x median SM clock"},
+        "roofline_hbm": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
+                         "algorithmic_bytes": alg, "kernel": "k_correct<3>"},
         "verify": {"ms": round(verify_ms, 4), "codes_equal": ver["codes_equal"], "wrong_labels": ver["wrong_labels"],
                    "false_extrema": ver["fp_max"] + ver["fn_max"] + ver["fp_min"] + ver["fn_min"]},
         "rules": {"halve": {"ms": round(ms, 4), "sweeps": first.stats["sweeps"], "edits": first.stats["edits"],
