@@ -704,16 +704,17 @@ extern "C" msz_status msz_learned_features(const float *d_f, const float *d_fhat
     GridDev G;
     msz_status st = make_grid(grid, G);
     if (st != MSZ_OK) return st;
+    if (grid.ndim != 3 || ((uintptr_t)d_x & 15u)) return MSZ_ERR_INVALID_ARG;
     DeviceInfo dev;
     if ((st = current_device(dev)) != MSZ_OK) return st;
-    if (grid.ndim != 3) return MSZ_ERR_INVALID_ARG;
     k_features<<<dev.sms * 8, 256, 0, (cudaStream_t)stream>>>(d_f, d_fhat, d_codes_f, d_codes_fhat, G, xi, d_x);
     return cudaGetLastError() == cudaSuccess ? MSZ_OK : MSZ_ERR_CUDA;
 }
 
 extern "C" msz_status msz_learned_weight_image(const float *d_w, int32_t cout_real, int32_t cin_real, int32_t cin,
                                                int32_t cout, int32_t mirror, uint16_t *d_img, msz_stream_t stream) {
-    if (!d_w || !d_img || cin % 16 || cout % 16 || cin < 16 || cout < 16 || cin > 32 || cout > 32)
+    if (!d_w || !d_img || cin % 16 || cout % 16 || cin < 16 || cout < 16 || cin > 32 || cout > 32 ||
+        cout_real < 1 || cin_real < 1)
         return MSZ_ERR_INVALID_ARG;
     if (!mirror && (cout_real > cout || cin_real > cin)) return MSZ_ERR_INVALID_ARG;
     if (mirror && (cout_real > cin || cin_real > cout)) return MSZ_ERR_INVALID_ARG;
@@ -723,6 +724,17 @@ extern "C" msz_status msz_learned_weight_image(const float *d_w, int32_t cout_re
 
 extern "C" size_t msz_learned_weight_image_size(int32_t cin, int32_t cout) { return (size_t)27 * cin * cout * 2; }
 
+// Channel combinations each conv mode is built for.
+static bool conv_supported(int mode, int cin, int cout) {
+    switch (mode) {
+        case MODE_RELU:
+        case MODE_DGRAD: return (cin == 16 || cin == 32) && cout == 32;
+        case MODE_HEAD: return cin == 32 && cout == 16;
+        case MODE_RAW: return (cin == 16 && cout == 32) || (cin == 32 && (cout == 32 || cout == 16));
+    }
+    return false;
+}
+
 extern "C" msz_status msz_learned_conv(const uint16_t *d_x, int32_t cin, int32_t cout, int32_t mode, msz_grid grid,
                                        const uint16_t *d_img, const float *d_bias, uint16_t *d_out_bf16,
                                        float *d_out_f32, const uint16_t *d_mask, const float *d_f,
@@ -731,7 +743,24 @@ extern "C" msz_status msz_learned_conv(const uint16_t *d_x, int32_t cin, int32_t
     GridDev G;
     msz_status st = make_grid(grid, G);
     if (st != MSZ_OK) return st;
-    if (grid.ndim != 3 || !d_x || !d_img || !d_err) return MSZ_ERR_INVALID_ARG;
+    if (grid.ndim != 3 || !d_x || !d_img || !d_err || !conv_supported(mode, cin, cout)) return MSZ_ERR_INVALID_ARG;
+    if (((uintptr_t)d_x & 15u) || ((uintptr_t)d_img & 15u)) return MSZ_ERR_INVALID_ARG;
+    switch (mode) {
+        case MODE_RELU:
+            if (!d_bias || !d_out_bf16 || ((uintptr_t)d_out_bf16 & 15u)) return MSZ_ERR_INVALID_ARG;
+            break;
+        case MODE_DGRAD:
+            if (!d_mask || !d_out_bf16 || ((uintptr_t)d_out_bf16 & 15u) || ((uintptr_t)d_mask & 3u))
+                return MSZ_ERR_INVALID_ARG;
+            break;
+        case MODE_HEAD:
+            if (!d_bias || (!d_out_f32 && !d_g0) || (d_g0 && (!d_f || !d_fhat || !(xi >= 0.0f))))
+                return MSZ_ERR_INVALID_ARG;
+            break;
+        case MODE_RAW:
+            if (!d_out_f32 || ((uintptr_t)d_out_f32 & 15u)) return MSZ_ERR_INVALID_ARG;
+            break;
+    }
     DeviceInfo dev;
     if ((st = current_device(dev)) != MSZ_OK) return st;
     ConvParams P{};
@@ -753,27 +782,18 @@ extern "C" msz_status msz_learned_conv(const uint16_t *d_x, int32_t cin, int32_t
     const int sms = dev.sms;
     switch (mode) {
         case MODE_RELU:
-            if (!d_bias || !d_out_bf16) return MSZ_ERR_INVALID_ARG;
-            if (cin == 16 && cout == 32) return launch_conv<16, 32, MODE_RELU>(d_x, P, sms, s);
-            if (cin == 32 && cout == 32) return launch_conv<32, 32, MODE_RELU>(d_x, P, sms, s);
-            return MSZ_ERR_INVALID_ARG;
+            if (cin == 16) return launch_conv<16, 32, MODE_RELU>(d_x, P, sms, s);
+            return launch_conv<32, 32, MODE_RELU>(d_x, P, sms, s);
         case MODE_DGRAD:
-            if (!d_mask || !d_out_bf16) return MSZ_ERR_INVALID_ARG;
-            if (cin == 16 && cout == 32) return launch_conv<16, 32, MODE_DGRAD>(d_x, P, sms, s);
-            if (cin == 32 && cout == 32) return launch_conv<32, 32, MODE_DGRAD>(d_x, P, sms, s);
-            return MSZ_ERR_INVALID_ARG;
+            if (cin == 16) return launch_conv<16, 32, MODE_DGRAD>(d_x, P, sms, s);
+            return launch_conv<32, 32, MODE_DGRAD>(d_x, P, sms, s);
         case MODE_HEAD:
-            if (!d_bias || (!d_out_f32 && !d_g0) || (d_g0 && (!d_f || !d_fhat))) return MSZ_ERR_INVALID_ARG;
-            if (cin == 32 && cout == 16) return launch_conv<32, 16, MODE_HEAD>(d_x, P, sms, s);
-            return MSZ_ERR_INVALID_ARG;
-        case MODE_RAW:
-            if (!d_out_f32) return MSZ_ERR_INVALID_ARG;
-            if (cin == 16 && cout == 32) return launch_conv<16, 32, MODE_RAW>(d_x, P, sms, s);
-            if (cin == 32 && cout == 32) return launch_conv<32, 32, MODE_RAW>(d_x, P, sms, s);
-            if (cin == 32 && cout == 16) return launch_conv<32, 16, MODE_RAW>(d_x, P, sms, s);
-            return MSZ_ERR_INVALID_ARG;
+            return launch_conv<32, 16, MODE_HEAD>(d_x, P, sms, s);
+        default:
+            if (cin == 16) return launch_conv<16, 32, MODE_RAW>(d_x, P, sms, s);
+            if (cout == 32) return launch_conv<32, 32, MODE_RAW>(d_x, P, sms, s);
+            return launch_conv<32, 16, MODE_RAW>(d_x, P, sms, s);
     }
-    return MSZ_ERR_INVALID_ARG;
 }
 
 extern "C" msz_status msz_learned_head_grad(const float *d_z, const float *d_target, int64_t n, float scale,
@@ -804,14 +824,16 @@ extern "C" msz_status msz_learned_wgrad(const uint16_t *d_x, int32_t cin, const 
     msz_status st = make_grid(grid, G);
     if (st != MSZ_OK) return st;
     if (grid.ndim != 3 || !d_x || !d_dz || !d_dw || !d_db) return MSZ_ERR_INVALID_ARG;
+    const bool shape_ok = (cin == 16 && cout == 32) || (cin == 32 && (cout == 32 || cout == 16));
+    if (!shape_ok || cin_real < 1 || cin_real > cin || cout_real < 1 || cout_real > cout) return MSZ_ERR_INVALID_ARG;
+    if (((uintptr_t)d_x & 15u) || ((uintptr_t)d_dz & 15u)) return MSZ_ERR_INVALID_ARG;
     DeviceInfo dev;
     if ((st = current_device(dev)) != MSZ_OK) return st;
     const int blocks = dev.sms * 2;
     cudaStream_t s = (cudaStream_t)stream;
-    if (cin == 16 && cout == 32) return launch_wgrad<16, 32>(d_x, d_dz, G, cin_real, cout_real, d_dw, d_db, blocks, s);
-    if (cin == 32 && cout == 32) return launch_wgrad<32, 32>(d_x, d_dz, G, cin_real, cout_real, d_dw, d_db, blocks, s);
-    if (cin == 32 && cout == 16) return launch_wgrad<32, 16>(d_x, d_dz, G, cin_real, cout_real, d_dw, d_db, blocks, s);
-    return MSZ_ERR_INVALID_ARG;
+    if (cin == 16) return launch_wgrad<16, 32>(d_x, d_dz, G, cin_real, cout_real, d_dw, d_db, blocks, s);
+    if (cout == 32) return launch_wgrad<32, 32>(d_x, d_dz, G, cin_real, cout_real, d_dw, d_db, blocks, s);
+    return launch_wgrad<32, 16>(d_x, d_dz, G, cin_real, cout_real, d_dw, d_db, blocks, s);
 }
 
 extern "C" msz_status msz_learned_adam(float *d_p, const float *d_g, float *d_m, float *d_v, int64_t n, float lr,

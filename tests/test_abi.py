@@ -70,3 +70,40 @@ def test_invalid_arguments_rejected_on_host():
     st = lib.msz_correct(fake, fake, ctypes.c_float(0.1), g, fake, None, None, 0, ctypes.byref(cnt),
                          ctypes.byref(bad_hook), None, fake, 1 << 30, None)
     assert st == api.ERR_INVALID_ARG
+
+
+def test_learned_arguments_rejected_on_host():
+    """The learned entry points check channels, modes, pointers and alignment
+    before any CUDA call."""
+    from paper_2601_01787_gb300 import api, learned
+    lib = learned.lib()
+    g3 = api.grid_of((4, 5, 130))
+    g2 = api.grid_of((5, 130))
+    a = ctypes.c_void_p(1 << 20)      # 16-byte aligned, never dereferenced
+    odd = ctypes.c_void_p((1 << 20) + 8)
+    F = ctypes.c_float
+    conv = lib.msz_learned_conv
+    ok_args = dict(x=a, cin=32, cout=32, mode=learned.MODE_RELU, grid=g3, img=a, bias=a, ob=a, of=None, mask=None)
+
+    def call(**kw):
+        d = dict(ok_args, **kw)
+        return conv(d["x"], d["cin"], d["cout"], d["mode"], d["grid"], d["img"], d["bias"], d["ob"], d["of"],
+                    d["mask"], None, None, F(0.0), 0, None, a, None)
+
+    assert call(cin=8) == api.ERR_INVALID_ARG                       # unsupported channels
+    assert call(cout=16) == api.ERR_INVALID_ARG                     # ReLU layers have 32 outputs
+    assert call(mode=7) == api.ERR_INVALID_ARG                      # unknown mode
+    assert call(grid=g2) == api.ERR_INVALID_ARG                     # 3D only
+    assert call(x=odd) == api.ERR_INVALID_ARG                       # TMA needs 16-byte alignment
+    assert call(bias=None) == api.ERR_INVALID_ARG
+    assert call(mode=learned.MODE_DGRAD) == api.ERR_INVALID_ARG     # no mask
+    assert call(mode=learned.MODE_HEAD, cout=16) == api.ERR_INVALID_ARG  # neither r nor g0 requested
+    assert call(mode=learned.MODE_RAW, ob=None) == api.ERR_INVALID_ARG   # no FP32 output
+    w = lib.msz_learned_wgrad
+    assert w(a, 16, a, 16, g3, 16, 16, a, a, None) == api.ERR_INVALID_ARG   # 16 -> 16 is not a layer
+    assert w(a, 32, a, 32, g3, 33, 32, a, a, None) == api.ERR_INVALID_ARG   # more real than padded channels
+    assert lib.msz_learned_weight_image(a, 0, 32, 32, 32, 0, a, None) == api.ERR_INVALID_ARG
+    assert lib.msz_learned_weight_image(a, 32, 32, 32, 48, 0, a, None) == api.ERR_INVALID_ARG
+    assert lib.msz_learned_features(a, a, F(1e-3), g2, a, a, a, None) == api.ERR_INVALID_ARG
+    assert lib.msz_learned_adam(a, a, a, a, 10, F(1e-3), F(0.9), F(0.999), F(1e-8), 0, None) == api.ERR_INVALID_ARG
+    assert int(lib.msz_learned_weight_image_size(32, 16)) == 27 * 32 * 16 * 2
