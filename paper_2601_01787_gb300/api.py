@@ -324,6 +324,46 @@ class BatchResult:
     fields: list  # CorrectResult per field
 
 
+def _batch_fields(fs, fhats, xis, edit_capacities, outs, tile_z):
+    """The msz_field array of a batch and the output buffers it points to."""
+    n = len(fs)
+    arr = (Field * n)()
+    keep = []
+    for k in range(n):
+        f, fh = fs[k], fhats[k]
+        assert f.dtype == torch.float32 and fh.dtype == torch.float32 and f.shape == fh.shape and f.dim() == 3
+        cap = f.numel() if edit_capacities is None else int(edit_capacities[k])
+        out = torch.empty_like(f) if outs is None else outs[k]
+        idx = torch.empty(max(cap, 1), dtype=torch.int32, device=f.device)
+        dl = torch.empty(max(cap, 1), dtype=torch.float32, device=f.device)
+        keep.append((out, idx, dl, cap))
+        tz = 0 if tile_z is None else int(tile_z[k])
+        arr[k] = Field(_dptr(f), _dptr(fh), ctypes.c_float(np.float32(xis[k])), -1, grid_of(f.shape), _dptr(out),
+                       _dptr(idx), _dptr(dl), cap, 0, Stats(), tz, 0)
+    return arr, keep
+
+
+def _batch_workspace(lib, arr, max_sweeps, ws, device):
+    need = int(lib.msz_batch_workspace_size(len(arr), arr, int(max_sweeps)))
+    if need == 0:
+        raise MszError(ERR_INVALID_ARG, "msz_batch_workspace_size")
+    return workspace(need, device) if ws is None else ws
+
+
+def _batch_results(arr, keep, log, log_capacity, status) -> "BatchResult":
+    results = []
+    for k in range(len(arr)):
+        out, idx, dl, cap = keep[k]
+        fk = arr[k]
+        m = min(int(fk.edit_count), cap)
+        stats = fk.stats.as_dict()
+        nlog = min(stats["sweeps"] + 1, log_capacity)
+        lg = log[4 * k * log_capacity:4 * (k * log_capacity + nlog)].reshape(-1, 4).copy() if log_capacity else \
+            np.zeros((0, 4), np.int64)
+        results.append(CorrectResult(int(fk.status), out, idx[:m], dl[:m], int(fk.edit_count), stats, lg))
+    return BatchResult(int(status), results)
+
+
 class BatchPlan:
     """A prepared batch (msz_batch_plan_create): launch() is asynchronous and
     can be captured in a CUDA graph; collect() synchronizes and returns the
@@ -332,33 +372,21 @@ class BatchPlan:
     def __init__(self, fs, fhats, xis, *, rule="halve", max_sweeps: int = 0, dense_min_items: int = 0,
                  edit_capacities=None, outs=None, ws: torch.Tensor | None = None, stream=None, tile_z=None):
         lib = load()
-        n = len(fs)
-        arr = (Field * n)()
-        keep = []
-        for k in range(n):
-            f, fh = fs[k], fhats[k]
-            assert f.dtype == torch.float32 and fh.dtype == torch.float32 and f.shape == fh.shape and f.dim() == 3
-            cap = f.numel() if edit_capacities is None else int(edit_capacities[k])
-            out = torch.empty_like(f) if outs is None else outs[k]
-            idx = torch.empty(max(cap, 1), dtype=torch.int32, device=f.device)
-            dl = torch.empty(max(cap, 1), dtype=torch.float32, device=f.device)
-            keep.append((out, idx, dl, cap))
-            tz = 0 if tile_z is None else int(tile_z[k])
-            arr[k] = Field(_dptr(f), _dptr(fh), ctypes.c_float(np.float32(xis[k])), -1, grid_of(f.shape),
-                           _dptr(out), _dptr(idx), _dptr(dl), cap, 0, Stats(), tz, 0)
-        need = int(lib.msz_batch_workspace_size(n, arr, int(max_sweeps)))
-        if need == 0:
-            raise MszError(ERR_INVALID_ARG, "msz_batch_workspace_size")
-        if ws is None:
-            ws = workspace(need, fs[0].device)
+        arr, keep = _batch_fields(fs, fhats, xis, edit_capacities, outs, tile_z)
+        ws = _batch_workspace(lib, arr, max_sweeps, ws, fs[0].device)
         opt, _ = _options(rule, max_sweeps, dense_min_items, None, 0)
         handle = ctypes.c_void_p()
-        st = lib.msz_batch_plan_create(n, arr, ctypes.byref(opt), _dptr(ws), ws.numel(), _stream(stream),
+        st = lib.msz_batch_plan_create(len(arr), arr, ctypes.byref(opt), _dptr(ws), ws.numel(), _stream(stream),
                                        ctypes.byref(handle))
         if st != OK:
             raise MszError(st, "msz_batch_plan_create")
-        self._lib, self._h, self.n, self.arr = lib, handle, n, arr
+        self._lib, self._h, self.n, self.arr = lib, handle, len(arr), arr
         self._keep = (list(fs), list(fhats), keep, ws, opt)
+
+    @property
+    def outputs(self):
+        """(out, edit_idx, edit_delta, capacity) of every field."""
+        return self._keep[2]
 
     def launch(self, stream=None) -> None:
         st = self._lib.msz_batch_launch(self._h, _stream(stream))
@@ -369,17 +397,7 @@ class BatchPlan:
         log = np.zeros(max(4 * self.n * log_capacity, 4), dtype=np.int64)
         st = self._lib.msz_batch_collect(self._h, self.arr, log.ctypes.data if log_capacity else None,
                                          int(log_capacity), _stream(stream))
-        results = []
-        for k in range(self.n):
-            out, idx, dl, cap = self._keep[2][k]
-            fk = self.arr[k]
-            m = min(int(fk.edit_count), cap)
-            stats = fk.stats.as_dict()
-            nlog = min(stats["sweeps"] + 1, log_capacity)
-            lg = log[4 * k * log_capacity:4 * (k * log_capacity + nlog)].reshape(-1, 4).copy() if log_capacity \
-                else np.zeros((0, 4), np.int64)
-            results.append(CorrectResult(int(fk.status), out, idx[:m], dl[:m], int(fk.edit_count), stats, lg))
-        return BatchResult(int(st), results)
+        return _batch_results(self.arr, self._keep[2], log, log_capacity, st)
 
     def graph(self, stream=None) -> "torch.cuda.CUDAGraph":
         """Capture one launch in a CUDA graph; replay() then reruns the whole
@@ -409,37 +427,10 @@ def correct_batch(fs, fhats, xis, *, rule="halve", max_sweeps: int = 0, dense_mi
                   stream=None, tile_z=None) -> BatchResult:
     """msz_correct_batch: many 3D fields (CUDA tensors) in one persistent launch."""
     lib = load()
-    n = len(fs)
-    arr = (Field * n)()
-    keep = []
-    for k in range(n):
-        f, fh = fs[k], fhats[k]
-        assert f.dtype == torch.float32 and fh.dtype == torch.float32 and f.shape == fh.shape and f.dim() == 3
-        cap = f.numel() if edit_capacities is None else int(edit_capacities[k])
-        out = torch.empty_like(f) if outs is None else outs[k]
-        idx = torch.empty(max(cap, 1), dtype=torch.int32, device=f.device)
-        dl = torch.empty(max(cap, 1), dtype=torch.float32, device=f.device)
-        keep.append((out, idx, dl, cap))
-        tz = 0 if tile_z is None else int(tile_z[k])
-        arr[k] = Field(_dptr(f), _dptr(fh), ctypes.c_float(np.float32(xis[k])), -1, grid_of(f.shape), _dptr(out),
-                       _dptr(idx), _dptr(dl), cap, 0, Stats(), tz, 0)
-    need = int(lib.msz_batch_workspace_size(n, arr, int(max_sweeps)))
-    if need == 0:
-        raise MszError(ERR_INVALID_ARG, "msz_batch_workspace_size")
-    if ws is None:
-        ws = workspace(need, fs[0].device)
+    arr, keep = _batch_fields(fs, fhats, xis, edit_capacities, outs, tile_z)
+    ws = _batch_workspace(lib, arr, max_sweeps, ws, fs[0].device)
     opt, _ = _options(rule, max_sweeps, dense_min_items, None, 0)
-    log = np.zeros(max(4 * n * log_capacity, 4), dtype=np.int64)
-    st = lib.msz_correct_batch(n, arr, ctypes.byref(opt), log.ctypes.data if log_capacity else None, log_capacity,
-                               _dptr(ws), ws.numel(), _stream(stream))
-    results = []
-    for k in range(n):
-        out, idx, dl, cap = keep[k]
-        fk = arr[k]
-        m = min(int(fk.edit_count), cap)
-        stats = fk.stats.as_dict()
-        nlog = min(stats["sweeps"] + 1, log_capacity)
-        lg = log[4 * k * log_capacity:4 * (k * log_capacity + nlog)].reshape(-1, 4).copy() if log_capacity else \
-            np.zeros((0, 4), np.int64)
-        results.append(CorrectResult(int(fk.status), out, idx[:m], dl[:m], int(fk.edit_count), stats, lg))
-    return BatchResult(int(st), results)
+    log = np.zeros(max(4 * len(arr) * log_capacity, 4), dtype=np.int64)
+    st = lib.msz_correct_batch(len(arr), arr, ctypes.byref(opt), log.ctypes.data if log_capacity else None,
+                               log_capacity, _dptr(ws), ws.numel(), _stream(stream))
+    return _batch_results(arr, keep, log, log_capacity, st)

@@ -113,7 +113,7 @@ def test_batch_graph_replay_matches_oracle(api):
     graph = plan.graph()
     refs = [oracle.correct(fl.f, fl.fhat, fl.xi, log_capacity=4096) for fl in fields]
     for rep in range(3):
-        for r in plan._keep[2]:
+        for r in plan.outputs:
             r[0].fill_(float("nan"))  # the replay must rewrite every output
         graph.replay()
         res = plan.collect(log_capacity=4096)
