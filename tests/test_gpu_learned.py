@@ -392,3 +392,19 @@ def test_trained_proposal_cuts_sweeps(L):
     g = lr.result.out
     xi = float(fl.xi)
     assert bool(((g.double() - f.double()).abs() <= xi).all())
+
+
+def test_learned_fallback_runs_the_plain_loop(L):
+    """When the loop from the proposal ends without a correct field (here: at
+    a one-sweep cap), the plain loop from fhat runs and its result is
+    returned, with the fallback recorded."""
+    from paper_2601_01787_gb300 import api
+    fl = synth.peaks3d((24, 40, 130), seed=81, eb_rel=1e-4)
+    f, fh = torch.from_numpy(fl.f).cuda(), torch.from_numpy(fl.fhat).cuda()
+    net = L.ProposalNet(seed=2)
+    lr = L.correct_learned(f, fh, float(fl.xi), net, max_sweeps=1)
+    assert lr.from_g0.status == api.ERR_MAX_SWEEPS
+    assert lr.fallback
+    plain = api.correct(f, fh, float(fl.xi), max_sweeps=1)
+    assert lr.result.status == plain.status
+    assert torch.equal(lr.result.out.view(torch.int32), plain.out.view(torch.int32))
