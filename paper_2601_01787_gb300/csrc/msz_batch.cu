@@ -68,12 +68,14 @@ struct BatchProblem {
     FieldRes *res;
     uint32_t *bsum;
     uint32_t max_sweeps;
-    long long dense_min;
+    long long dense_min;             // > 0: one threshold for the whole batch; < 0: never dense
+    uint32_t per_field_dense;        // 1: each field by its own count (6 x distorted >= n / 16)
     uint32_t *tb, *dm[2], *eb, *ub;  // shared bitmaps (global words)
+    const uint8_t *bfield;           // field of each 1024-vertex block
 };
 
 struct BatchLayout {
-    size_t ctrl, fields, log, res, bsum, tb, d0, d1, eb, ub, codes, total, zero_bytes;
+    size_t ctrl, fields, log, res, bsum, tb, d0, d1, eb, ub, codes, bfield, total, zero_bytes;
 };
 
 BatchLayout batch_layout(uint32_t nfields, uint64_t ntot, uint32_t max_sweeps) {
@@ -92,9 +94,15 @@ BatchLayout batch_layout(uint32_t nfields, uint64_t ntot, uint32_t max_sweeps) {
     L.zero_bytes = o;
     L.fields = o; o = align_up(o + nfields * sizeof(FieldDev));
     L.codes = o;  o = align_up(o + ntot);
+    L.bfield = o; o = align_up(o + ntot / 1024);
     L.total = o;
     return L;
 }
+
+// Field of vertex v of the shared space: field bases are 1024-aligned, so one
+// byte per 1024 vertices names it.
+static_assert(MSZ_BATCH_MAX_FIELDS <= 256, "field indices are stored in one byte");
+__device__ __forceinline__ uint32_t field_of(const uint8_t *bfield, uint32_t v) { return __ldg(&bfield[v >> 10]); }
 
 // Field of a vertex (or tile) of the shared space: the last k with tab[k] <= v.
 __device__ __forceinline__ uint32_t find_field(const uint32_t *tab, uint32_t n, uint32_t v) {
@@ -130,7 +138,7 @@ template <class Alive>
 __device__ __forceinline__ void detect_pair(const BatchProblem &P, const uint32_t *s_base, uint32_t nf,
                                             uint32_t (*s_cnt)[4], uint32_t next_parity, Alive &&alive, bool h1,
                                             uint32_t v1, bool h2, uint32_t v2) {
-    const uint32_t f1 = h1 ? find_field(s_base, nf, v1) : 0u, f2 = h2 ? find_field(s_base, nf, v2) : 0u;
+    const uint32_t f1 = h1 ? field_of(P.bfield, v1) : 0u, f2 = h2 ? field_of(P.bfield, v2) : 0u;
     const bool l1 = h1 && alive(f1), l2 = h2 && alive(f2);
     const FieldView &F1 = P.fields[f1].F;
     const FieldView &F2 = P.fields[f2].F;
@@ -154,6 +162,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
     __shared__ uint32_t s_tile[MSZ_BATCH_MAX_FIELDS + 1];
     __shared__ uint32_t s_cnt[MSZ_BATCH_MAX_FIELDS][4];
     __shared__ uint32_t s_alive[(MSZ_BATCH_MAX_FIELDS + 31) / 32];
+    __shared__ uint32_t s_dense[(MSZ_BATCH_MAX_FIELDS + 31) / 32];  // next sweep scans the field whole
     __shared__ uint32_t s_next;
     __shared__ unsigned long long s_sum;
     __shared__ uint32_t sm[40];
@@ -230,7 +239,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
             uint32_t nt = 0;
             walk_bits<true>(P.tb, nullptr, P.all, nt, [&](bool has, uint32_t t) {
                 if (has) {
-                    const uint32_t f = find_field(s_base, nf, t);
+                    const uint32_t f = field_of(P.bfield, t);
                     if (alive(f)) atomicAdd(&s_cnt[f][2], 1u);
                 }
             });
@@ -239,17 +248,31 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
             ok = grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
             break;
         }
-        const bool dense_next = P.dense_min >= 0 && m_tot * kDenseFactorB >= (unsigned long long)P.dense_min;
+        // whole-field scans for the next sweep: per field, or one verdict for all
+        const bool all_dense = !P.per_field_dense && P.dense_min >= 0 &&
+                               m_tot * kDenseFactorB >= (unsigned long long)P.dense_min;
+        for (uint32_t w = threadIdx.x; w < (nf + 31) / 32; w += blockDim.x) s_dense[w] = 0u;
+        __syncthreads();
+        for (uint32_t f = threadIdx.x; f < nf; f += blockDim.x) {
+            if (!alive(f)) continue;
+            const unsigned long long nfv = P.fields[f].F.G.n;
+            const bool d = P.per_field_dense
+                               ? (unsigned long long)ld_relaxed(&rec[f].distorted) * kDenseFactorB * 16ull >= nfv
+                               : all_dense;
+            if (d) atomicOr(&s_dense[f >> 5], 1u << (f & 31u));
+        }
+        __syncthreads();
+        auto dense_f = [&](uint32_t f) { return ((s_dense[f >> 5] >> (f & 31u)) & 1u) != 0u; };
         // ---- edit phase of sweep k
         {
             uint32_t targets = 0;
             walk_bits<true>(P.tb, nullptr, P.all, targets, [&](bool has, uint32_t t) {
                 if (!has) return;
-                const uint32_t f = find_field(s_base, nf, t);
+                const uint32_t f = field_of(P.bfield, t);
                 if (!alive(f)) return;
                 const FieldView &F = P.fields[f].F;
                 atomicAdd(&s_cnt[f][2], 1u);
-                if (apply_target<3>(F, t - s_base[f], dense_next, F.dm[(k + 1) & 1])) atomicAdd(&s_cnt[f][3], 1u);
+                if (apply_target<3>(F, t - s_base[f], dense_f(f), F.dm[(k + 1) & 1])) atomicAdd(&s_cnt[f][3], 1u);
             });
             (void)targets;
             flush_counts(s_cnt, nf, rec);
@@ -271,35 +294,32 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
         const uint32_t k1 = k + 1;
         BatchRec *rec1 = P.log + (size_t)k1 * nf;
         uint32_t *dcur = P.dm[k1 & 1];
-        if (dense_next) {
+        {
             const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-            for (uint32_t w = gtid; w < P.all.words; w += stride) dcur[w] = 0;
             for (uint32_t f = gtid; f < nf; f += stride)
-                if (alive(f)) {
+                if (alive(f) && dense_f(f)) {
                     rec1[f].worklist = P.fields[f].F.G.n;
                     rec1[f].dense = 1;
                 }
-            uint32_t seen = 0;
-            walk_bits_pairs<false>(P.ub, nullptr, P.all, seen, [&](bool h1, uint32_t v1, bool h2, uint32_t v2) {
-                detect_pair(P, s_base, nf, s_cnt, (k1 + 1) & 1, alive, h1, v1, h2, v2);
-            });
-        } else {
-            const uint32_t lane = lane_id();
-            const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-            const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-            // worklist sizes per field (each bitmap word belongs to one field)
-            for (uint32_t base = gw * 32u; base < P.all.words; base += nw * 32u) {
-                const uint32_t wi = base + lane;
-                const uint32_t bits = wi < P.all.words ? dcur[wi] : 0u;
-                if (bits) {
-                    const uint32_t f = find_field(s_base, nf, wi * 32u);
-                    if (alive(f)) atomicAdd(&s_cnt[f][0], (uint32_t)__popc(bits));
-                }
-            }
-            uint32_t seen = 0;
-            walk_bits_pairs<true>(dcur, P.ub, P.all, seen, [&](bool h1, uint32_t v1, bool h2, uint32_t v2) {
-                detect_pair(P, s_base, nf, s_cnt, (k1 + 1) & 1, alive, h1, v1, h2, v2);
-            });
+            // per word: a whole-scan field examines its uncertified vertices, a
+            // worklist field those of its worklist; done fields none.  The
+            // worklist is cleared as it is read (a word never straddles two
+            // fields: bases are 1024-aligned).
+            walk_words_pairs(
+                P.all,
+                [&](uint32_t wi) -> uint32_t {
+                    const uint32_t f = field_of(P.bfield, wi * 32u);
+                    const uint32_t wl = dcur[wi];
+                    if (wl) dcur[wi] = 0u;
+                    if (!alive(f)) return 0u;
+                    if (dense_f(f)) return P.ub[wi];
+                    if (!wl) return 0u;
+                    atomicAdd(&s_cnt[f][0], (uint32_t)__popc(wl));
+                    return wl & P.ub[wi];
+                },
+                [&](bool h1, uint32_t v1, bool h2, uint32_t v2) {
+                    detect_pair(P, s_base, nf, s_cnt, (k1 + 1) & 1, alive, h1, v1, h2, v2);
+                });
         }
         flush_counts(s_cnt, nf, rec1);
         ok = grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
@@ -315,7 +335,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
     for (uint32_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) {
         const uint32_t c = __popc(P.eb[w]);
         cnt += c;
-        if (c) atomicAdd(&s_cnt[find_field(s_base, nf, w * 32u)][0], c);
+        if (c) atomicAdd(&s_cnt[field_of(P.bfield, w * 32u)][0], c);
     }
     uint32_t tot;
     block_exclusive_scan(cnt, sm, tot);
@@ -346,7 +366,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
         uint32_t rt;
         const uint32_t ex = block_exclusive_scan((uint32_t)__popc(word), sm, rt);
         if (word) {
-            const uint32_t f = find_field(s_base, nf, w * 32u);
+            const uint32_t f = field_of(P.bfield, w * 32u);
             const FieldDev &D = P.fields[f];
             unsigned long long pos = (unsigned long long)(prefix + ex) - s_tile[f];
             uint32_t bits = word;
@@ -523,19 +543,28 @@ extern "C" msz_status msz_batch_plan_create(int32_t n, const msz_field *fields, 
     P.res = (FieldRes *)(ws + L.res);
     P.bsum = (uint32_t *)(ws + L.bsum);
     P.max_sweeps = max_sweeps;
-    // default: whole-grid scans while 6 x distorted >= N/16 (measured faster
-    // than the worklist for the many small fields of a batch)
+    // default: every field scans whole while 6 x (all fields' distorted
+    // vertices) >= N / 16 (measured faster here than deciding per field)
     P.dense_min = o.dense_min_items == 0 ? (long long)(ntot / 16 > 0 ? ntot / 16 : 1) : (long long)o.dense_min_items;
+    P.per_field_dense = 0u;
     P.tb = (uint32_t *)(ws + L.tb);
     P.dm[0] = (uint32_t *)(ws + L.d0);
     P.dm[1] = (uint32_t *)(ws + L.d1);
     P.eb = (uint32_t *)(ws + L.eb);
     P.ub = (uint32_t *)(ws + L.ub);
+    P.bfield = (const uint8_t *)(ws + L.bfield);
+    std::vector<uint8_t> bfield(ntot / 1024, 0);
+    for (int32_t k = 0; k < n; ++k)
+        for (uint64_t b = bases[k] / 1024; b < (bases[k] + (uint64_t)grids[k].n + 1023) / 1024; ++b)
+            bfield[b] = (uint8_t)k;
     int blocks = 0;
     if ((st = batch_blocks(dev, blocks)) != MSZ_OK) return st;
     // the descriptor table is uploaded once; launches only clear the control
     // block and bitmaps, so a captured launch can be replayed
     if (cudaMemcpyAsync(ws + L.fields, tab.data(), n * sizeof(FieldDev), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return MSZ_ERR_CUDA;
+    if (!bfield.empty() &&
+        cudaMemcpyAsync(ws + L.bfield, bfield.data(), bfield.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
         return MSZ_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return MSZ_ERR_CUDA;
     msz_batch_plan *p = new (std::nothrow) msz_batch_plan;

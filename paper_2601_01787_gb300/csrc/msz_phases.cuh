@@ -109,10 +109,15 @@ __device__ __forceinline__ void walk_bits(uint32_t *bm, const uint32_t *filter, 
 
 // walk_bits for detection: two vertices per lane per step (two dense words,
 // or two bits of a lane's sparse word), so that each lane has the neighbour
-// loads of both in flight at once.  fn(has1, v1, has2, v2).
-template <bool CLEAR, class F>
+// loads of both in flight at once.  fn(has1, v1, has2, v2).  word_ok(w)
+// false drops word w (after counting it in `seen`).
+struct AllWords {
+    __device__ __forceinline__ bool operator()(uint32_t) const { return true; }
+};
+
+template <bool CLEAR, class F, class W = AllWords>
 __device__ __forceinline__ void walk_bits_pairs(uint32_t *bm, const uint32_t *filter, const GridDev &G,
-                                                uint32_t &seen, F &&fn) {
+                                                uint32_t &seen, F &&fn, W word_ok = W()) {
     const uint32_t lane = lane_id();
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
@@ -124,7 +129,51 @@ __device__ __forceinline__ void walk_bits_pairs(uint32_t *bm, const uint32_t *fi
             if (CLEAR && bits) bm[wi] = 0u;
             seen += (uint32_t)__popc(bits);
             if (filter && bits) bits &= filter[wi];
+            if (bits && !word_ok(wi)) bits = 0u;
         }
+        const bool dense = __popc(bits) >= kDenseWord;
+        uint32_t dm = __ballot_sync(kFull, dense);
+        while (dm) {
+            const int j1 = __ffs(dm) - 1;
+            dm &= dm - 1u;
+            const uint32_t w1 = __shfl_sync(kFull, bits, j1);
+            int j2 = -1;
+            if (dm) {
+                j2 = __ffs(dm) - 1;
+                dm &= dm - 1u;
+            }
+            const uint32_t w2 = __shfl_sync(kFull, bits, j2 < 0 ? 0 : j2);
+            fn(((w1 >> lane) & 1u) != 0u, (base + (uint32_t)j1) * 32u + lane,
+               j2 >= 0 && ((w2 >> lane) & 1u) != 0u, (base + (uint32_t)(j2 < 0 ? 0 : j2)) * 32u + lane);
+        }
+        if (dense) bits = 0u;
+        while (__any_sync(kFull, bits != 0u)) {
+            const bool h1 = bits != 0u;
+            uint32_t v1 = 0, v2 = 0;
+            if (h1) {
+                v1 = wi * 32u + (uint32_t)(__ffs(bits) - 1);
+                bits &= bits - 1u;
+            }
+            const bool h2 = bits != 0u;
+            if (h2) {
+                v2 = wi * 32u + (uint32_t)(__ffs(bits) - 1);
+                bits &= bits - 1u;
+            }
+            fn(h1, v1, h2, v2);
+        }
+    }
+}
+
+// Like walk_bits_pairs, with the bits of word w supplied by load_word(w)
+// (which may read, clear and count whatever it needs).
+template <class LW, class F>
+__device__ __forceinline__ void walk_words_pairs(const GridDev &G, LW &&load_word, F &&fn) {
+    const uint32_t lane = lane_id();
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t base = gw * 32u; base < G.words; base += nw * 32u) {
+        const uint32_t wi = base + lane;
+        uint32_t bits = wi < G.words ? load_word(wi) : 0u;
         const bool dense = __popc(bits) >= kDenseWord;
         uint32_t dm = __ballot_sync(kFull, dense);
         while (dm) {
