@@ -179,11 +179,13 @@ msz_status msz_segment(const uint8_t *d_codes, msz_grid grid, int32_t *d_min_lab
 /* Sec. V-C verification counts between the segmentations of f and g:
  * h_counts[0] wrongly labelled vertices (either label differs), [1] false
  * positive maxima (maximum in g only), [2] false negative maxima, [3] false
- * positive minima, [4] false negative minima.  All device arrays hold n
- * entries.  Workspace: at least MSZ_SMALL_WORKSPACE bytes.  Synchronizes `stream`. */
+ * positive minima, [4] false negative minima, and [5] vertices whose code
+ * differs (the loop's stopping condition, Sec. IV-A).  All device arrays hold
+ * n entries.  Workspace: at least MSZ_SMALL_WORKSPACE bytes.  Synchronizes
+ * `stream`. */
 msz_status msz_compare(const uint8_t *d_codes_f, const uint8_t *d_codes_g, const int32_t *d_min_f,
                        const int32_t *d_max_f, const int32_t *d_min_g, const int32_t *d_max_g, int64_t n,
-                       int64_t h_counts[5], void *d_workspace, size_t workspace_bytes, msz_stream_t stream);
+                       int64_t h_counts[6], void *d_workspace, size_t workspace_bytes, msz_stream_t stream);
 
 /* One field of a batch (msz_correct_batch).  Inputs: d_f, d_fhat, xi, grid
  * (ndim 3), d_out and the edit-list arrays as in msz_correct.  Outputs, written

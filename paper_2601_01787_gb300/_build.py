@@ -8,6 +8,7 @@ change.
 from __future__ import annotations
 
 import hashlib
+import re
 import os
 import shutil
 import subprocess
@@ -59,10 +60,18 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def _code_only(text: bytes) -> bytes:
+    """Source text without C/C++ comments and with whitespace collapsed."""
+    t = re.sub(rb"/\*.*?\*/", b" ", text, flags=re.S)
+    t = re.sub(rb"//[^\n]*", b" ", t)
+    return re.sub(rb"\s+", b" ", t).strip()
+
+
 def unit_hash(unit: str) -> str:
-    """Hash of one translation unit, every header it can include and its
-    flags: identifies the kernels of that unit a profile was taken of (a
-    change to another unit leaves it unchanged)."""
+    """Hash of the code (comments and layout ignored) of one translation
+    unit, every header it can include and its flags: identifies the kernels
+    of that unit a profile was taken of (a change to another unit, or to a
+    comment, leaves it unchanged)."""
     h = hashlib.sha256()
     names = [unit] + sorted(n for n in os.listdir(CSRC) if n.endswith((".cuh", ".h"))) + ["../../include/msz.h"]
     for name in names:
@@ -70,7 +79,7 @@ def unit_hash(unit: str) -> str:
         if os.path.isfile(p):
             h.update(name.encode())
             with open(p, "rb") as fh:
-                h.update(fh.read())
+                h.update(_code_only(fh.read()))
     flags = [u for u in UNITS if (u[0] if isinstance(u, (tuple, list)) else u) == unit]
     h.update(repr(([c for c in COMMON if not c.startswith("/")], flags)).encode())
     return h.hexdigest()[:16]

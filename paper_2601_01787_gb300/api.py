@@ -297,15 +297,17 @@ def segment(codes: torch.Tensor, ws: torch.Tensor | None = None, stream=None):
 
 
 def compare(codes_f, codes_g, min_f, max_f, min_g, max_g, ws: torch.Tensor | None = None, stream=None) -> dict:
-    """Wrong labels and false extrema between two segmentations (msz_compare)."""
-    counts = (ctypes.c_int64 * 5)()
+    """Wrong labels, false extrema and code mismatches between two fields'
+    codes and segmentations (msz_compare)."""
+    counts = (ctypes.c_int64 * 6)()
     if ws is None:
         ws = workspace(SMALL_WORKSPACE, codes_f.device)
     st = load().msz_compare(_dptr(codes_f), _dptr(codes_g), _dptr(min_f), _dptr(max_f), _dptr(min_g),
                             _dptr(max_g), codes_f.numel(), counts, _dptr(ws), ws.numel(), _stream(stream))
     if st != OK:
         raise MszError(st, "msz_compare")
-    return dict(wrong_labels=counts[0], fp_max=counts[1], fn_max=counts[2], fp_min=counts[3], fn_min=counts[4])
+    return dict(wrong_labels=counts[0], fp_max=counts[1], fn_max=counts[2], fp_min=counts[3], fn_min=counts[4],
+                code_mismatches=counts[5])
 
 
 def verify(f: torch.Tensor, g: torch.Tensor) -> dict:
@@ -314,7 +316,7 @@ def verify(f: torch.Tensor, g: torch.Tensor) -> dict:
     mf, Mf = segment(cf)
     mg, Mg = segment(cg)
     res = compare(cf, cg, mf, Mf, mg, Mg)
-    res["codes_equal"] = bool(torch.equal(cf, cg))
+    res["codes_equal"] = res["code_mismatches"] == 0
     return res
 
 

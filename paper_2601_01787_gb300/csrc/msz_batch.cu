@@ -68,8 +68,7 @@ struct BatchProblem {
     FieldRes *res;
     uint32_t *bsum;
     uint32_t max_sweeps;
-    long long dense_min;             // > 0: one threshold for the whole batch; < 0: never dense
-    uint32_t per_field_dense;        // 1: each field by its own count (6 x distorted >= n / 16)
+    long long dense_min;             // < 0: never scan whole fields after sweep 0
     uint32_t *tb, *dm[2], *eb, *ub;  // shared bitmaps (global words)
     const uint8_t *bfield;           // field of each 1024-vertex block
 };
@@ -162,7 +161,6 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
     __shared__ uint32_t s_tile[MSZ_BATCH_MAX_FIELDS + 1];
     __shared__ uint32_t s_cnt[MSZ_BATCH_MAX_FIELDS][4];
     __shared__ uint32_t s_alive[(MSZ_BATCH_MAX_FIELDS + 31) / 32];
-    __shared__ uint32_t s_dense[(MSZ_BATCH_MAX_FIELDS + 31) / 32];  // next sweep scans the field whole
     __shared__ uint32_t s_next;
     __shared__ unsigned long long s_sum;
     __shared__ uint32_t sm[40];
@@ -248,21 +246,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
             ok = grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
             break;
         }
-        // whole-field scans for the next sweep: per field, or one verdict for all
-        const bool all_dense = !P.per_field_dense && P.dense_min >= 0 &&
-                               m_tot * kDenseFactorB >= (unsigned long long)P.dense_min;
-        for (uint32_t w = threadIdx.x; w < (nf + 31) / 32; w += blockDim.x) s_dense[w] = 0u;
-        __syncthreads();
-        for (uint32_t f = threadIdx.x; f < nf; f += blockDim.x) {
-            if (!alive(f)) continue;
-            const unsigned long long nfv = P.fields[f].F.G.n;
-            const bool d = P.per_field_dense
-                               ? (unsigned long long)ld_relaxed(&rec[f].distorted) * kDenseFactorB * 16ull >= nfv
-                               : all_dense;
-            if (d) atomicOr(&s_dense[f >> 5], 1u << (f & 31u));
-        }
-        __syncthreads();
-        auto dense_f = [&](uint32_t f) { return ((s_dense[f >> 5] >> (f & 31u)) & 1u) != 0u; };
+        // whole-field scans for the next sweep (one verdict for every field)
+        const bool dense_next = P.dense_min >= 0 && m_tot * kDenseFactorB >= (unsigned long long)P.dense_min;
         // ---- edit phase of sweep k
         {
             uint32_t targets = 0;
@@ -272,7 +257,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
                 if (!alive(f)) return;
                 const FieldView &F = P.fields[f].F;
                 atomicAdd(&s_cnt[f][2], 1u);
-                if (apply_target<3>(F, t - s_base[f], dense_f(f), F.dm[(k + 1) & 1])) atomicAdd(&s_cnt[f][3], 1u);
+                if (apply_target<3>(F, t - s_base[f], dense_next, F.dm[(k + 1) & 1])) atomicAdd(&s_cnt[f][3], 1u);
             });
             (void)targets;
             flush_counts(s_cnt, nf, rec);
@@ -297,12 +282,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
         {
             const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
             for (uint32_t f = gtid; f < nf; f += stride)
-                if (alive(f) && dense_f(f)) {
+                if (alive(f) && dense_next) {
                     rec1[f].worklist = P.fields[f].F.G.n;
                     rec1[f].dense = 1;
                 }
-            // per word: a whole-scan field examines its uncertified vertices, a
-            // worklist field those of its worklist; done fields none.  The
+            // per word: in a whole-field sweep every uncertified vertex of a
+            // live field, else those of its worklist; done fields none.  The
             // worklist is cleared as it is read (a word never straddles two
             // fields: bases are 1024-aligned).
             walk_words_pairs(
@@ -312,7 +297,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
                     const uint32_t wl = dcur[wi];
                     if (wl) dcur[wi] = 0u;
                     if (!alive(f)) return 0u;
-                    if (dense_f(f)) return P.ub[wi];
+                    if (dense_next) return P.ub[wi];
                     if (!wl) return 0u;
                     atomicAdd(&s_cnt[f][0], (uint32_t)__popc(wl));
                     return wl & P.ub[wi];
@@ -544,9 +529,9 @@ extern "C" msz_status msz_batch_plan_create(int32_t n, const msz_field *fields, 
     P.bsum = (uint32_t *)(ws + L.bsum);
     P.max_sweeps = max_sweeps;
     // default: every field scans whole while 6 x (all fields' distorted
-    // vertices) >= N / 16 (measured faster here than deciding per field)
+    // vertices) >= N / 16 (measured faster than the worklist, and than a
+    // verdict per field, on a batch of many small fields)
     P.dense_min = o.dense_min_items == 0 ? (long long)(ntot / 16 > 0 ? ntot / 16 : 1) : (long long)o.dense_min_items;
-    P.per_field_dense = 0u;
     P.tb = (uint32_t *)(ws + L.tb);
     P.dm[0] = (uint32_t *)(ws + L.d0);
     P.dm[1] = (uint32_t *)(ws + L.d1);

@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(kSegThreads) k_seg_jump(uint32_t n, int32_t *m
 __global__ void __launch_bounds__(256) k_compare(const uint8_t *cf, const uint8_t *cg, const int32_t *mnf,
                                                  const int32_t *mxf, const int32_t *mng, const int32_t *mxg,
                                                  uint64_t n, Ctrl *C) {
-    uint32_t c[5] = {0, 0, 0, 0, 0};
+    uint32_t c[6] = {0, 0, 0, 0, 0, 0};
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const uint8_t a = cf[i], b = cg[i];
@@ -94,9 +94,10 @@ __global__ void __launch_bounds__(256) k_compare(const uint8_t *cf, const uint8_
         c[2] += maxf && !maxg;
         c[3] += ming && !minf;
         c[4] += minf && !ming;
+        c[5] += a != b;
     }
 #pragma unroll
-    for (int q = 0; q < 5; ++q) {
+    for (int q = 0; q < 6; ++q) {
         uint32_t v = c[q];
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(kFull, v, d);
@@ -162,7 +163,7 @@ extern "C" msz_status msz_segment(const uint8_t *d_codes, msz_grid grid, int32_t
 
 extern "C" msz_status msz_compare(const uint8_t *d_codes_f, const uint8_t *d_codes_g, const int32_t *d_min_f,
                                   const int32_t *d_max_f, const int32_t *d_min_g, const int32_t *d_max_g, int64_t n,
-                                  int64_t h_counts[5], void *d_workspace, size_t workspace_bytes,
+                                  int64_t h_counts[6], void *d_workspace, size_t workspace_bytes,
                                   msz_stream_t stream) {
     if (!d_codes_f || !d_codes_g || !d_min_f || !d_max_f || !d_min_g || !d_max_g || !h_counts || n < 0)
         return MSZ_ERR_INVALID_ARG;
@@ -181,6 +182,6 @@ extern "C" msz_status msz_compare(const uint8_t *d_codes_f, const uint8_t *d_cod
     unsigned long long c[8];
     if (cudaMemcpyAsync(c, C->counts, sizeof c, cudaMemcpyDeviceToHost, s) != cudaSuccess) return MSZ_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return MSZ_ERR_CUDA;
-    for (int q = 0; q < 5; ++q) h_counts[q] = (int64_t)c[q];
+    for (int q = 0; q < 6; ++q) h_counts[q] = (int64_t)c[q];
     return MSZ_OK;
 }

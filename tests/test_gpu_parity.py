@@ -250,7 +250,9 @@ def test_segment_labels_and_compare(api, shape, seed):
     c, d = api.segment(gch)
     assert np.array_equal(a.cpu().numpy(), mnf) and np.array_equal(b.cpu().numpy(), mxf)
     assert np.array_equal(c.cpu().numpy(), mnh) and np.array_equal(d.cpu().numpy(), mxh)
-    assert api.compare(gcf, gch, a, b, c, d) == oracle.compare(cf, ch, mnf, mxf, mnh, mxh)
+    got = api.compare(gcf, gch, a, b, c, d)
+    assert got.pop("code_mismatches") == int((cf != ch).sum())
+    assert got == oracle.compare(cf, ch, mnf, mxf, mnh, mxh)
 
 
 def test_segment_rejects_codes_outside_grid(api):
