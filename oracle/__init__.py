@@ -60,6 +60,9 @@ def _load():
             lib.orc_edit.restype = I
             lib.orc_correct.argtypes = [P, P, ctypes.c_float, I, I64, I64, I64, I, I, I64, P, P,
                                         P, P, I64, ctypes.POINTER(I64), P, P, I64]
+            lib.orc_correct_relaxed.argtypes = [P, P, ctypes.c_float, I, I64, I64, I64, I64, I64, I64, I, I64,
+                                                I64, P, P]
+            lib.orc_correct_relaxed.restype = I
             lib.orc_correct.restype = I
             lib.orc_labels.argtypes = [P, I, I64, I64, I64, P, P]
             lib.orc_labels.restype = I
@@ -189,6 +192,22 @@ def correct(f, fhat, xi, *, worklist: bool = True, rule: int = RULE_HALVE, max_s
     nlog = min(int(stats[0]) + 1, log_capacity)
     return Result(int(st), g, eidx[:m].copy(), edel[:m].copy(), int(cnt.value), stats,
                   log[:4 * nlog].reshape(-1, 4).copy())
+
+
+def correct_relaxed(f, fhat, xi, tile, *, rule: int = RULE_HALVE, local_cap: int = 0, max_iters: int = 100000):
+    """Relaxed synchronization (Sec. IV-B) with tiles of tile = (tz, ty, tx)
+    vertices (2D: (ty, tx)): returns (status, g, stats[8])."""
+    f = np.ascontiguousarray(f, dtype=np.float32)
+    fhat = np.ascontiguousarray(fhat, dtype=np.float32)
+    assert f.shape == fhat.shape
+    ndim, nx, ny, nz = grid_of(f.shape)
+    t = tuple(int(v) for v in tile)
+    tz, ty, tx = t if len(t) == 3 else (1,) + t
+    g = np.empty_like(f)
+    stats = np.zeros(8, dtype=np.int64)
+    st = _load().orc_correct_relaxed(_p(f), _p(fhat), np.float32(xi), ndim, nx, ny, nz, tx, ty, tz, rule,
+                                     int(local_cap), int(max_iters), _p(g), _p(stats))
+    return int(st), g, stats
 
 
 def labels(codes_arr: np.ndarray):

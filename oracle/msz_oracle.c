@@ -400,6 +400,148 @@ int orc_correct(const float *f, const float *fhat, float xi,
 }
 
 /* ---------------------------------------------------------------------------
+ * Relaxed synchronization (Sec. IV-B), emulated on one device.  The grid is
+ * cut into tiles of tx x ty x tz vertices (the paper's per-process blocks);
+ * the one-vertex ring around a tile plays the ghost layer.  Iteration k:
+ *   1. detect every vertex distorted in g^k; stop with OK when there is none
+ *      (or with MAX_SWEEPS after max_iters iterations);
+ *   2. every tile that holds a distorted vertex takes a copy of g^k over the
+ *      tile and its ring and runs synchronous sweeps on that copy alone: its
+ *      own vertices are examined, each distinct target (an own or a ring
+ *      vertex) gets one application of Eq. 1 per sweep, until no own vertex is
+ *      distorted, a sweep changes nothing, or local_cap sweeps (<= 0: 65536);
+ *   3. merge: g^(k+1)_v = the minimum of g^k_v and of every tile's copy at v
+ *      (the minimum of the candidates, Sec. IV-B); stop with STUCK when no
+ *      value decreased.
+ * Tiles read only g^k and the merge is a minimum, so the result does not
+ * depend on the order in which tiles run.  Values are compared in IEEE
+ * totalOrder (-0 below +0), so even signed zeros merge the same way in any
+ * order.  With one tile covering the grid, iteration 0 is the synchronous
+ * loop of orc_correct run to its end.
+ * stats (may be NULL), 8 entries: [0] iterations that decreased g, [1] local
+ * sweeps summed over tile runs, [2] distinct edited vertices (g != fhat),
+ * [3] distorted vertices in iteration 0, [4] distorted vertices left, [5] tile
+ * runs, [6] status, [7] 0.
+ * ------------------------------------------------------------------------- */
+/* IEEE totalOrder key of a float: unsigned comparison of keys orders the
+ * floats, with -0 below +0. */
+static uint32_t total_key(float v)
+{
+    uint32_t b;
+    memcpy(&b, &v, 4);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+int orc_correct_relaxed(const float *f, const float *fhat, float xi, int ndim, int64_t nx, int64_t ny,
+                        int64_t nz, int64_t tx, int64_t ty, int64_t tz, int rule, int64_t local_cap,
+                        int64_t max_iters, float *g, int64_t *stats)
+{
+    if (!f || !fhat || !g || nx < 1 || ny < 1 || nz < 1 || (ndim != 2 && ndim != 3) || (ndim == 2 && nz != 1) ||
+        tx < 1 || ty < 1 || tz < 1 || max_iters < 0 || (rule != ORC_RULE_HALVE && rule != ORC_RULE_SNAP))
+        return ORC_ERR_INVALID_ARG;
+    if (local_cap <= 0) local_cap = 65536;
+    int64_t n = nx * ny * nz;
+    int st = orc_validate(f, fhat, n, xi);
+    if (st != ORC_OK) return st;
+    int64_t ntx = (nx + tx - 1) / tx, nty = (ny + ty - 1) / ty, ntz = (nz + tz - 1) / tz;
+    int64_t ntiles = ntx * nty * ntz;
+    uint8_t *cf = malloc((size_t)n);
+    uint8_t *active = malloc((size_t)ntiles);
+    uint8_t *is_target = calloc((size_t)n, 1);
+    int64_t *tlist = malloc(sizeof(int64_t) * (size_t)n);
+    float *L = malloc(sizeof(float) * (size_t)n);
+    float *snap = malloc(sizeof(float) * (size_t)n);
+    float *local = malloc(sizeof(float) * (size_t)n);
+    if (!cf || !active || !is_target || !tlist || !L || !snap || !local) {
+        free(cf); free(active); free(is_target); free(tlist); free(L); free(snap); free(local);
+        return ORC_ERR_OOM;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        g[i] = fhat[i];
+        L[i] = orc_floor(f[i], xi);
+    }
+    orc_codes(f, ndim, nx, ny, nz, cf);
+
+    int64_t iters = 0, local_sweeps = 0, first_distorted = -1, left = 0, runs = 0;
+    int status = ORC_ERR_MAX_SWEEPS;
+    for (int64_t k = 0;; ++k) {
+        /* 1. detect over the whole grid */
+        int64_t distorted = 0;
+        memset(active, 0, (size_t)ntiles);
+        for (int64_t i = 0; i < n; ++i) {
+            if (orc_code_at(g, ndim, nx, ny, nz, i) == cf[i]) continue;
+            ++distorted;
+            int64_t x = i % nx, y = (i / nx) % ny, z = i / (nx * ny);
+            active[(x / tx) + ntx * ((y / ty) + nty * (z / tz))] = 1;
+        }
+        if (k == 0) first_distorted = distorted;
+        if (distorted == 0) { status = ORC_OK; break; }
+        if (k >= max_iters) { status = ORC_ERR_MAX_SWEEPS; left = distorted; break; }
+        /* 2. local sweeps of every active tile on its own copy of g^k */
+        memcpy(snap, g, sizeof(float) * (size_t)n);
+        memcpy(local, g, sizeof(float) * (size_t)n);
+        for (int64_t b = 0; b < ntiles; ++b) {
+            if (!active[b]) continue;
+            ++runs;
+            int64_t bx = b % ntx, by = (b / ntx) % nty, bz = b / (ntx * nty);
+            int64_t x0 = bx * tx, y0 = by * ty, z0 = bz * tz;
+            int64_t x1 = x0 + tx < nx ? x0 + tx : nx, y1 = y0 + ty < ny ? y0 + ty : ny, z1 = z0 + tz < nz ? z0 + tz : nz;
+            /* ring-extended box, clipped to the grid */
+            int64_t rx0 = x0 > 0 ? x0 - 1 : 0, ry0 = y0 > 0 ? y0 - 1 : 0, rz0 = z0 > 0 ? z0 - 1 : 0;
+            int64_t rx1 = x1 < nx ? x1 + 1 : nx, ry1 = y1 < ny ? y1 + 1 : ny, rz1 = z1 < nz ? z1 + 1 : nz;
+            for (int64_t ls = 0; ls < local_cap; ++ls) {
+                int64_t nt = 0, dist_here = 0;
+                for (int64_t z = z0; z < z1; ++z)
+                    for (int64_t y = y0; y < y1; ++y)
+                        for (int64_t x = x0; x < x1; ++x) {
+                            int64_t i = x + nx * (y + ny * z);
+                            uint8_t cg = orc_code_at(local, ndim, nx, ny, nz, i);
+                            if (cg == cf[i]) continue;
+                            ++dist_here;
+                            int64_t t[2];
+                            int m = targets_of(ndim, nx, ny, nz, i, cf[i], cg, t);
+                            for (int q = 0; q < m; ++q)
+                                if (!is_target[t[q]]) { is_target[t[q]] = 1; tlist[nt++] = t[q]; }
+                        }
+                if (dist_here == 0) break;
+                ++local_sweeps;
+                int64_t changed = 0;
+                for (int64_t q = 0; q < nt; ++q) {
+                    is_target[tlist[q]] = 0;
+                    changed += orc_edit(&local[tlist[q]], L[tlist[q]], rule);
+                }
+                if (changed == 0) break;
+            }
+            /* 3. merge by minimum, then restore the copy for the next tile */
+            for (int64_t z = rz0; z < rz1; ++z)
+                for (int64_t y = ry0; y < ry1; ++y)
+                    for (int64_t x = rx0; x < rx1; ++x) {
+                        int64_t i = x + nx * (y + ny * z);
+                        if (total_key(local[i]) < total_key(g[i])) g[i] = local[i];
+                        local[i] = snap[i];
+                    }
+        }
+        int64_t decreased = 0;
+        for (int64_t i = 0; i < n; ++i) decreased += total_key(g[i]) < total_key(snap[i]);
+        if (decreased == 0) { status = ORC_STUCK; left = distorted; break; }
+        ++iters;
+    }
+    if (stats) {
+        int64_t ne = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            uint32_t a, c;
+            memcpy(&a, &g[i], 4);
+            memcpy(&c, &fhat[i], 4);
+            ne += a != c;
+        }
+        stats[0] = iters; stats[1] = local_sweeps; stats[2] = ne; stats[3] = first_distorted;
+        stats[4] = left; stats[5] = runs; stats[6] = status; stats[7] = 0;
+    }
+    free(cf); free(active); free(is_target); free(tlist); free(L); free(snap); free(local);
+    return status;
+}
+
+/* ---------------------------------------------------------------------------
  * Sec. III-A: integral lines and the ascending/descending segmentations.
  * max_label[i] = the maximum reached from i by repeatedly stepping to n_max
  * (the code's low nibble) until a vertex that is a maximum; min_label[i]
