@@ -102,7 +102,7 @@ typedef struct {
                                  end of sweep k's detection and of its edit phase (-1: none) */
     int32_t tile_z;           /* z-planes per tile of the code pass (3D); 0: 32; at most 1024.
                                  Affects speed only (see the autotuner), never results */
-    int32_t reserved2;
+    int32_t local_cap;        /* msz_correct_relaxed: local sweeps per tile run; 0: 65536 */
 } msz_options;
 
 typedef struct {
@@ -117,6 +117,8 @@ typedef struct {
     int64_t codes_ns;         /* ... of its first phase: the codes of f and their certification */
     int64_t uncertified;      /* vertices sweep 0 could not certify (only these can ever be
                                  distorted); 0 in msz_correct_batch results */
+    int64_t local_sweeps;     /* msz_correct_relaxed: local sweeps summed over tile runs */
+    int64_t tile_runs;        /* msz_correct_relaxed: tile runs summed over iterations */
 } msz_stats;
 
 /* Bytes of device workspace msz_correct needs for this grid (about 13.5 bytes
@@ -326,6 +328,33 @@ msz_status msz_learned_wgrad(const uint16_t *d_x, int32_t cin, const uint16_t *d
 /* One Adam step on n FP32 parameters (bias-corrected; step >= 1). */
 msz_status msz_learned_adam(float *d_p, const float *d_g, float *d_m, float *d_v, int64_t n, float lr, float beta1,
                             float beta2, float eps, int64_t step, msz_stream_t stream);
+
+/* ---- Relaxed synchronization (Sec. IV-B) emulated on one GPU.  The paper's
+ * per-process blocks become tiles of MSZ_RELAXED_TILE_X x _Y x _Z vertices
+ * (one thread block each), its ghost layer the one-vertex ring around a tile,
+ * its ghost exchange a merge by minimum.  Iteration k: detect every vertex
+ * distorted in g^k (none: MSZ_OK); every tile holding one runs synchronous
+ * sweeps (the rule of msz_correct) on its own copy of g^k over the tile and
+ * its ring -- its own vertices are examined, targets may lie on the ring --
+ * until no own vertex is distorted, a sweep changes nothing, or
+ * opt->local_cap sweeps; then g^(k+1) = the minimum, in IEEE totalOrder, of
+ * g^k and every tile's copy (MSZ_STUCK when nothing decreased).  The result
+ * does not depend on the order in which tiles run.  3D grids only; no
+ * d_g_init; opt->max_sweeps caps the iterations.  stats: sweeps = iterations
+ * that decreased g, local_sweeps, tile_runs, edited, first_distorted, left,
+ * kernel_ns, codes_ns, uncertified (other fields 0).  h_sweep_log per
+ * iteration: tile runs, distorted vertices, local sweeps, decreased values.
+ * Arguments, outputs and statuses otherwise as msz_correct.  Workspace:
+ * msz_relaxed_workspace_size(grid) bytes (msz_workspace_size plus 4 bytes and
+ * one bit per vertex).  Synchronizes `stream`. */
+#define MSZ_RELAXED_TILE_X 32
+#define MSZ_RELAXED_TILE_Y 8
+#define MSZ_RELAXED_TILE_Z 8
+size_t msz_relaxed_workspace_size(msz_grid grid);
+msz_status msz_correct_relaxed(const float *d_f, const float *d_fhat, float xi, msz_grid grid, float *d_out,
+                               uint32_t *d_edit_idx, float *d_edit_delta, int64_t edit_capacity,
+                               int64_t *h_edit_count, const msz_options *opt, msz_stats *h_stats,
+                               void *d_workspace, size_t workspace_bytes, msz_stream_t stream);
 
 /* msz_correct for callers that cannot allocate device memory.  (The paper has
  * no counterpart: this entry point exists for how callers use the library.)

@@ -34,6 +34,7 @@ UNITS = [
     ("msz_segment.cu", EXACT),
     ("msz_static.cu", EXACT),
     ("msz_batch.cu", EXACT),
+    ("msz_relaxed.cu", EXACT),
     ("msz_learned.cu", []),
 ]
 

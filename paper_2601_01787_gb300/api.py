@@ -39,13 +39,13 @@ class Options(ctypes.Structure):
     _fields_ = [("rule", ctypes.c_int32), ("test_fault", ctypes.c_int32), ("max_sweeps", ctypes.c_int64),
                 ("dense_min_items", ctypes.c_int64), ("d_g_init", ctypes.c_void_p),
                 ("h_sweep_log", ctypes.c_void_p), ("log_capacity", ctypes.c_int64),
-                ("h_timeline", ctypes.c_void_p), ("tile_z", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
+                ("h_timeline", ctypes.c_void_p), ("tile_z", ctypes.c_int32), ("local_cap", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("sweeps", "edits", "edited", "first_distorted", "left",
                                               "examined", "dense_sweeps", "kernel_ns", "codes_ns",
-                                              "uncertified")]
+                                              "uncertified", "local_sweeps", "tile_runs")]
 
     def as_dict(self) -> dict:
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
@@ -115,6 +115,10 @@ def load(build_if_missing: bool = True):
         lib.msz_batch_collect.restype = st
         lib.msz_batch_plan_destroy.argtypes = [P]
         lib.msz_batch_plan_destroy.restype = None
+        lib.msz_relaxed_workspace_size.argtypes = [Grid]
+        lib.msz_relaxed_workspace_size.restype = SZ
+        lib.msz_correct_relaxed.argtypes = lib.msz_correct.argtypes
+        lib.msz_correct_relaxed.restype = st
         lib.msz_status_str.argtypes = [st]
         lib.msz_status_str.restype = ctypes.c_char_p
         _lib = lib
@@ -196,13 +200,13 @@ class CorrectResult:
         return self.status == OK
 
 
-def _options(rule, max_sweeps, dense_min_items, g_init, log_capacity, tile_z=0, test_fault=0):
+def _options(rule, max_sweeps, dense_min_items, g_init, log_capacity, tile_z=0, test_fault=0, local_cap=0):
     log = np.zeros(max(4 * log_capacity, 4), dtype=np.int64)
     tl = np.full(max(2 * log_capacity, 2), -1, dtype=np.int64)
     opt = Options(RULES[rule] if isinstance(rule, str) else int(rule), int(test_fault), int(max_sweeps),
                   int(dense_min_items),
                   _dptr(g_init), log.ctypes.data if log_capacity else None, int(log_capacity),
-                  tl.ctypes.data if log_capacity else None, int(tile_z), 0)
+                  tl.ctypes.data if log_capacity else None, int(tile_z), int(local_cap))
     opt._keep = (log, tl)
     return opt, log
 
@@ -235,6 +239,41 @@ def correct(f: torch.Tensor, fhat: torch.Tensor, xi: float, *, rule="halve", max
                          ctypes.byref(stats), _dptr(ws), ws.numel(), _stream(stream))
     if check and st not in (OK,):
         raise MszError(st, "msz_correct")
+    m = min(int(count.value), cap)
+    nlog = min(stats.sweeps + 1, log_capacity)
+    res = CorrectResult(int(st), out, edit_idx[:m], edit_delta[:m], int(count.value), stats.as_dict(),
+                        log[:4 * nlog].reshape(-1, 4).copy())
+    res.timeline = opt._keep[1][:2 * nlog].reshape(-1, 2).copy()
+    return res
+
+
+RELAXED_TILE = (8, 8, 32)  # (z, y, x) vertices per tile of msz_correct_relaxed
+
+
+def correct_relaxed(f: torch.Tensor, fhat: torch.Tensor, xi: float, *, rule="halve", max_iters: int = 0,
+                    local_cap: int = 0, edit_capacity: int | None = None, log_capacity: int = 0,
+                    out: torch.Tensor | None = None, edit_idx: torch.Tensor | None = None,
+                    edit_delta: torch.Tensor | None = None, ws: torch.Tensor | None = None, stream=None,
+                    tile_z: int = 0) -> CorrectResult:
+    """The relaxed synchronization of Sec. IV-B on one GPU (msz_correct_relaxed)."""
+    assert f.dtype == torch.float32 and fhat.dtype == torch.float32 and f.shape == fhat.shape and f.dim() == 3
+    lib = load()
+    g = grid_of(f.shape)
+    cap = f.numel() if edit_capacity is None else int(edit_capacity)
+    if out is None:
+        out = torch.empty_like(f)
+    if edit_idx is None or edit_idx.numel() < cap:
+        edit_idx = torch.empty(max(cap, 1), dtype=torch.int32, device=f.device)
+    if edit_delta is None or edit_delta.numel() < cap:
+        edit_delta = torch.empty(max(cap, 1), dtype=torch.float32, device=f.device)
+    if ws is None:
+        ws = workspace(int(lib.msz_relaxed_workspace_size(g)), f.device)
+    opt, log = _options(rule, max_iters, 0, None, log_capacity, tile_z, 0, local_cap)
+    stats = Stats()
+    count = ctypes.c_int64()
+    st = lib.msz_correct_relaxed(_dptr(f), _dptr(fhat), ctypes.c_float(np.float32(xi)), g, _dptr(out),
+                                 _dptr(edit_idx), _dptr(edit_delta), cap, ctypes.byref(count), ctypes.byref(opt),
+                                 ctypes.byref(stats), _dptr(ws), ws.numel(), _stream(stream))
     m = min(int(count.value), cap)
     nlog = min(stats.sweeps + 1, log_capacity)
     res = CorrectResult(int(st), out, edit_idx[:m], edit_delta[:m], int(count.value), stats.as_dict(),

@@ -428,6 +428,21 @@ static __device__ void first_tiled(const FieldView &P, uint32_t *tile_next, floa
     if (bad) atomicOr(err, kErrInput);
 }
 
+// Marks vertex t and its neighbours in bitmap bm.
+template <int NDIM>
+__device__ __forceinline__ void mark_closed(const GridDev &G, uint32_t t, uint32_t *bm) {
+    red_or(&bm[t >> 5], 1u << (t & 31u));
+    uint32_t x, y, z;
+    coords_of(G, t, x, y, z);
+    constexpr int ns = NDIM == 2 ? 6 : 14;
+#pragma unroll
+    for (int s = 0; s < ns; ++s) {
+        if (!slot_in_domain(G, s, x, y, z)) continue;
+        const uint32_t j = (uint32_t)((int64_t)t + G.off[s]);
+        red_or(&bm[j >> 5], 1u << (j & 31u));
+    }
+}
+
 // Eq. 1 on target t of field P (once per sweep); a changed target marks the
 // edited bitmap and, unless the next sweep scans densely, its closed
 // neighbourhood in the next worklist.  Returns whether g_t decreased.
@@ -440,16 +455,7 @@ __device__ __forceinline__ bool apply_target(const FieldView &P, uint32_t t, boo
     P.g[t] = h;
     red_or(&P.eb[t >> 5], 1u << (t & 31u));
     if (dense_next) return true;
-    red_or(&dnext[t >> 5], 1u << (t & 31u));
-    uint32_t x, y, z;
-    coords_of(P.G, t, x, y, z);
-    constexpr int ns = NDIM == 2 ? 6 : 14;
-#pragma unroll
-    for (int s = 0; s < ns; ++s) {
-        if (!slot_in_domain(P.G, s, x, y, z)) continue;
-        const uint32_t j = (uint32_t)((int64_t)t + P.G.off[s]);
-        red_or(&dnext[j >> 5], 1u << (j & 31u));
-    }
+    mark_closed<NDIM>(P.G, t, dnext);
     return true;
 }
 
