@@ -264,11 +264,21 @@ static msz_status correct_blocks(const DeviceInfo &d, int &blocks) {
     return MSZ_OK;
 }
 
+// Default planes per tile of the code pass: the deepest of 32, 16, 8 that
+// still gives every block of the persistent grid two tiles or more (deeper
+// tiles re-read fewer halo planes; more tiles balance the blocks' work).
+static uint32_t default_tile_z(const GridDev &G, int blocks) {
+    for (uint32_t tz = kTileZ; tz > 8; tz /= 2)
+        if ((uint64_t)tile::tile_geom(G.nx, G.ny, G.nz, tz).count >= 2ull * (uint64_t)blocks) return tz;
+    return 8;
+}
+
 template <int NDIM>
 static msz_status run_correct(Problem &P, const DeviceInfo &dev, cudaStream_t stream) {
     int blocks = 0;
     msz_status st = correct_blocks<NDIM>(dev, blocks);
     if (st != MSZ_OK) return st;
+    if (P.F.tile_z == 0) P.F.tile_z = default_tile_z(P.F.G, blocks);
     void *args[] = {(void *)&P};
     if (cudaLaunchCooperativeKernel((const void *)k_correct<NDIM>, dim3(blocks), dim3(kThreads), args,
                                     correct_smem<NDIM>(), stream) != cudaSuccess)
@@ -343,7 +353,7 @@ extern "C" msz_status msz_correct(const float *d_f, const float *d_fhat, float x
     F.xi = xi;
     F.two_xi = 2.0f * xi;  // exact (power-of-two scaling), +inf on overflow
     F.rule = o.rule;
-    F.tile_z = o.tile_z > 0 ? (uint32_t)o.tile_z : kTileZ;
+    F.tile_z = o.tile_z > 0 ? (uint32_t)o.tile_z : 0u;  // 0: chosen from the grid and the launch
     P.ctrl = (Ctrl *)(ws + L.ctrl);
     P.log = (SweepRec *)(ws + L.log);
     P.bsum = (uint32_t *)(ws + L.bsum);
