@@ -116,7 +116,8 @@ typedef struct {
     int64_t examined;         /* vertices examined over all sweeps (dense sweeps count N) */
     int64_t dense_sweeps;     /* sweeps run as whole-grid scans, sweep 0 included */
     int64_t kernel_ns;        /* device time of the correction kernel (globaltimer) */
-    int64_t codes_ns;         /* ... of its first phase: the codes of f and their certification */
+    int64_t codes_ns;         /* ... of its first phase: the codes of f and their certification
+                                 (3D grids: with sweep 0's detection, done in the same pass) */
     int64_t uncertified;      /* vertices sweep 0 could not certify (only these can ever be
                                  distorted); 0 in msz_correct_batch results */
     int64_t local_sweeps;     /* msz_correct_relaxed: local sweeps summed over tile runs */

@@ -177,7 +177,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
     if (leader) C->t_start = global_ns();
     auto alive = [&](uint32_t k) { return (s_alive[k >> 5] >> (k & 31u)) & 1u; };
 
-    // ---- codes of every field, one shared tile queue
+    // ---- codes of every field and the detection of sweep 0 over their
+    // uncertified vertices, one shared tile queue
     {
         bool bad = false;
         for (;;) {
@@ -193,25 +194,18 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
             const uint32_t txi = lt % tg.tx, tyi = (lt / tg.tx) % tg.ty, tzi = lt / (tg.tx * tg.ty);
             const int zb = (int)(tzi * tg.bz);
             bool fb = false;
-            first_tile(F, (int)(txi * tile::BX), (int)(tyi * tile::BY), zb, min(zb + (int)tg.bz, (int)F.G.nz), smem,
-                       fb);
+            uint32_t dist = 0;
+            first_tile<true>(F, (int)(txi * tile::BX), (int)(tyi * tile::BY), zb,
+                             min(zb + (int)tg.bz, (int)F.G.nz), smem, fb, dist);
+            warp_add(dist, &s_cnt[k][1]);
             if (fb) atomicOr(&P.res[k].error, kErrInput);
             bad = bad || fb;
         }
         if (bad) atomicOr(&C->error, kErrInput);
+        flush_counts(s_cnt, nf, P.log);
     }
     bool ok = grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
     if (leader) C->t_codes = global_ns();
-
-    // ---- detection of sweep 0 over the uncertified vertices of every field
-    if (ok) {
-        uint32_t seen = 0;
-        walk_bits_pairs<false>(P.ub, nullptr, P.all, seen, [&](bool h1, uint32_t v1, bool h2, uint32_t v2) {
-            detect_pair(P, s_base, nf, s_cnt, 1u, [](uint32_t) { return true; }, h1, v1, h2, v2);
-        });
-        flush_counts(s_cnt, nf, P.log);
-    }
-    ok = ok && grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
     uint32_t k = 0;
     while (ok) {
         BatchRec *rec = P.log + (size_t)k * nf;

@@ -65,27 +65,38 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
     const bool leader = gtid == 0;
     if (leader) C->t_start = global_ns();
 
-    // ---- sweep 0: codes of f with their certification, g = start, bound check
-    if (NDIM == 3) first_tiled(F, &P.log[0].tile_next, smem, &C->error);
-    else first_generic<NDIM>(F, &C->error);
-    bool ok = P.test_fault ? grid_barrier(&C->bar_count, &C->bar_gen, &C->error, kTestBarrierNs, blockIdx.x == 0)
-                           : grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
-    if (leader) C->t_codes = global_ns();
-    // ---- detection of sweep 0: only uncertified vertices can be distorted
-    if (ok) {
-        Emitter E{F.dm[1], 0};
-        uint32_t seen = 0;
-        walk_bits_pairs<false>(F.ub, nullptr, G, seen, [&](bool h1, uint32_t v1, bool h2, uint32_t v2) {
-            detect_vertex2<NDIM>(F, E, h1, v1, h2, v2);
-        });
-        warp_add(E.distorted, &P.log[0].distorted);
-    }
+    // ---- sweep 0: codes of f with their certification, g = start, bound
+    // check, and the detection of sweep 0 (only uncertified vertices can be
+    // distorted).  3D tiles detect their own uncertified vertices from the
+    // staged start field; 2D grids detect in a second phase.
     if (leader) {
         P.log[0].worklist = G.n;
         C->examined = G.n;
         C->dense_sweeps = 1;
     }
-    ok = ok && grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
+    bool ok;
+    if (NDIM == 3) {
+        uint32_t distorted = 0;
+        first_tiled<true>(F, &P.log[0].tile_next, smem, &C->error, distorted);
+        warp_add(distorted, &P.log[0].distorted);
+        ok = P.test_fault ? grid_barrier(&C->bar_count, &C->bar_gen, &C->error, kTestBarrierNs, blockIdx.x == 0)
+                          : grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
+        if (leader) C->t_codes = global_ns();
+    } else {
+        first_generic<NDIM>(F, &C->error);
+        ok = P.test_fault ? grid_barrier(&C->bar_count, &C->bar_gen, &C->error, kTestBarrierNs, blockIdx.x == 0)
+                          : grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
+        if (leader) C->t_codes = global_ns();
+        if (ok) {
+            Emitter E{F.dm[1], 0};
+            uint32_t seen = 0;
+            walk_bits_pairs<false>(F.ub, nullptr, G, seen, [&](bool h1, uint32_t v1, bool h2, uint32_t v2) {
+                detect_vertex2<NDIM>(F, E, h1, v1, h2, v2);
+            });
+            warp_add(E.distorted, &P.log[0].distorted);
+        }
+        ok = ok && grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
+    }
     if (leader) P.log[0].t_detect = global_ns();
     uint32_t k = 0;
     while (ok) {

@@ -273,11 +273,16 @@ __device__ void first_generic(const FieldView &P, uint32_t *err) {
 }
 
 // ------------------------------------------------ tiled (3D) codes of f
-// One tile (x0, y0, planes zb .. ze-1) of field P: codes of f with their
-// certification, g = start value, bound check (bad is set on a violation).
+// One tile (x0, y0, planes zb .. ze-1) of field P: certification of every
+// vertex, codes of f at the uncertified ones, g = start value, bound check
+// (bad is set on a violation).
+// DETECT: also sweep 0's detection of the tile's uncertified vertices, whose
+// codes in the start field come from the staged planes; they mark targets and
+// the worklist P.dm[1], and add to `distorted`.
 // Block-collective; the caller synchronizes the block before the next tile.
+template <bool DETECT>
 __device__ __forceinline__ void first_tile(const FieldView &P, int x0, int y0, int zb, int ze, float *smem,
-                                           bool &bad) {
+                                           bool &bad, uint32_t &distorted) {
     using namespace tile;
     const GridDev &G = P.G;
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
@@ -294,6 +299,10 @@ __device__ __forceinline__ void first_tile(const FieldView &P, int x0, int y0, i
         inm |= (uint32_t)in << j;
         ownm |= (uint32_t)(in && r >= 1 && r <= BY && c >= 1 && c <= BX) << j;
     }
+    // second staged field: the start field over the whole region when this
+    // pass detects (it needs the start values of the halo), else fhat over the
+    // owned region
+    const uint32_t secm = DETECT ? inm : ownm;
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
     const int gbase = (y0 - 1) * (int)G.nx + (x0 - 1);  // plane offset of staged element 0
     const float qnan = __int_as_float(0x7fffffff);
@@ -305,15 +314,19 @@ __device__ __forceinline__ void first_tile(const FieldView &P, int x0, int y0, i
         const int e = (int)tid + j * THREADS;
         if (e >= ELEMS || (inm >> j & 1u)) continue;
         const int r = e / LOADW, c = e - r * LOADW;
-        for (int sl = 0; sl < NSLOT; ++sl) smem[sl * SLOT + r * PW + c + 3] = qnan;
+        for (int sl = 0; sl < NSLOT; ++sl) {
+            smem[sl * SLOT + r * PW + c + 3] = qnan;
+            if (DETECT) smem[sl * SLOT + PLANE + r * PW + c + 3] = qnan;
+        }
     }
-    // asynchronous copy of plane p (f over the staged region, fhat over the
-    // owned region) into its ring slot; planes outside the grid become NaN
+    // asynchronous copy of plane p (f over the staged region, the second
+    // field over its region) into its ring slot; planes outside the grid
+    // become NaN
     auto issue = [&](int p) {
         if (p >= 0 && p <= ze) {
             const int slot = (p - zb + 1) % NSLOT;
             const bool inside = p < (int)G.nz;
-            const size_t pb = (size_t)p * G.nxy;
+            const uint32_t pb = (uint32_t)p * G.nxy;
 #pragma unroll
             for (int j = 0; j < PER_THREAD; ++j) {
                 if (!(inm >> j & 1u)) continue;
@@ -322,11 +335,13 @@ __device__ __forceinline__ void first_tile(const FieldView &P, int x0, int y0, i
                 const uint32_t so = (uint32_t)(slot * SLOT + r * PW + c + 3);
                 if (!inside) {
                     smem[so] = qnan;
+                    if (DETECT) smem[so + PLANE] = qnan;
                     continue;
                 }
-                const size_t gi = pb + (size_t)(gbase + r * (int)G.nx + c);
+                const uint32_t gi = pb + (uint32_t)(gbase + r * (int)G.nx + c);
                 cp_async4(sbase + 4u * so, P.f + gi);
-                if (ownm >> j & 1u) cp_async4(sbase + 4u * (so + (uint32_t)PLANE), P.fhat + gi);
+                if (secm >> j & 1u)
+                    cp_async4(sbase + 4u * (so + (uint32_t)PLANE), (DETECT && P.ginit ? P.ginit : P.fhat) + gi);
             }
         } else if (p < 0) {
             const int slot = (p - zb + 1) % NSLOT;
@@ -336,6 +351,7 @@ __device__ __forceinline__ void first_tile(const FieldView &P, int x0, int y0, i
                 const int e = (int)tid + j * THREADS;
                 const int r = e / LOADW, c = e - r * LOADW;
                 smem[slot * SLOT + r * PW + c + 3] = qnan;
+                if (DETECT) smem[slot * SLOT + PLANE + r * PW + c + 3] = qnan;
             }
         }
         cp_async_commit();
@@ -343,16 +359,20 @@ __device__ __forceinline__ void first_tile(const FieldView &P, int x0, int y0, i
     // owned vertices of plane p: bound check and g = start value
     auto own = [&](int p) {
         const int slot = (p - zb + 1) % NSLOT;
-        const size_t pb = (size_t)p * G.nxy;
+        const uint32_t pb = (uint32_t)p * G.nxy;
 #pragma unroll
         for (int j = 0; j < PER_THREAD; ++j) {
             if (!(ownm >> j & 1u)) continue;
             const int e = (int)tid + j * THREADS;
             const int r = e / LOADW, c = e - r * LOADW;
             const int so = slot * SLOT + r * PW + c + 3;
-            const float fi = smem[so], fh = smem[so + PLANE];
-            const size_t gi = pb + (size_t)(gbase + r * (int)G.nx + c);
-            const float gs = P.ginit ? P.ginit[gi] : fh;
+            const uint32_t gi = pb + (uint32_t)(gbase + r * (int)G.nx + c);
+            const float fi = smem[so], sv = smem[so + PLANE];
+            float fh = sv, gs = sv;
+            if (P.ginit) {
+                if (DETECT) fh = P.fhat[gi];
+                else gs = P.ginit[gi];
+            }
             const float L = floor_bound(fi, P.xi), U = ceil_bound(fi, P.xi);
             bool ok = isfinite(fi) && isfinite(fh) && fh >= L && fh <= U;
             if (P.ginit) {
@@ -376,40 +396,64 @@ __device__ __forceinline__ void first_tile(const FieldView &P, int x0, int y0, i
         own(z);
         if (y >= (int)G.ny) continue;
         auto plane = [&](int p) { return smem + ((p - zb + 1) % NSLOT) * SLOT; };
-        uint32_t cf[4], cert;
-        tile::codes4_cert(plane(z - 1), plane(z), plane(z + 1), r, lane, P.two_xi, cf, cert);
-        const size_t rowbase = (size_t)z * G.nxy + (size_t)y * G.nx;
-        const size_t i0 = rowbase + xl;
-        if (xl + 3 < (int)G.nx && (i0 & 3) == 0) {
-            *reinterpret_cast<uint32_t *>(P.codes_f + i0) = cf[0] | cf[1] << 8 | cf[2] << 16 | cf[3] << 24;
-        } else {
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                if (xl + e < (int)G.nx) P.codes_f[i0 + e] = (uint8_t)cf[e];
-        }
+        const uint32_t cert = tile::cert4(plane(z - 1), plane(z), plane(z + 1), r, lane, P.two_xi);
+        const uint32_t rowbase = (uint32_t)z * G.nxy + (uint32_t)y * G.nx;
+        const uint32_t i0 = rowbase + (uint32_t)xl;
         // uncertified bits of this lane's vertices (outside the grid: 0)
         uint32_t nib = 0;
 #pragma unroll
         for (int e = 0; e < 4; ++e) nib |= (uint32_t)(xl + e < (int)G.nx && !((cert >> e) & 1u)) << e;
-        const bool words_ok = ((rowbase + (size_t)x0) & 31u) == 0 && x0 + BX <= (int)G.nx;
+        // the row's 128 uncertified bits as 4 words: word q (lanes 8q .. 8q+7)
+        // covers columns 32q .. 32q+31
+        uint32_t w = nib << (4u * (lane & 7u));
+        w |= __shfl_xor_sync(kFull, w, 1);
+        w |= __shfl_xor_sync(kFull, w, 2);
+        w |= __shfl_xor_sync(kFull, w, 4);
+        const bool words_ok = ((rowbase + (uint32_t)x0) & 31u) == 0 && x0 + BX <= (int)G.nx;
         if (words_ok) {
-            // the warp's 128 vertices are 4 whole bitmap words
-            uint32_t w = nib << (4u * (lane & 7u));
-            w |= __shfl_xor_sync(kFull, w, 1);
-            w |= __shfl_xor_sync(kFull, w, 2);
-            w |= __shfl_xor_sync(kFull, w, 4);
-            if ((lane & 7u) == 0) P.ub[(i0) >> 5] = w;
+            if ((lane & 7u) == 0) P.ub[i0 >> 5] = w;
         } else {
 #pragma unroll
             for (int e = 0; e < 4; ++e)
                 if ((nib >> e) & 1u) red_or(&P.ub[(i0 + e) >> 5], 1u << ((i0 + e) & 31u));
         }
+        // The row's uncertified vertices, 32 at a time in column order (lane
+        // j takes the j-th one): the exact code in f, written to codes_f (the
+        // loop reads codes_f at uncertified vertices only) and, when this
+        // pass detects, the code in the start field, compared with it.
+        const uint32_t w0 = __shfl_sync(kFull, w, 0), w1 = __shfl_sync(kFull, w, 8);
+        const uint32_t w2 = __shfl_sync(kFull, w, 16), w3 = __shfl_sync(kFull, w, 24);
+        const uint32_t c0 = (uint32_t)__popc(w0), c1 = c0 + (uint32_t)__popc(w1);
+        const uint32_t c2 = c1 + (uint32_t)__popc(w2), total = c2 + (uint32_t)__popc(w3);
+        Emitter E{P.dm[1], 0};
+        for (uint32_t j0 = 0; j0 < total; j0 += 32u) {
+            const uint32_t j = j0 + lane;
+            const bool has = j < total;
+            uint32_t col = 0, cf = 0, cg = 0;
+            if (has) {
+                const uint32_t q = j < c0 ? 0u : j < c1 ? 1u : j < c2 ? 2u : 3u;
+                const uint32_t wq = q == 0 ? w0 : q == 1 ? w1 : q == 2 ? w2 : w3;
+                const uint32_t before = q == 0 ? 0u : q == 1 ? c0 : q == 2 ? c1 : c2;
+                col = 32u * q + nth_set(wq, j - before);
+                cf = tile::code1(plane(z - 1), plane(z), plane(z + 1), r, 4 + (int)col);
+                P.codes_f[rowbase + (uint32_t)x0 + col] = (uint8_t)cf;
+                if (DETECT)
+                    cg = tile::code1(plane(z - 1) + PLANE, plane(z) + PLANE, plane(z + 1) + PLANE, r,
+                                     4 + (int)col);
+            }
+            if (DETECT) report(P, E, has, rowbase + (uint32_t)x0 + col, cf, cg);
+        }
+        distorted += E.distorted;
     }
     cp_async_wait<0>();
 }
 
 // Tiles of one field handed out by an atomic counter (block-collective).
-static __device__ void first_tiled(const FieldView &P, uint32_t *tile_next, float *smem, uint32_t *err) {
+// DETECT: the pass also runs sweep 0's detection (distorted vertices counted
+// in `distorted`).
+template <bool DETECT>
+__device__ __forceinline__ void first_tiled(const FieldView &P, uint32_t *tile_next, float *smem, uint32_t *err,
+                                            uint32_t &distorted) {
     using namespace tile;
     const GridDev &G = P.G;
     const TileGeom tg = tile_geom(G.nx, G.ny, G.nz, P.tile_z);
@@ -423,7 +467,8 @@ static __device__ void first_tiled(const FieldView &P, uint32_t *tile_next, floa
         if (t >= tg.count) break;
         const uint32_t txi = t % tg.tx, tyi = (t / tg.tx) % tg.ty, tzi = t / (tg.tx * tg.ty);
         const int zb = (int)(tzi * tg.bz);
-        first_tile(P, (int)(txi * BX), (int)(tyi * BY), zb, min(zb + (int)tg.bz, (int)G.nz), smem, bad);
+        first_tile<DETECT>(P, (int)(txi * BX), (int)(tyi * BY), zb, min(zb + (int)tg.bz, (int)G.nz), smem, bad,
+                           distorted);
     }
     if (bad) atomicOr(err, kErrInput);
 }

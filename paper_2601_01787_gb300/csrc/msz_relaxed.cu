@@ -260,7 +260,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_relaxed(__grid_constan
     if (leader) C->t_start = global_ns();
 
     // ---- sweep 0: codes of f with their certification, g = fhat, bound check
-    first_tiled(F, &P.log[0].tile_next, smem, &C->error);
+    uint32_t unused = 0;
+    first_tiled<false>(F, &P.log[0].tile_next, smem, &C->error, unused);
     bool ok = grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
     if (leader) C->t_codes = global_ns();
     uint32_t k = 0;

@@ -2,14 +2,15 @@
 //
 // A block of 256 threads (8 warps) owns a tile of 128 (x) x 8 (y) vertices
 // and marches it through a range of z planes.  The field planes it needs
-// (rows y0-1 .. y0+8, columns x0-1 .. x0+128) are staged through a ring of 4
+// (rows y0-1 .. y0+8, columns x0-1 .. x0+128) are staged through a ring of 5
 // shared-memory slots filled by cp.async: planes z+2 and z+3 are in flight
 // while plane z is computed from the slots of z-1, z and z+1.  Staged
-// positions outside the grid hold NaN, which never wins a comparison.  Each lane computes the
-// codes of 4 consecutive vertices of its warp's row; the 15 candidates of a
-// vertex come from 7 row segments (ascending linear index order), each read
-// as one 16-byte shared-memory load plus one halo value passed by a warp
-// shuffle.
+// positions outside the grid hold NaN, which never wins a comparison.  Each
+// lane certifies 4 consecutive vertices of its warp's row from the two
+// largest and two smallest values of their closed neighbourhoods, read as 7
+// row segments (one 16-byte shared-memory load plus one halo value passed by
+// a warp shuffle each); the exact codes are then formed one vertex per lane,
+// only for the vertices left uncertified.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -40,8 +41,10 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// One ring slot: the staged plane of f, then fhat over the owned region (same
-// indexing, only rows 1..BY and columns 1..BX are filled).
+// One ring slot: the staged plane of f, then the plane of a second field with
+// the same indexing (fhat over the owned region only, or the start field of
+// the loop over the whole staged region when sweep 0's detection runs in the
+// pass).
 constexpr int SLOT = 2 * PLANE;
 constexpr size_t kRingBytes = (size_t)NSLOT * SLOT * sizeof(float);
 
@@ -61,57 +64,39 @@ __host__ __device__ inline TileGeom tile_geom(uint32_t nx, uint32_t ny, uint32_t
     return t;
 }
 
-// Per-lane extremes of 4 consecutive vertices.
-struct Ext4 {
-    float hv[4], lv[4];
-    uint32_t hs[4], ls[4];
-    __device__ __forceinline__ void init() {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            hv[e] = -__int_as_float(0x7f800000);
-            lv[e] = __int_as_float(0x7f800000);
-            hs[e] = kSelf;
-            ls[e] = kSelf;
-        }
-    }
-    template <bool MASK>
-    __device__ __forceinline__ void take(int e, float w, uint32_t slot, bool ok) {
-        if ((!MASK || ok) && w >= hv[e]) { hv[e] = w; hs[e] = slot; }
-        if ((!MASK || ok) && w < lv[e]) { lv[e] = w; ls[e] = slot; }
-    }
-    __device__ __forceinline__ uint32_t code(int e) const { return hs[e] | (ls[e] << 4); }
-};
+// NaN-propagating min / max (PTX min.NaN / max.NaN): a NaN operand gives NaN.
+__device__ __forceinline__ float fmin_nan(float a, float b) {
+    float d;
+    asm("min.NaN.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+__device__ __forceinline__ float fmax_nan(float a, float b) {
+    float d;
+    asm("max.NaN.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
 
-// Per-lane extremes of 4 consecutive vertices with the runner-up values: the
-// margins hv - h2 and l2 - lv decide whether a vertex can ever be distorted.
-struct Ext4M {
+// Per-lane two largest and two smallest values of the closed neighbourhoods
+// of 4 consecutive vertices (ties count twice: equal values give a zero
+// margin).  The margins hv - h2 and l2 - lv decide whether a vertex can ever
+// be distorted; the winners' slots are not tracked.
+struct Top2x4 {
     float hv[4], h2[4], lv[4], l2[4];
-    uint32_t hs[4], ls[4];
     __device__ __forceinline__ void init() {
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             hv[e] = h2[e] = -__int_as_float(0x7f800000);
             lv[e] = l2[e] = __int_as_float(0x7f800000);
-            hs[e] = kSelf;
-            ls[e] = kSelf;
         }
     }
-    template <bool MASK>
-    __device__ __forceinline__ void take(int e, float w, uint32_t slot, bool ok) {
-        if (!MASK || ok) {
-            // a NaN candidate (outside the grid) fails both tests and leaves
-            // every running value unchanged (fmaxf / fminf ignore NaN)
-            const bool p = w >= hv[e];
-            h2[e] = fmaxf(h2[e], p ? hv[e] : w);
-            hv[e] = fmaxf(hv[e], w);
-            hs[e] = p ? slot : hs[e];
-            const bool q = w < lv[e];
-            l2[e] = fminf(l2[e], q ? lv[e] : w);
-            lv[e] = fminf(lv[e], w);
-            ls[e] = q ? slot : ls[e];
-        }
+    // A NaN candidate (outside the grid) leaves all four values unchanged:
+    // min.NaN / max.NaN turn it into NaN, which fmaxf / fminf then ignore.
+    __device__ __forceinline__ void take(int e, float w) {
+        h2[e] = fmaxf(h2[e], fmin_nan(hv[e], w));
+        hv[e] = fmaxf(hv[e], w);
+        l2[e] = fminf(l2[e], fmax_nan(lv[e], w));
+        lv[e] = fminf(lv[e], w);
     }
-    __device__ __forceinline__ uint32_t code(int e) const { return hs[e] | (ls[e] << 4); }
     // Certified: in f the winner beats the runner-up by more than 2 xi in both
     // directions (differences rounded down), so no g with |g - f| <= xi can
     // change either winner.
@@ -143,104 +128,91 @@ __device__ __forceinline__ Seg seg_right(const float *row, uint32_t lane) {
     return s;
 }
 
-// Domain predicates of one lane's 4 vertices (used only on edge warps).
-struct Dom {
-    bool xm[4], xp[4];  // x-1 / x+1 inside
-    bool ym, yp, zm, zp;
-};
-
-// Codes of the 4 vertices of this lane in the field staged at pm / p0 / pp
-// (planes z-1, z, z+1; each pointer at the start of the tile plane) for warp
-// row r (1 .. BY).  Candidates in ascending linear index order:
-//   (y-1,z-1): 13 12   (y,z-1): 11 9   (y-1,z): 10 8   (y,z): 7 SELF 0
-//   (y+1,z): 1 3       (y,z+1): 2 4    (y+1,z+1): 5 6
-template <bool MASK, class EXT>
-__device__ __forceinline__ void codes4_into(const float *pm, const float *p0, const float *pp, int r, uint32_t lane,
-                                            const Dom &d, EXT &x) {
+// Certification bits (bit e) of the 4 vertices of this lane in the field
+// staged at pm / p0 / pp (planes z-1, z, z+1; each pointer at the start of the
+// tile plane) for warp row r (1 .. BY).  The 15 values of a closed
+// neighbourhood come from 7 row segments: (y-1,z-1) and (y,z-1) at x-1, x;
+// (y-1,z) at x-1, x; (y,z) at x-1, x, x+1; (y+1,z), (y,z+1) and (y+1,z+1) at
+// x, x+1.  Every staged position outside the grid holds NaN, so no domain
+// mask is needed.
+__device__ __forceinline__ uint32_t cert4(const float *pm, const float *p0, const float *pp, int r, uint32_t lane,
+                                          float two_xi) {
+    Top2x4 x;
     x.init();
-    {
-        const Seg s = seg_left(pm + (r - 1) * PW, lane);  // (y-1, z-1): x-1, x
+    auto pair_left = [&](const float *row) {  // x-1 and x
+        const Seg s = seg_left(row, lane);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            x.template take<MASK>(e, s.v[e], 13, d.xm[e] && d.ym && d.zm);
-            x.template take<MASK>(e, s.v[e + 1], 12, d.ym && d.zm);
+            x.take(e, s.v[e]);
+            x.take(e, s.v[e + 1]);
         }
-    }
-    {
-        const Seg s = seg_left(pm + r * PW, lane);  // (y, z-1): x-1, x
+    };
+    auto pair_right = [&](const float *row) {  // x and x+1
+        const Seg s = seg_right(row, lane);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            x.template take<MASK>(e, s.v[e], 11, d.xm[e] && d.zm);
-            x.template take<MASK>(e, s.v[e + 1], 9, d.zm);
+            x.take(e, s.v[e]);
+            x.take(e, s.v[e + 1]);
         }
-    }
+    };
+    pair_left(pm + (r - 1) * PW);
+    pair_left(pm + r * PW);
+    pair_left(p0 + (r - 1) * PW);
     {
-        const Seg s = seg_left(p0 + (r - 1) * PW, lane);  // (y-1, z): x-1, x
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            x.template take<MASK>(e, s.v[e], 10, d.xm[e] && d.ym);
-            x.template take<MASK>(e, s.v[e + 1], 8, d.ym);
-        }
-    }
-    {
-        const Seg s = seg_left(p0 + r * PW, lane);  // (y, z): x-1, x
+        const Seg s = seg_left(p0 + r * PW, lane);  // (y, z): x-1, x, x+1
         float right = __shfl_down_sync(kFull, s.v[1], 1);
         if (lane == 31) right = p0[r * PW + 4 + BX];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            x.template take<MASK>(e, s.v[e], 7, d.xm[e]);
-            x.template take<false>(e, s.v[e + 1], kSelf, true);
-            x.template take<MASK>(e, e < 3 ? s.v[e + 2] : right, 0, d.xp[e]);
+            x.take(e, s.v[e]);
+            x.take(e, s.v[e + 1]);
+            x.take(e, e < 3 ? s.v[e + 2] : right);
         }
     }
-    {
-        const Seg s = seg_right(p0 + (r + 1) * PW, lane);  // (y+1, z): x, x+1
+    pair_right(p0 + (r + 1) * PW);
+    pair_right(pp + r * PW);
+    pair_right(pp + (r + 1) * PW);
+    uint32_t cert = 0;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            x.template take<MASK>(e, s.v[e], 1, d.yp);
-            x.template take<MASK>(e, s.v[e + 1], 3, d.xp[e] && d.yp);
-        }
-    }
-    {
-        const Seg s = seg_right(pp + r * PW, lane);  // (y, z+1): x, x+1
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            x.template take<MASK>(e, s.v[e], 2, d.zp);
-            x.template take<MASK>(e, s.v[e + 1], 4, d.xp[e] && d.zp);
-        }
-    }
-    {
-        const Seg s = seg_right(pp + (r + 1) * PW, lane);  // (y+1, z+1): x, x+1
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            x.template take<MASK>(e, s.v[e], 5, d.yp && d.zp);
-            x.template take<MASK>(e, s.v[e + 1], 6, d.xp[e] && d.yp && d.zp);
-        }
-    }
+    for (int e = 0; e < 4; ++e) cert |= (uint32_t)x.certified(e, two_xi) << e;
+    return cert;
 }
 
-template <bool MASK>
-__device__ __forceinline__ void codes4(const float *pm, const float *p0, const float *pp, int r, uint32_t lane,
-                                       const Dom &d, uint32_t out[4]) {
-    Ext4 x;
-    codes4_into<MASK>(pm, p0, pp, r, lane, d, x);
+// Position of the k-th set bit (k counted from 0) of w; k < popc(w).
+__device__ __forceinline__ uint32_t nth_set(uint32_t w, uint32_t k) {
+    uint32_t pos = 0;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) out[e] = x.code(e);
+    for (int s = 16; s > 0; s >>= 1) {
+        const uint32_t lo = (uint32_t)__popc(w & ((1u << s) - 1u));
+        if (k >= lo) {
+            k -= lo;
+            w >>= s;
+            pos += (uint32_t)s;
+        }
+    }
+    return pos;
 }
 
-// Codes plus the certification bit (bit e of cert) of the 4 vertices.  Every
-// staged position outside the grid holds NaN, so no domain mask is needed.
-__device__ __forceinline__ void codes4_cert(const float *pm, const float *p0, const float *pp, int r, uint32_t lane,
-                                            float two_xi, uint32_t out[4], uint32_t &cert) {
-    Ext4M x;
-    const Dom d{};
-    codes4_into<false>(pm, p0, pp, r, lane, d, x);
-    cert = 0;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        out[e] = x.code(e);
-        cert |= (uint32_t)x.certified(e, two_xi) << e;
-    }
+// Code (n_max slot | n_min slot << 4) of one vertex (staged column c, warp row
+// r) in the field staged at pm / p0 / pp.  Candidates in ascending linear
+// index order, the later one winning a tie for the maximum and the earlier
+// one for the minimum; NaN (outside the grid) never wins.
+__device__ __forceinline__ uint32_t code1(const float *pm, const float *p0, const float *pp, int r, int c) {
+    float hv = -__int_as_float(0x7f800000), lv = __int_as_float(0x7f800000);
+    uint32_t hs = kSelf, ls = kSelf;
+    auto take = [&](float w, uint32_t s) {
+        if (w >= hv) { hv = w; hs = s; }
+        if (w < lv) { lv = w; ls = s; }
+    };
+    const int a = (r - 1) * PW + c, b = r * PW + c, d = (r + 1) * PW + c;
+    take(pm[a - 1], 13); take(pm[a], 12);
+    take(pm[b - 1], 11); take(pm[b], 9);
+    take(p0[a - 1], 10); take(p0[a], 8);
+    take(p0[b - 1], 7);  take(p0[b], kSelf); take(p0[b + 1], 0);
+    take(p0[d], 1);      take(p0[d + 1], 3);
+    take(pp[b], 2);      take(pp[b + 1], 4);
+    take(pp[d], 5);      take(pp[d + 1], 6);
+    return hs | (ls << 4);
 }
 
 }  // namespace tile

@@ -107,3 +107,28 @@ def test_learned_arguments_rejected_on_host():
     assert lib.msz_learned_features(a, a, F(1e-3), g2, a, a, a, None) == api.ERR_INVALID_ARG
     assert lib.msz_learned_adam(a, a, a, a, 10, F(1e-3), F(0.9), F(0.999), F(1e-8), 0, None) == api.ERR_INVALID_ARG
     assert int(lib.msz_learned_weight_image_size(32, 16)) == 27 * 32 * 16 * 2
+
+
+def test_relaxed_arguments_rejected_on_host():
+    from paper_2601_01787_gb300 import api
+    lib = api.load()
+    fake = ctypes.c_void_p(256)
+    cnt = ctypes.c_int64()
+    g2 = api.grid_of((8, 9))
+    g3 = api.grid_of((4, 5, 6))
+    assert lib.msz_relaxed_workspace_size(g2) == 0
+    assert lib.msz_relaxed_workspace_size(g3) > lib.msz_workspace_size(g3)
+    st = lib.msz_correct_relaxed(fake, fake, ctypes.c_float(0.1), g2, fake, None, None, 0, ctypes.byref(cnt), None,
+                                 None, fake, 1 << 30, None)
+    assert st == api.ERR_INVALID_ARG  # 3D only
+    opt, _ = api._options("halve", 0, 0, None, 0, 0, 1)  # the test hook is not offered here
+    st = lib.msz_correct_relaxed(fake, fake, ctypes.c_float(0.1), g3, fake, None, None, 0, ctypes.byref(cnt),
+                                 ctypes.byref(opt), None, fake, 1 << 30, None)
+    assert st == api.ERR_INVALID_ARG
+    opt, _ = api._options("halve", 0, 0, None, 0, 0, 0, -1)  # negative local cap
+    st = lib.msz_correct_relaxed(fake, fake, ctypes.c_float(0.1), g3, fake, None, None, 0, ctypes.byref(cnt),
+                                 ctypes.byref(opt), None, fake, 1 << 30, None)
+    assert st == api.ERR_INVALID_ARG
+    st = lib.msz_correct_relaxed(fake, fake, ctypes.c_float(0.1), g3, fake, None, None, 0, ctypes.byref(cnt), None,
+                                 None, fake, 16, None)
+    assert st == api.ERR_WORKSPACE

@@ -144,3 +144,21 @@ def test_batch_plan_launch_matches_one_call(api):
         assert np.array_equal(a.sweep_log, b.sweep_log)
         assert {k: v for k, v in a.stats.items() if not k.endswith("_ns")} == \
             {k: v for k, v in b.stats.items() if not k.endswith("_ns")}
+
+
+def test_batch_at_the_field_limit(api):
+    """MSZ_BATCH_MAX_FIELDS tiny uneven fields in one launch, each equal to its
+    own correction; one more field is rejected."""
+    n = api.BATCH_MAX_FIELDS
+    shapes = [(2 + k % 5, 3 + k % 7, 5 + k % 11) for k in range(n)]
+    fields = [synth.perlin3d_prequant(s, seed=3000 + k, eb_rel=1e-3, octaves=2) for k, s in enumerate(shapes)]
+    fs = [torch.from_numpy(fl.f).cuda() for fl in fields]
+    fhs = [torch.from_numpy(fl.fhat).cuda() for fl in fields]
+    res = api.correct_batch(fs, fhs, [fl.xi for fl in fields])
+    assert res.status == api.OK
+    for k in range(0, n, 17):
+        one = api.correct(fs[k], fhs[k], fields[k].xi)
+        assert res.fields[k].status == one.status
+        assert np.array_equal(_bits(res.fields[k].out), _bits(one.out))
+    with pytest.raises(api.MszError):
+        api.correct_batch(fs + fs[:1], fhs + fhs[:1], [fl.xi for fl in fields] + [fields[0].xi])
