@@ -131,14 +131,15 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------- roofline
-def algorithmic_bytes(n: int, log: np.ndarray, edited: int) -> int:
+def algorithmic_bytes(n: int, log: np.ndarray, edited: int, uncertified: int) -> int:
     """Compulsory HBM bytes of one correction:
-    sweep 0 reads f, fhat and writes codes_f, g (13 B/vertex); a later sweep
+    sweep 0 reads f, fhat and writes g (12 B/vertex) and the code of f at
+    each uncertified vertex (1 B; no other vertex's code is ever read); a later sweep
     reads g and codes_f of every examined vertex (5 B each: the whole grid for
     dense sweeps, the worklist otherwise); every distinct target reads f and g
     and writes g (12 B); the edit list reads the edited bitmap (N/8 B) and
     writes 8 B per edit."""
-    total = 13 * n
+    total = 12 * n + uncertified
     for k in range(1, log.shape[0]):
         total += 5 * int(log[k, 0])
     total += 12 * int(log[:, 2].sum())
@@ -148,18 +149,20 @@ def algorithmic_bytes(n: int, log: np.ndarray, edited: int) -> int:
 
 # ALU operations of one steepest-neighbour code over the 14 neighbours and
 # the vertex itself: per candidate and direction a compare, a value select and
-# a slot select (3 ops); the certification of sweep 0 adds the runner-up value
-# (a select and a min/max: 2 ops) per candidate and direction.
+# a slot select (3 ops).  The certification of sweep 0 keeps the two largest
+# and two smallest values instead: per candidate and direction a
+# NaN-propagating min / max against the leader, a max / min into the
+# runner-up and one into the leader (3 ops).
 ALU_OPS_CODE = 14 * 2 * 3
-ALU_OPS_CODE_CERT = 14 * 2 * 5
+ALU_OPS_CERT = 14 * 2 * 3
 
 
 def algorithmic_alu_ops(n: int, log: np.ndarray, uncertified: int) -> int:
-    """ALU operations of one correction: the certified codes of f at every
-    vertex, the codes of g at the uncertified vertices in sweep 0 and at every
-    vertex examined by a later sweep (dense sweeps examine the uncertified
-    ones)."""
-    total = ALU_OPS_CODE_CERT * n + ALU_OPS_CODE * uncertified
+    """ALU operations of one correction: the certification of every vertex,
+    the codes of f and g at the uncertified vertices in sweep 0, and the codes
+    of g at every vertex examined by a later sweep (dense sweeps examine the
+    uncertified ones)."""
+    total = ALU_OPS_CERT * n + 2 * ALU_OPS_CODE * uncertified
     for k in range(1, log.shape[0]):
         total += ALU_OPS_CODE * min(int(log[k, 0]), uncertified)
     return total
@@ -250,7 +253,7 @@ def run_ours(args, ws, rank, local):
     # roofline of the (single) correction kernel
     peak, peak_kind = load_peaks()
     log = first.sweep_log
-    alg = algorithmic_bytes(n, log, first.edit_count)
+    alg = algorithmic_bytes(n, log, first.edit_count, first.stats["uncertified"])
     kernel_ms = statistics.mean(kernel_ns) / 1e6
     achieved = alg / (ms_local * 1e-3) / 1e9
     traffic = None
