@@ -377,6 +377,59 @@ msz_status msz_correct_static(const float *d_f, const float *d_fhat, float xi, m
                               int64_t *h_edit_count, const msz_options *opt, msz_stats *h_stats,
                               msz_stream_t stream);
 
+/* ---- Edit-list encoding.  The paper stores the corrected field as the
+ * decompressed field plus its edits and counts their storage as the method's
+ * overhead (Sec. V, computation and storage overhead); it fixes no format.
+ * This one is exact and decodes block by block in parallel.
+ *
+ * An edit is (i, m): a vertex i where g and fhat differ bitwise and its ulp
+ * distance m = (ord(fhat_i) - ord(g_i)) mod 2^32, where ord maps a float's
+ * bits b to an unsigned key in value order (b | 0x80000000 when the sign bit
+ * is clear, ~b when it is set); g_i = ord^-1(ord(fhat_i) - m) bit for bit.
+ * Stream (little-endian), B = MSZ_EDIT_BLOCK, nb = ceil(count / B):
+ *   u32 MSZ_EDIT_MAGIC, u32 B, u64 count;
+ *   nb x u32: the first index of each block;
+ *   nb x u32: where each block's payload starts, in 32-bit words from the
+ *             start of the payload;
+ *   nb x u8 wd (bit width of the block's index gaps), nb x u8 wm (bit width
+ *   of its ulp distances minus one); zero bytes up to a multiple of 4;
+ *   payload, per block of c edits: d_j (d_0 = 0, d_j = i_j - i_{j-1} - 1)
+ *   packed wd bits each, LSB first, into 32-bit words (value j at bit j*wd
+ *   of the section), padded to a whole word; then (m_j - 1) mod 2^32 packed
+ *   wm bits each the same way.
+ * A width is the bit length of its section's largest value (0: no words). */
+#define MSZ_EDIT_MAGIC 0x45535A4Du
+#define MSZ_EDIT_BLOCK 256
+
+/* Largest stream of `count` edits (bytes): the table plus 8 bytes an edit. */
+size_t msz_edits_encoded_bound(int64_t count);
+/* Device workspace of msz_edits_encode / msz_edits_decode for `count` edits:
+ * 256 bytes plus about 10 bytes a block.  0 when count < 0. */
+size_t msz_edits_workspace_size(int64_t count);
+
+/* Encodes the edits at d_idx[0 .. count) (strictly ascending vertex indices
+ * below n, as msz_correct lists them) of g = d_g against d_fhat (n floats
+ * each) into d_stream (capacity bytes, 4-byte aligned); *h_bytes = the
+ * stream's length.  Workspace: msz_edits_workspace_size(count) bytes, 256-byte
+ * aligned.  MSZ_ERR_INVALID_ARG: a null pointer, n outside [0,
+ * MSZ_MAX_VERTICES], count outside [0, n], a misaligned d_stream, or indices
+ * not strictly ascending or not below n (nothing is written to d_stream);
+ * MSZ_ERR_CAPACITY: the stream needs more than capacity bytes (*h_bytes =
+ * needed; nothing is written); MSZ_ERR_WORKSPACE.  Synchronizes `stream`. */
+msz_status msz_edits_encode(const float *d_fhat, const float *d_g, int64_t n, const uint32_t *d_idx, int64_t count,
+                            uint8_t *d_stream, size_t capacity, size_t *h_bytes, void *d_workspace,
+                            size_t workspace_bytes, msz_stream_t stream);
+
+/* Applies the stream d_stream (bytes long, 4-byte aligned) to d_field (n
+ * floats: fhat on entry, g on return); *h_count = its number of edits.
+ * Workspace: msz_edits_workspace_size(*h_count) bytes (the count is in bytes
+ * 8..15 of the stream).  MSZ_ERR_INVALID_ARG: not a stream of this format,
+ * shorter than its table or payload, a width above 32, an index not below n
+ * or indices not ascending -- the whole stream is checked before d_field is
+ * touched.  Synchronizes `stream`. */
+msz_status msz_edits_decode(const uint8_t *d_stream, size_t bytes, float *d_field, int64_t n, int64_t *h_count,
+                            void *d_workspace, size_t workspace_bytes, msz_stream_t stream);
+
 /* Human-readable name of a status. */
 const char *msz_status_str(msz_status status);
 

@@ -36,6 +36,7 @@ UNITS = [
     ("msz_batch.cu", EXACT),
     ("msz_relaxed.cu", EXACT),
     ("msz_learned.cu", []),
+    ("msz_edits.cu", []),
 ]
 
 

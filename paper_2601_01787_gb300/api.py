@@ -119,6 +119,14 @@ def load(build_if_missing: bool = True):
         lib.msz_relaxed_workspace_size.restype = SZ
         lib.msz_correct_relaxed.argtypes = lib.msz_correct.argtypes
         lib.msz_correct_relaxed.restype = st
+        lib.msz_edits_encoded_bound.argtypes = [I64]
+        lib.msz_edits_encoded_bound.restype = SZ
+        lib.msz_edits_workspace_size.argtypes = [I64]
+        lib.msz_edits_workspace_size.restype = SZ
+        lib.msz_edits_encode.argtypes = [P, P, I64, P, I64, P, SZ, ctypes.POINTER(SZ), P, SZ, P]
+        lib.msz_edits_encode.restype = st
+        lib.msz_edits_decode.argtypes = [P, SZ, P, I64, ctypes.POINTER(I64), P, SZ, P]
+        lib.msz_edits_decode.restype = st
         lib.msz_status_str.argtypes = [st]
         lib.msz_status_str.restype = ctypes.c_char_p
         _lib = lib
@@ -475,3 +483,50 @@ def correct_batch(fs, fhats, xis, *, rule="halve", max_sweeps: int = 0, dense_mi
     st = lib.msz_correct_batch(len(arr), arr, ctypes.byref(opt), log.ctypes.data if log_capacity else None,
                                log_capacity, _dptr(ws), ws.numel(), _stream(stream))
     return _batch_results(arr, keep, log, log_capacity, st)
+
+
+# ------------------------------------------------------------ edit encoding
+EDIT_MAGIC = 0x45535A4D
+EDIT_BLOCK = 256
+
+
+def encode_edits(fhat: torch.Tensor, g: torch.Tensor, edit_idx: torch.Tensor, stream=None) -> torch.Tensor:
+    """Stream of the edit list edit_idx (ascending int32/uint32 vertex indices,
+    as correct() returns them) of g against fhat (msz_edits_encode): a uint8
+    CUDA tensor of the stream's length."""
+    lib = load()
+    n = fhat.numel()
+    if g.numel() != n or fhat.dtype != torch.float32 or g.dtype != torch.float32:
+        raise ValueError("fhat and g must be float32 tensors of one size")
+    if edit_idx.dtype not in (torch.int32, torch.uint32):
+        raise ValueError("edit_idx must be int32 or uint32")
+    count = edit_idx.numel()
+    cap = int(lib.msz_edits_encoded_bound(count))
+    out = torch.empty(cap, dtype=torch.uint8, device=fhat.device)
+    ws = workspace(int(lib.msz_edits_workspace_size(count)), fhat.device)
+    nbytes = ctypes.c_size_t(0)
+    st = lib.msz_edits_encode(_dptr(fhat), _dptr(g), n, _dptr(edit_idx) if count else None, count, _dptr(out), cap,
+                              ctypes.byref(nbytes), _dptr(ws), ws.numel(), _stream(stream))
+    if st != OK:
+        raise MszError(st, "msz_edits_encode")
+    return out[:nbytes.value]
+
+
+def decode_edits(stream_bytes: torch.Tensor, field: torch.Tensor, stream=None) -> int:
+    """Applies an edit stream to `field` in place (fhat in, g out;
+    msz_edits_decode) and returns its edit count."""
+    lib = load()
+    if stream_bytes.dtype != torch.uint8 or field.dtype != torch.float32:
+        raise ValueError("expected a uint8 stream and a float32 field")
+    if stream_bytes.numel() < 16:
+        raise MszError(ERR_INVALID_ARG, "msz_edits_decode")
+    count = int(stream_bytes[8:16].cpu().view(torch.int64)[0])
+    if count < 0 or count > field.numel():
+        raise MszError(ERR_INVALID_ARG, "msz_edits_decode")
+    ws = workspace(int(lib.msz_edits_workspace_size(max(count, 0))), field.device)
+    got = ctypes.c_int64(0)
+    st = lib.msz_edits_decode(_dptr(stream_bytes), stream_bytes.numel(), _dptr(field), field.numel(),
+                              ctypes.byref(got), _dptr(ws), ws.numel(), _stream(stream))
+    if st != OK:
+        raise MszError(st, "msz_edits_decode")
+    return int(got.value)

@@ -132,3 +132,32 @@ def test_relaxed_arguments_rejected_on_host():
     st = lib.msz_correct_relaxed(fake, fake, ctypes.c_float(0.1), g3, fake, None, None, 0, ctypes.byref(cnt), None,
                                  None, fake, 16, None)
     assert st == api.ERR_WORKSPACE
+
+
+def test_edit_encoding_sizes_and_arguments_on_host():
+    from oracle import edits as E
+    from paper_2601_01787_gb300 import api
+    lib = api.load()
+    for count in (0, 1, 3, 256, 257, 100000):
+        nb = (count + 255) // 256
+        table = 16 + 10 * nb + (-(10 * nb) % 4)
+        assert lib.msz_edits_encoded_bound(count) == table + 8 * count
+        assert lib.msz_edits_workspace_size(count) >= 256 + 10 * nb
+    worst = E.encode([0, 1 << 30, (1 << 31) - 1], [0, 0, 0])  # 30-bit gaps, 32-bit distances
+    assert len(worst) <= lib.msz_edits_encoded_bound(3)
+    assert lib.msz_edits_encoded_bound(-1) == 0 and lib.msz_edits_workspace_size(-1) == 0
+    fake = ctypes.c_void_p(256)
+    nbytes = ctypes.c_size_t()
+    cnt = ctypes.c_int64()
+    ws = 1 << 20
+    enc = lib.msz_edits_encode
+    assert enc(None, fake, 10, fake, 3, fake, 64, ctypes.byref(nbytes), fake, ws, None) == api.ERR_INVALID_ARG
+    assert enc(fake, fake, 10, fake, 11, fake, 64, ctypes.byref(nbytes), fake, ws, None) == api.ERR_INVALID_ARG
+    assert enc(fake, fake, 10, None, 3, fake, 64, ctypes.byref(nbytes), fake, ws, None) == api.ERR_INVALID_ARG
+    assert enc(fake, fake, 10, fake, 3, ctypes.c_void_p(258), 64, ctypes.byref(nbytes), fake, ws,
+               None) == api.ERR_INVALID_ARG  # stream not 4-byte aligned
+    assert enc(fake, fake, 10, fake, 3, fake, 64, ctypes.byref(nbytes), fake, 8, None) == api.ERR_WORKSPACE
+    dec = lib.msz_edits_decode
+    assert dec(None, 64, fake, 10, ctypes.byref(cnt), fake, ws, None) == api.ERR_INVALID_ARG
+    assert dec(fake, 15, fake, 10, ctypes.byref(cnt), fake, ws, None) == api.ERR_INVALID_ARG
+    assert dec(ctypes.c_void_p(257), 64, fake, 10, ctypes.byref(cnt), fake, ws, None) == api.ERR_INVALID_ARG
