@@ -288,6 +288,7 @@ def run_ours(args, ws, rank, local):
     snap_ms, snap = timed_ms(lambda: api.correct(f, fh, fl.xi, rule="snap", out=out, edit_idx=eidx, edit_delta=edel,
                                                  edit_capacity=cap, ws=ws_buf, stream=stream))
     step()  # leave the HALVE result in out
+    stream_stats = edit_stream(fh, out, eidx, first.edit_count, stream)
 
     # end to end through the host-buffer entry point (pinned buffers)
     hf = torch.from_numpy(fl.f).pin_memory()
@@ -340,6 +341,7 @@ def run_ours(args, ws, rank, local):
         "clocks": clk,
         "sweeps": first.stats["sweeps"], "edited": first.edit_count, "first_distorted": first.stats["first_distorted"],
         "edit_ratio": round(first.edit_count / n, 6),
+        "edit_stream": stream_stats,
         "sweep_log": log.tolist(),
         "phase_ms": [[round(a / 1e6, 4), round(b / 1e6, 4)] for a, b in first.timeline.tolist()],
         "wall_s_timed": round(wall, 4),
@@ -538,6 +540,7 @@ def run_learned(dev, stream, reps: int = 3) -> dict:
     t_plain, rp = timed(lambda: api.correct(f, fh, fl.xi, **kw))
     assert rp.status == api.OK, api.status_str(rp.status)
     vp = api.verify(f, out)
+    stream_plain = edit_stream(fh, out, eidx, rp.edit_count, stream)
     timed(lambda: learned.correct_learned(f, fh, fl.xi, net, **kw))
     t_learned, rl = timed(lambda: learned.correct_learned(f, fh, fl.xi, net, **kw))
     assert rl.result.status == api.OK, api.status_str(rl.result.status)
@@ -552,7 +555,8 @@ def run_learned(dev, stream, reps: int = 3) -> dict:
             "plain": {"ms": round(t_plain, 4), "value": round(n / (t_plain * 1e-3) / 1e9, 4),
                       "sweeps": rp.stats["sweeps"], "first_distorted": rp.stats["first_distorted"],
                       "edited": rp.edit_count, "kernel_ms": round(rp.stats["kernel_ns"] / 1e6, 4),
-                      "verified": bool(vp["codes_equal"] and vp["wrong_labels"] == 0)},
+                      "verified": bool(vp["codes_equal"] and vp["wrong_labels"] == 0),
+                      "edit_stream": stream_plain},
             "learned": {"ms": round(t_learned, 4), "value": round(n / (t_learned * 1e-3) / 1e9, 4),
                         "propose_ms": round(rl.propose_ms, 4),
                         "loop_kernel_ms": round(rl.from_g0.stats["kernel_ns"] / 1e6, 4),
@@ -566,6 +570,41 @@ def run_learned(dev, stream, reps: int = 3) -> dict:
             "training": {"recipe": learned.RECIPE | {"shape": list(learned.RECIPE["shape"])},
                          "cached": info["cached"], "train_s": None if info.get("train_s") is None else
                          round(info["train_s"], 2), "final_loss": info.get("final_loss")}}
+
+
+def edit_stream(fh, g, eidx, count: int, stream, reps: int = 3) -> dict:
+    """The edit list of a corrected field as an encoded stream
+    (msz_edits_encode): its length against the raw 8-byte (index, delta)
+    pairs, and the device time of encoding it and of decoding it onto a copy
+    of fhat (checked to give back g bit for bit)."""
+    import torch
+
+    from paper_2601_01787_gb300 import api
+    fh1, g1, idx = fh.reshape(-1), g.reshape(-1), eidx[:count]
+    field = torch.empty_like(fh1)
+
+    def timed(fn):
+        fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            res = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps, res
+
+    enc_ms, s = timed(lambda: api.encode_edits(fh1, g1, idx, stream=stream))
+
+    def dec():
+        field.copy_(fh1)
+        return api.decode_edits(s, field, stream=stream)
+
+    dec_ms, got = timed(dec)
+    exact = got == count and torch.equal(field.view(torch.int32), g1.view(torch.int32))
+    nbytes = int(s.numel())
+    return {"edits": count, "bytes": nbytes, "bytes_per_edit": round(nbytes / max(count, 1), 4),
+            "raw_bytes_per_edit": 8, "ratio_vs_raw": round(8 * count / max(nbytes, 1), 3),
+            "encode_ms": round(enc_ms, 4), "decode_ms": round(dec_ms, 4), "decode_exact": bool(exact)}
 
 
 def conv_flops_per_voxel(cin: int, cout: int) -> int:
