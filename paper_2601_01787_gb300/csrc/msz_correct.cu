@@ -168,18 +168,27 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
     }
     if (!ok) return;
 
-    // ---- edit list: every vertex of the edited bitmap, ascending index
+    // ---- edit list: every vertex of the edited bitmap, ascending index.
+    // Each warp owns a contiguous range of bitmap words; a block scan of the
+    // warps' counts and a grid-wide prefix over the blocks give each warp its
+    // first output position, and the warp then writes its range 32 words at
+    // a time with warp scans only.
     const uint32_t W = G.words;
-    const uint32_t per = (W + gridDim.x - 1) / gridDim.x;
-    const uint32_t w0 = min(blockIdx.x * per, W), w1 = min(w0 + per, W);
+    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    const uint32_t nwarps = gridDim.x * wpb;
+    const uint32_t per = (W + nwarps - 1) / nwarps;
+    const uint32_t gw = blockIdx.x * wpb + warp;
+    const uint32_t w0 = min(gw * per, W), w1 = min(w0 + per, W);
     uint32_t cnt = 0, unc = 0;
-    for (uint32_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) {
+    for (uint32_t w = w0 + lane; w < w1; w += 32) {
         cnt += __popc(F.eb[w]);
         unc += __popc(F.ub[w]);
     }
     warp_add(unc, &C->uncertified);
     uint32_t tot;
-    block_exclusive_scan(cnt, sm, tot);
+    const uint32_t wcnt = __reduce_add_sync(kFull, cnt);
+    const uint32_t wpre = block_exclusive_scan(lane == 0 ? wcnt : 0u, sm, tot);
+    const uint32_t warp_pre = __shfl_sync(kFull, wpre, 0);  // this warp's offset in its block
     if (threadIdx.x == 0) P.bsum[blockIdx.x] = tot;
     if (!grid_barrier(&C->bar_count, &C->bar_gen, &C->error)) return;
     uint32_t pre = 0, all = 0;
@@ -188,16 +197,22 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
         all += s;
         if (b < blockIdx.x) pre += s;
     }
-    uint32_t prefix;
-    block_exclusive_scan(pre, sm, prefix);
+    uint32_t bpre;
+    block_exclusive_scan(pre, sm, bpre);
     block_exclusive_scan(all, sm, all);
     if (leader) C->edit_count = all;
-    for (uint32_t r = w0; r < w1; r += blockDim.x) {
-        const uint32_t w = r + threadIdx.x;
+    unsigned long long prefix = (unsigned long long)bpre + warp_pre;
+    for (uint32_t r = w0; r < w1; r += 32) {
+        const uint32_t w = r + lane;
         const uint32_t word = w < w1 ? F.eb[w] : 0u;
-        uint32_t rt;
-        const uint32_t ex = block_exclusive_scan((uint32_t)__popc(word), sm, rt);
-        unsigned long long pos = (unsigned long long)prefix + ex;
+        const uint32_t c = (uint32_t)__popc(word);
+        uint32_t incl = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, incl, d);
+            if (lane >= (uint32_t)d) incl += y;
+        }
+        unsigned long long pos = prefix + incl - c;
         uint32_t bits = word;
         while (bits) {
             const uint32_t b = (uint32_t)(__ffs(bits) - 1);
@@ -209,7 +224,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
             }
             ++pos;
         }
-        prefix += rt;
+        prefix += __shfl_sync(kFull, incl, 31);
     }
     if (!grid_barrier(&C->bar_count, &C->bar_gen, &C->error)) return;
     if (leader) C->t_end = global_ns();

@@ -473,18 +473,43 @@ __device__ __forceinline__ void first_tiled(const FieldView &P, uint32_t *tile_n
     if (bad) atomicOr(err, kErrInput);
 }
 
-// Marks vertex t and its neighbours in bitmap bm.
+// Sets the bits of up to 3 consecutive vertices j0, j0+1, j0+2 (bit k of m
+// for vertex j0+k) with one reduction per bitmap word touched.
+__device__ __forceinline__ void mark_run(uint32_t *bm, uint32_t j0, uint32_t m) {
+    const uint32_t w = j0 >> 5, s = j0 & 31u;
+    red_or(&bm[w], m << s);
+    if (s && (m >> (32u - s))) red_or(&bm[w + 1], m >> (32u - s));
+}
+
+// Marks vertex t and its neighbours in bitmap bm.  The closed neighbourhood
+// lies on 7 grid rows in 3D (3 in 2D), each holding a run of 2 or 3
+// consecutive vertices: (y, z) at x-1 .. x+1; (y-1, z), (y, z-1) and
+// (y-1, z-1) at x-1, x; (y+1, z), (y, z+1) and (y+1, z+1) at x, x+1.  One
+// reduction marks a run (two where it crosses a word).
 template <int NDIM>
 __device__ __forceinline__ void mark_closed(const GridDev &G, uint32_t t, uint32_t *bm) {
-    red_or(&bm[t >> 5], 1u << (t & 31u));
     uint32_t x, y, z;
     coords_of(G, t, x, y, z);
-    constexpr int ns = NDIM == 2 ? 6 : 14;
-#pragma unroll
-    for (int s = 0; s < ns; ++s) {
-        if (!slot_in_domain(G, s, x, y, z)) continue;
-        const uint32_t j = (uint32_t)((int64_t)t + G.off[s]);
-        red_or(&bm[j >> 5], 1u << (j & 31u));
+    // bit 0: x-1, bit 1: x, bit 2: x+1 -- dropped outside the grid
+    const uint32_t xm = x > 0 ? 1u : 0u, xp = x + 1 < G.nx ? 4u : 0u;
+    auto row = [&](uint32_t rt, uint32_t m) {
+        m &= xm | 2u | xp;
+        if (x == 0) mark_run(bm, rt, m >> 1);
+        else mark_run(bm, rt - 1u, m);
+    };
+    const uint32_t nx = G.nx, nxy = G.nxy;
+    row(t, 7u);
+    if (y > 0) row(t - nx, 3u);
+    if (y + 1 < G.ny) row(t + nx, 6u);
+    if (NDIM == 3) {
+        if (z > 0) {
+            row(t - nxy, 3u);
+            if (y > 0) row(t - nxy - nx, 3u);
+        }
+        if (z + 1 < G.nz) {
+            row(t + nxy, 6u);
+            if (y + 1 < G.ny) row(t + nxy + nx, 6u);
+        }
     }
 }
 
