@@ -17,6 +17,8 @@
 // Target sets and worklists are bitmaps marked with fire-and-forget
 // reductions (duplicates merge for free, no warp waits on an atomic); the
 // edit and sparse detection phases walk their set bits word by word.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -40,6 +42,8 @@ constexpr int kMinBlocks = MSZ_MIN_BLOCKS;  // resident blocks per SM the regist
 constexpr uint32_t kDenseFactor = 6;        // worklist estimate: 6 x distorted vertices
 
 struct Problem {
+    CUtensorMap map_f;  // TMA maps of f and of the start field (the TMA code pass only)
+    CUtensorMap map_s;
     FieldView F;
     Ctrl *ctrl;
     SweepRec *log;
@@ -53,7 +57,7 @@ struct Problem {
 };
 
 // ------------------------------------------------------ the persistent kernel
-template <int NDIM>
+template <int NDIM, bool TMA>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constant__ const Problem P) {
     extern __shared__ __align__(16) float smem[];
     const FieldView &F = P.F;
@@ -77,7 +81,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
     bool ok;
     if (NDIM == 3) {
         uint32_t distorted = 0;
-        first_tiled<true>(F, &P.log[0].tile_next, smem, &C->error, distorted);
+        if (TMA) first_tiled_tma<true>(F, &P.map_f, &P.map_s, &P.log[0].tile_next, smem, &C->error, distorted);
+        else first_tiled<true>(F, &P.log[0].tile_next, smem, &C->error, distorted);
         warp_add(distorted, &P.log[0].distorted);
         ok = P.test_fault ? grid_barrier(&C->bar_count, &C->bar_gen, &C->error, kTestBarrierNs, blockIdx.x == 0)
                           : grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
@@ -266,20 +271,21 @@ msz_status current_device(DeviceInfo &info) {
     return MSZ_OK;
 }
 
-template <int NDIM>
-static size_t correct_smem() { return NDIM == 3 ? tile::kRingBytes : 0; }
+template <int NDIM, bool TMA>
+static size_t correct_smem() { return NDIM == 3 ? (TMA ? tile::kTmaRingBytes : tile::kRingBytes) : 0; }
 
-template <int NDIM>
+template <int NDIM, bool TMA>
 static msz_status correct_blocks(const DeviceInfo &d, int &blocks) {
     static int cache[64];
     std::lock_guard<std::mutex> lk(g_mu);
     if (!cache[d.device]) {
-        const size_t sm = correct_smem<NDIM>();
+        const size_t sm = correct_smem<NDIM, TMA>();
         if (sm > 48 * 1024 &&
-            cudaFuncSetAttribute(k_correct<NDIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+            cudaFuncSetAttribute(k_correct<NDIM, TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+                cudaSuccess)
             return MSZ_ERR_CUDA;
         int per = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_correct<NDIM>, kThreads, sm) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_correct<NDIM, TMA>, kThreads, sm) != cudaSuccess)
             return MSZ_ERR_CUDA;
         if (per < 1) return MSZ_ERR_UNSUPPORTED;
         int b = per * d.sms;
@@ -299,17 +305,65 @@ static uint32_t default_tile_z(const GridDev &G, int blocks) {
     return 8;
 }
 
-template <int NDIM>
-static msz_status run_correct(Problem &P, const DeviceInfo &dev, cudaStream_t stream) {
+// The TMA ring stages planes of the whole staged width: 3D grids whose x
+// extent is a multiple of 4 (row strides of whole 16-byte units) and at least
+// one box wide, at least one box high, with 16-byte aligned arrays.
+static bool tma_eligible(const FieldView &F) {
+    const GridDev &G = F.G;
+    auto al = [](const void *p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+    return G.ndim == 3 && G.nx % 4 == 0 && G.nx >= (uint32_t)tile::PW && G.ny >= (uint32_t)tile::ROWS && al(F.f) &&
+           al(F.fhat) && al(F.ginit) && al(F.g);
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 plane_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// Tensor map of one float field for the code pass: boxes of PW x ROWS x 1
+// (x, y, z), positions outside the grid read as NaN.
+static bool plane_map(const float *v, const GridDev &G, CUtensorMap &map) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = plane_map_encoder();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {G.nx, G.ny, G.nz};
+    cuuint64_t strides[2] = {(cuuint64_t)G.nx * 4u, (cuuint64_t)G.nxy * 4u};
+    cuuint32_t box[3] = {(cuuint32_t)tile::PW, (cuuint32_t)tile::ROWS, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)v, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NAN_REQUEST_ZERO_FMA) == CUDA_SUCCESS;
+}
+
+template <int NDIM, bool TMA>
+static msz_status launch_correct(Problem &P, const DeviceInfo &dev, cudaStream_t stream) {
     int blocks = 0;
-    msz_status st = correct_blocks<NDIM>(dev, blocks);
+    msz_status st = correct_blocks<NDIM, TMA>(dev, blocks);
     if (st != MSZ_OK) return st;
     if (P.F.tile_z == 0) P.F.tile_z = default_tile_z(P.F.G, blocks);
     void *args[] = {(void *)&P};
-    if (cudaLaunchCooperativeKernel((const void *)k_correct<NDIM>, dim3(blocks), dim3(kThreads), args,
-                                    correct_smem<NDIM>(), stream) != cudaSuccess)
+    if (cudaLaunchCooperativeKernel((const void *)k_correct<NDIM, TMA>, dim3(blocks), dim3(kThreads), args,
+                                    correct_smem<NDIM, TMA>(), stream) != cudaSuccess)
         return MSZ_ERR_CUDA;
     return MSZ_OK;
+}
+
+template <int NDIM>
+static msz_status run_correct(Problem &P, const DeviceInfo &dev, cudaStream_t stream) {
+    if constexpr (NDIM == 3) {
+        if (tma_eligible(P.F) && plane_map(P.F.f, P.F.G, P.map_f) &&
+            plane_map(P.F.ginit ? P.F.ginit : P.F.fhat, P.F.G, P.map_s))
+            return launch_correct<3, true>(P, dev, stream);
+    }
+    return launch_correct<NDIM, false>(P, dev, stream);
 }
 
 }  // namespace msz

@@ -13,6 +13,7 @@
 #include "msz.h"
 #include "msz_device.cuh"
 #include "msz_tile.cuh"
+#include "msz_tma.cuh"
 #include "msz_workspace.h"
 
 namespace msz {
@@ -272,6 +273,66 @@ __device__ void first_generic(const FieldView &P, uint32_t *err) {
     if (bad) atomicOr(err, kErrInput);
 }
 
+// One warp row of the code pass (warp-collective): row r (1 .. BY) of the
+// planes pm / p0 / pp staged at pitch PW (column c <-> x = x0 - 4 + c), the
+// second field soff floats after each plane; rowbase = the linear index of
+// (0, y, z).  Certifies the row's 128 vertices, marks the uncertified ones in
+// P.ub and forms their exact codes of f (codes_f) and, when DETECT, of the
+// second field, reporting sweep 0's distortions.
+template <bool DETECT>
+__device__ __forceinline__ void tile_row(const FieldView &P, const float *pm, const float *p0, const float *pp,
+                                         int soff, int r, int x0, uint32_t rowbase, uint32_t &distorted) {
+    using namespace tile;
+    const GridDev &G = P.G;
+    const uint32_t lane = lane_id();
+    const int xl = x0 + 4 * (int)lane;
+    const uint32_t cert = cert4(pm, p0, pp, r, lane, P.two_xi);
+    const uint32_t i0 = rowbase + (uint32_t)xl;
+    // uncertified bits of this lane's vertices (outside the grid: 0)
+    uint32_t nib = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) nib |= (uint32_t)(xl + e < (int)G.nx && !((cert >> e) & 1u)) << e;
+    // the row's 128 uncertified bits as 4 words: word q (lanes 8q .. 8q+7)
+    // covers columns 32q .. 32q+31
+    uint32_t w = nib << (4u * (lane & 7u));
+    w |= __shfl_xor_sync(kFull, w, 1);
+    w |= __shfl_xor_sync(kFull, w, 2);
+    w |= __shfl_xor_sync(kFull, w, 4);
+    const bool words_ok = ((rowbase + (uint32_t)x0) & 31u) == 0 && x0 + BX <= (int)G.nx;
+    if (words_ok) {
+        if ((lane & 7u) == 0) P.ub[i0 >> 5] = w;
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if ((nib >> e) & 1u) red_or(&P.ub[(i0 + e) >> 5], 1u << ((i0 + e) & 31u));
+    }
+    // The row's uncertified vertices, 32 at a time in column order (lane j
+    // takes the j-th one): the exact code in f, written to codes_f (the loop
+    // reads codes_f at uncertified vertices only) and, when this pass
+    // detects, the code in the second field, compared with it.
+    const uint32_t w0 = __shfl_sync(kFull, w, 0), w1 = __shfl_sync(kFull, w, 8);
+    const uint32_t w2 = __shfl_sync(kFull, w, 16), w3 = __shfl_sync(kFull, w, 24);
+    const uint32_t c0 = (uint32_t)__popc(w0), c1 = c0 + (uint32_t)__popc(w1);
+    const uint32_t c2 = c1 + (uint32_t)__popc(w2), total = c2 + (uint32_t)__popc(w3);
+    Emitter E{P.dm[1], 0};
+    for (uint32_t j0 = 0; j0 < total; j0 += 32u) {
+        const uint32_t j = j0 + lane;
+        const bool has = j < total;
+        uint32_t col = 0, cf = 0, cg = 0;
+        if (has) {
+            const uint32_t q = j < c0 ? 0u : j < c1 ? 1u : j < c2 ? 2u : 3u;
+            const uint32_t wq = q == 0 ? w0 : q == 1 ? w1 : q == 2 ? w2 : w3;
+            const uint32_t before = q == 0 ? 0u : q == 1 ? c0 : q == 2 ? c1 : c2;
+            col = 32u * q + nth_set(wq, j - before);
+            cf = code1(pm, p0, pp, r, 4 + (int)col);
+            P.codes_f[rowbase + (uint32_t)x0 + col] = (uint8_t)cf;
+            if (DETECT) cg = code1(pm + soff, p0 + soff, pp + soff, r, 4 + (int)col);
+        }
+        if (DETECT) report(P, E, has, rowbase + (uint32_t)x0 + col, cf, cg);
+    }
+    distorted += E.distorted;
+}
+
 // ------------------------------------------------ tiled (3D) codes of f
 // One tile (x0, y0, planes zb .. ze-1) of field P: certification of every
 // vertex, codes of f at the uncertified ones, g = start value, bound check
@@ -388,7 +449,6 @@ __device__ __forceinline__ void first_tile(const FieldView &P, int x0, int y0, i
     issue(zb + 1);
     issue(zb + 2);
     const int y = y0 + (int)warp, r = (int)warp + 1;
-    const int xl = x0 + 4 * (int)lane;
     for (int z = zb; z < ze; ++z) {
         cp_async_wait<1>();  // planes up to z+1 of this thread have landed (z+2 may be in flight)
         __syncthreads();     // ... of every thread; the slot of z-2 is free
@@ -396,54 +456,8 @@ __device__ __forceinline__ void first_tile(const FieldView &P, int x0, int y0, i
         own(z);
         if (y >= (int)G.ny) continue;
         auto plane = [&](int p) { return smem + ((p - zb + 1) % NSLOT) * SLOT; };
-        const uint32_t cert = tile::cert4(plane(z - 1), plane(z), plane(z + 1), r, lane, P.two_xi);
-        const uint32_t rowbase = (uint32_t)z * G.nxy + (uint32_t)y * G.nx;
-        const uint32_t i0 = rowbase + (uint32_t)xl;
-        // uncertified bits of this lane's vertices (outside the grid: 0)
-        uint32_t nib = 0;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) nib |= (uint32_t)(xl + e < (int)G.nx && !((cert >> e) & 1u)) << e;
-        // the row's 128 uncertified bits as 4 words: word q (lanes 8q .. 8q+7)
-        // covers columns 32q .. 32q+31
-        uint32_t w = nib << (4u * (lane & 7u));
-        w |= __shfl_xor_sync(kFull, w, 1);
-        w |= __shfl_xor_sync(kFull, w, 2);
-        w |= __shfl_xor_sync(kFull, w, 4);
-        const bool words_ok = ((rowbase + (uint32_t)x0) & 31u) == 0 && x0 + BX <= (int)G.nx;
-        if (words_ok) {
-            if ((lane & 7u) == 0) P.ub[i0 >> 5] = w;
-        } else {
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                if ((nib >> e) & 1u) red_or(&P.ub[(i0 + e) >> 5], 1u << ((i0 + e) & 31u));
-        }
-        // The row's uncertified vertices, 32 at a time in column order (lane
-        // j takes the j-th one): the exact code in f, written to codes_f (the
-        // loop reads codes_f at uncertified vertices only) and, when this
-        // pass detects, the code in the start field, compared with it.
-        const uint32_t w0 = __shfl_sync(kFull, w, 0), w1 = __shfl_sync(kFull, w, 8);
-        const uint32_t w2 = __shfl_sync(kFull, w, 16), w3 = __shfl_sync(kFull, w, 24);
-        const uint32_t c0 = (uint32_t)__popc(w0), c1 = c0 + (uint32_t)__popc(w1);
-        const uint32_t c2 = c1 + (uint32_t)__popc(w2), total = c2 + (uint32_t)__popc(w3);
-        Emitter E{P.dm[1], 0};
-        for (uint32_t j0 = 0; j0 < total; j0 += 32u) {
-            const uint32_t j = j0 + lane;
-            const bool has = j < total;
-            uint32_t col = 0, cf = 0, cg = 0;
-            if (has) {
-                const uint32_t q = j < c0 ? 0u : j < c1 ? 1u : j < c2 ? 2u : 3u;
-                const uint32_t wq = q == 0 ? w0 : q == 1 ? w1 : q == 2 ? w2 : w3;
-                const uint32_t before = q == 0 ? 0u : q == 1 ? c0 : q == 2 ? c1 : c2;
-                col = 32u * q + nth_set(wq, j - before);
-                cf = tile::code1(plane(z - 1), plane(z), plane(z + 1), r, 4 + (int)col);
-                P.codes_f[rowbase + (uint32_t)x0 + col] = (uint8_t)cf;
-                if (DETECT)
-                    cg = tile::code1(plane(z - 1) + PLANE, plane(z) + PLANE, plane(z + 1) + PLANE, r,
-                                     4 + (int)col);
-            }
-            if (DETECT) report(P, E, has, rowbase + (uint32_t)x0 + col, cf, cg);
-        }
-        distorted += E.distorted;
+        tile_row<DETECT>(P, plane(z - 1), plane(z), plane(z + 1), PLANE, r, x0,
+                         (uint32_t)z * G.nxy + (uint32_t)y * G.nx, distorted);
     }
     cp_async_wait<0>();
 }
@@ -469,6 +483,154 @@ __device__ __forceinline__ void first_tiled(const FieldView &P, uint32_t *tile_n
         const int zb = (int)(tzi * tg.bz);
         first_tile<DETECT>(P, (int)(txi * BX), (int)(tyi * BY), zb, min(zb + (int)tg.bz, (int)G.nz), smem, bad,
                            distorted);
+    }
+    if (bad) atomicOr(err, kErrInput);
+}
+
+// ------------------------------------------------ tiled (3D) codes, TMA ring
+// The code pass with its planes staged by TMA (grids whose x extent is a
+// multiple of 4 and at least PW, y extent at least ROWS, and whose arrays
+// are 16-byte aligned).  A slot holds one plane of f and of the second field
+// (map_s: the start field when DETECT, else fhat); a fill completes on the
+// slot's mbarrier, and out-of-grid positions arrive as NaN from the maps'
+// fill mode.  Warps never wait for one another inside a tile: each waits only
+// for the planes it needs, and the last warp to finish with a plane refills
+// its slot with the plane NSLOT further on, so fast warps run up to three
+// planes ahead of slow ones.  Every wait is bounded; a wait that runs out
+// records kErrTimeout, stops the block's tiles and, before leaving, waits
+// (bounded) for the block's copies still in flight.
+
+// The warp's row of plane p0 (row r, x0 .. x0+127): bound check and g =
+// start value, 4 vertices a lane (nx is a multiple of 4: all in or all out).
+template <bool DETECT>
+__device__ __forceinline__ void own_row_tma(const FieldView &P, const float *p0, int r, int x0, uint32_t rowbase,
+                                            bool &bad) {
+    using namespace tile;
+    const uint32_t lane = lane_id();
+    const int xl = x0 + 4 * (int)lane;
+    if (xl >= (int)P.G.nx) return;
+    const uint32_t gi = rowbase + (uint32_t)xl;
+    const float4 f4 = *reinterpret_cast<const float4 *>(p0 + r * PW + 4 + 4 * (int)lane);
+    const float4 s4 = *reinterpret_cast<const float4 *>(p0 + TFIELD + r * PW + 4 + 4 * (int)lane);
+    float4 fh4 = s4, gs4 = s4;
+    if (P.ginit) {
+        if (DETECT) fh4 = *reinterpret_cast<const float4 *>(P.fhat + gi);
+        else gs4 = *reinterpret_cast<const float4 *>(P.ginit + gi);
+    }
+    const float fv[4] = {f4.x, f4.y, f4.z, f4.w}, hv[4] = {fh4.x, fh4.y, fh4.z, fh4.w};
+    const float gv[4] = {gs4.x, gs4.y, gs4.z, gs4.w};
+    uint32_t differs = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const float L = floor_bound(fv[e], P.xi), U = ceil_bound(fv[e], P.xi);
+        bool ok = isfinite(fv[e]) && isfinite(hv[e]) && hv[e] >= L && hv[e] <= U;
+        if (P.ginit) {
+            ok = ok && isfinite(gv[e]) && gv[e] >= L && gv[e] <= U;
+            differs |= (uint32_t)(__float_as_uint(hv[e]) != __float_as_uint(gv[e])) << e;
+        }
+        bad = bad || !ok;
+    }
+    if (differs) red_or(&P.eb[gi >> 5], differs << (gi & 31u));  // gi is a multiple of 4: one word
+    *reinterpret_cast<float4 *>(P.g + gi) = gs4;
+}
+
+template <bool DETECT>
+__device__ __forceinline__ void first_tiled_tma(const FieldView &P, const CUtensorMap *map_f, const CUtensorMap *map_s,
+                                                uint32_t *tile_next, float *smem_raw, uint32_t *err,
+                                                uint32_t &distorted) {
+    using namespace tile;
+    const GridDev &G = P.G;
+    const TileGeom tg = tile_geom(G.nx, G.ny, G.nz, P.tile_z);
+    constexpr uint32_t kWarps = THREADS / 32;
+    __shared__ uint32_t s_tile;
+    __shared__ __align__(8) uint64_t s_full[NSLOT];
+    __shared__ uint32_t s_rel[NSLOT];
+    __shared__ uint32_t s_pending[NSLOT];
+    __shared__ uint32_t s_dead;
+    float *ring = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
+    const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+    if (tid == 0) {
+        for (int q = 0; q < NSLOT; ++q) {
+            tma::mbar_init(tma::smem_u32(&s_full[q]), 1);
+            s_rel[q] = 0;
+            s_pending[q] = 0;
+        }
+        s_dead = 0;
+        tma::fence_mbarrier_init();
+    }
+    __syncthreads();
+    uint32_t ph = 0;  // bit q: parity of the next completion of slot q's barrier
+    bool bad = false;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_tile = atomicAdd(tile_next, 1u);
+        __syncthreads();
+        const uint32_t t = s_tile;
+        if (t >= tg.count || s_dead) break;
+        const uint32_t txi = t % tg.tx, tyi = (t / tg.tx) % tg.ty, tzi = t / (tg.tx * tg.ty);
+        const int x0 = (int)(txi * BX), y0 = (int)(tyi * BY), zb = (int)(tzi * tg.bz);
+        const int ze = min(zb + (int)tg.bz, (int)G.nz);
+        auto slot_of = [&](int p) { return (p - zb + 1) % NSLOT; };
+        auto issue = [&](int p, int q) {
+            const uint32_t bar = tma::smem_u32(&s_full[q]);
+            const uint32_t dst = tma::smem_u32(ring + q * TSLOT);
+            s_pending[q] = 1;
+            tma::mbar_expect_tx(bar, 2u * kTboxBytes);
+            tma::load_3d(dst, map_f, x0 - 4, y0 - 1, p, bar);
+            tma::load_3d(dst + 4u * TFIELD, map_s, x0 - 4, y0 - 1, p, bar);
+        };
+        auto wait_plane = [&](int p) -> bool {
+            const int q = slot_of(p);
+            if (!tma::mbar_wait_bounded(tma::smem_u32(&s_full[q]), (ph >> q) & 1u, &s_dead)) return false;
+            ph ^= 1u << q;
+            if (tid == 0) s_pending[q] = 0;
+            return true;
+        };
+        // planes zb-1 .. ze; the first NSLOT now, each later one when the
+        // plane NSLOT before it is released
+        if (tid == 0) {
+            tma::fence_proxy_async();  // the previous tile's reads of the ring come first
+            for (int q = 0; q < NSLOT && zb - 1 + q <= ze; ++q) issue(zb - 1 + q, q);
+        }
+        bool alive = wait_plane(zb - 1) && wait_plane(zb);
+        const int y = y0 + (int)warp, r = (int)warp + 1;
+        for (int z = zb; alive && z < ze; ++z) {
+            if (!wait_plane(z + 1)) {
+                alive = false;
+                break;
+            }
+            const float *pm = ring + slot_of(z - 1) * TSLOT, *p0 = ring + slot_of(z) * TSLOT;
+            const float *pp = ring + slot_of(z + 1) * TSLOT;
+            if (y < (int)G.ny) {
+                const uint32_t rowbase = (uint32_t)z * G.nxy + (uint32_t)y * G.nx;
+                own_row_tma<DETECT>(P, p0, r, x0, rowbase, bad);
+                tile_row<DETECT>(P, pm, p0, pp, TFIELD, r, x0, rowbase, distorted);
+            }
+            // this warp is done with plane z-1
+            __syncwarp();
+            if (lane == 0) {
+                const int q = slot_of(z - 1);
+                __threadfence_block();
+                if (atomicAdd(&s_rel[q], 1u) == kWarps - 1u) {
+                    s_rel[q] = 0;
+                    __threadfence_block();
+                    if (z - 1 + NSLOT <= ze) {
+                        tma::fence_proxy_async();
+                        issue(z - 1 + NSLOT, q);
+                    }
+                }
+            }
+        }
+        if (!alive) {
+            atomicOr(err, kErrTimeout);
+            s_dead = 1;
+        }
+    }
+    if (s_dead && tid == 0) {
+        // copies still in flight land before the block leaves (bounded)
+        uint32_t none = 0;
+        for (int q = 0; q < NSLOT; ++q)
+            if (s_pending[q]) tma::mbar_wait_bounded(tma::smem_u32(&s_full[q]), (ph >> q) & 1u, &none);
     }
     if (bad) atomicOr(err, kErrInput);
 }

@@ -48,6 +48,17 @@ __device__ __forceinline__ void cp_async_wait() {
 constexpr int SLOT = 2 * PLANE;
 constexpr size_t kRingBytes = (size_t)NSLOT * SLOT * sizeof(float);
 
+// The ring when TMA stages the planes: each slot holds two boxes of ROWS x PW
+// floats (x0-4 .. x0+131, y0-1 .. y0+8: the same indexing as above), f first,
+// then the second field TFIELD floats later; every box starts on a 128-byte
+// boundary.
+constexpr int TBOX = ROWS * PW;                                  // 1360 floats
+constexpr int TFIELD = 1376;                                     // 5504 bytes
+constexpr int TSLOT = 2 * TFIELD;
+constexpr uint32_t kTboxBytes = (uint32_t)TBOX * sizeof(float);  // 5440
+constexpr size_t kTmaRingBytes = (size_t)NSLOT * TSLOT * sizeof(float) + 128;  // + alignment slack
+static_assert(TFIELD >= TBOX && (TFIELD * 4) % 128 == 0, "TMA boxes must start on 128-byte boundaries");
+
 struct TileGeom {
     uint32_t tx, ty, tz;   // tiles along each axis
     uint32_t bz;           // planes per tile
@@ -75,6 +86,18 @@ __device__ __forceinline__ float fmax_nan(float a, float b) {
     asm("max.NaN.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
     return d;
 }
+// Three-input max / min ignoring NaN operands (NaN only when all three are):
+// one instruction, at the rate of the two-input form.
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
 
 // Per-lane two largest and two smallest values of the closed neighbourhoods
 // of 4 consecutive vertices (ties count twice: equal values give a zero
@@ -96,6 +119,16 @@ struct Top2x4 {
         hv[e] = fmaxf(hv[e], w);
         l2[e] = fminf(l2[e], fmax_nan(lv[e], w));
         lv[e] = fminf(lv[e], w);
+    }
+    // Two candidates at once (5 ops a direction instead of 6): the pair's
+    // larger value against the leader, its smaller one straight into the
+    // runner-up.  A NaN in the pair drops out the same way.
+    __device__ __forceinline__ void take2(int e, float a, float b) {
+        const float hi = fmaxf(a, b), lo = fminf(a, b);
+        h2[e] = fmax3(h2[e], fmin_nan(a, b), fmin_nan(hv[e], hi));
+        hv[e] = fmaxf(hv[e], hi);
+        l2[e] = fmin3(l2[e], fmax_nan(a, b), fmax_nan(lv[e], lo));
+        lv[e] = fminf(lv[e], lo);
     }
     // Certified: in f the winner beats the runner-up by more than 2 xi in both
     // directions (differences rounded down), so no g with |g - f| <= xi can
@@ -142,18 +175,12 @@ __device__ __forceinline__ uint32_t cert4(const float *pm, const float *p0, cons
     auto pair_left = [&](const float *row) {  // x-1 and x
         const Seg s = seg_left(row, lane);
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            x.take(e, s.v[e]);
-            x.take(e, s.v[e + 1]);
-        }
+        for (int e = 0; e < 4; ++e) x.take2(e, s.v[e], s.v[e + 1]);
     };
     auto pair_right = [&](const float *row) {  // x and x+1
         const Seg s = seg_right(row, lane);
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            x.take(e, s.v[e]);
-            x.take(e, s.v[e + 1]);
-        }
+        for (int e = 0; e < 4; ++e) x.take2(e, s.v[e], s.v[e + 1]);
     };
     pair_left(pm + (r - 1) * PW);
     pair_left(pm + r * PW);
@@ -164,8 +191,7 @@ __device__ __forceinline__ uint32_t cert4(const float *pm, const float *p0, cons
         if (lane == 31) right = p0[r * PW + 4 + BX];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            x.take(e, s.v[e]);
-            x.take(e, s.v[e + 1]);
+            x.take2(e, s.v[e], s.v[e + 1]);
             x.take(e, e < 3 ? s.v[e + 2] : right);
         }
     }

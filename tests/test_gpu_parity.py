@@ -54,6 +54,11 @@ CASES = {
     "perlin3d_prequant_coarse": lambda: synth.perlin3d_prequant((40, 50, 60), seed=33, eb_rel=1e-3, octaves=4),
     "peaks3d_small": lambda: synth.peaks3d((33, 41, 57), seed=34, eb_rel=1e-4),
     "peaks3d_flat": lambda: synth.peaks3d((16, 16, 16), seed=35, eb_rel=1e-3, npeaks=2),
+    # x extents that are multiples of 4 and at least 136 wide: the code pass
+    # stages these by TMA (ragged last tiles in x and y; the smallest box)
+    "perlin3d_tma_ragged": lambda: synth.perlin3d_prequant((37, 13, 140), seed=36, eb_rel=1e-4),
+    "peaks3d_tma": lambda: synth.peaks3d((21, 26, 264), seed=37, eb_rel=1e-4),
+    "perlin3d_tma_min": lambda: synth.perlin3d_prequant((5, 10, 136), seed=38, eb_rel=1e-3),
 }
 
 
@@ -133,14 +138,39 @@ def test_snap_rule_bit_exact(api):
     _check_against(res, ref, fl, worklist_column=False)
 
 
-def test_g_init_bit_exact(api):
-    fl = synth.perlin3d_prequant((24, 35, 47), seed=41, eb_rel=1e-4)
+@pytest.mark.parametrize("shape", [(24, 35, 47), (20, 17, 144)])
+def test_g_init_bit_exact(api, shape):
+    fl = synth.perlin3d_prequant(shape, seed=41, eb_rel=1e-4)
     lo = np.array([oracle.floor_bound(a, fl.xi) for a in fl.f.reshape(-1)], dtype=np.float32).reshape(fl.shape)
     r = synth.uniform(fl.n, seed=41).reshape(fl.shape)
     g0 = np.maximum(lo, (fl.fhat.astype(np.float64) - 0.5 * r * (fl.fhat - lo)).astype(np.float32))
     ref = oracle.correct(fl.f, fl.fhat, fl.xi, g_init=g0, log_capacity=1000)
     res = api.correct(dev(fl.f), dev(fl.fhat), fl.xi, g_init=dev(g0), log_capacity=1000)
     _check_against(res, ref, fl, worklist_column=False)
+
+
+def _unaligned(a):
+    # a copy whose data starts 4 bytes past a 16-byte boundary
+    buf = torch.empty(a.size + 4, dtype=torch.float32, device="cuda")
+    v = buf[1:1 + a.size].view(a.shape)
+    v.copy_(torch.from_numpy(np.ascontiguousarray(a)))
+    assert v.data_ptr() % 16 == 4
+    return v
+
+
+@pytest.mark.parametrize("shape", [(37, 13, 140), (9, 24, 392)])
+def test_tma_and_cp_async_staging_agree(api, shape):
+    """16-byte aligned arrays take the TMA-staged code pass, unaligned ones
+    the cp.async one: the same result, edit list and per-sweep records."""
+    fl = synth.peaks3d(shape, seed=42, eb_rel=1e-4)
+    a = api.correct(dev(fl.f), dev(fl.fhat), fl.xi, log_capacity=1000)
+    b = api.correct(_unaligned(fl.f), _unaligned(fl.fhat), fl.xi, log_capacity=1000)
+    assert a.status == b.status == api.OK
+    assert np.array_equal(bits(a.out), bits(b.out))
+    assert np.array_equal(a.edit_idx.cpu().numpy(), b.edit_idx.cpu().numpy())
+    assert np.array_equal(a.sweep_log, b.sweep_log)
+    assert {k: v for k, v in a.stats.items() if not k.endswith("_ns")} == \
+        {k: v for k, v in b.stats.items() if not k.endswith("_ns")}
 
 
 # ----------------------------------------------------- edges and errors
