@@ -149,12 +149,14 @@ def algorithmic_bytes(n: int, log: np.ndarray, edited: int, uncertified: int) ->
 
 # ALU operations of one steepest-neighbour code over the 14 neighbours and
 # the vertex itself: per candidate and direction a compare, a value select and
-# a slot select (3 ops).  The certification of sweep 0 keeps the two largest
-# and two smallest values instead: per candidate and direction a
-# NaN-propagating min / max against the leader, a max / min into the
-# runner-up and one into the leader (3 ops).
+# a slot select (3 ops).  The certification of sweep 0 keeps only the two
+# largest and two smallest values, taking the 15 values as 7 pairs of one row
+# segment plus one: the first pair sets them (2 ops: the pair's max and min),
+# each further pair takes 8 (its max and min; per direction a NaN-propagating
+# min / max against the leader, a three-input max / min into the runner-up and
+# one into the leader), the single value 4.
 ALU_OPS_CODE = 14 * 2 * 3
-ALU_OPS_CERT = 14 * 2 * 3
+ALU_OPS_CERT = 2 + 6 * 8 + 4
 
 
 def algorithmic_alu_ops(n: int, log: np.ndarray, uncertified: int) -> int:

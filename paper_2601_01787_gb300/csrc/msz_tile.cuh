@@ -103,36 +103,43 @@ __device__ __forceinline__ float fmin3(float a, float b, float c) {
 // of 4 consecutive vertices (ties count twice: equal values give a zero
 // margin).  The margins hv - h2 and l2 - lv decide whether a vertex can ever
 // be distorted; the winners' slots are not tracked.
+//
+// Candidates come in pairs (a, b) of one row segment.  A NaN (a position
+// outside the grid) must never make a vertex look certified; it may make one
+// look uncertified, which only costs an examination:
+//   - pair of two NaNs: hi = lo = NaN, and the NaN-propagating min against
+//     the leader keeps every value unchanged;
+//   - pair (NaN, w): hi = lo = w, so w counts twice -- a false tie at worst.
 struct Top2x4 {
     float hv[4], h2[4], lv[4], l2[4];
-    __device__ __forceinline__ void init() {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            hv[e] = h2[e] = -__int_as_float(0x7f800000);
-            lv[e] = l2[e] = __int_as_float(0x7f800000);
-        }
+    // the first pair: leader and runner-up in each direction (all NaN when
+    // the pair is, which later pairs then replace)
+    __device__ __forceinline__ void first2(int e, float a, float b) {
+        const float hi = fmaxf(a, b), lo = fminf(a, b);
+        hv[e] = hi;
+        h2[e] = lo;
+        lv[e] = lo;
+        l2[e] = hi;
     }
-    // A NaN candidate (outside the grid) leaves all four values unchanged:
-    // min.NaN / max.NaN turn it into NaN, which fmaxf / fminf then ignore.
+    // 8 ops a pair (both directions): its larger value against the leader,
+    // its smaller one straight into the runner-up, and the mirror image
+    __device__ __forceinline__ void take2(int e, float a, float b) {
+        const float hi = fmaxf(a, b), lo = fminf(a, b);
+        h2[e] = fmax3(h2[e], lo, fmin_nan(hv[e], hi));
+        hv[e] = fmaxf(hv[e], hi);
+        l2[e] = fmin3(l2[e], hi, fmax_nan(lv[e], lo));
+        lv[e] = fminf(lv[e], lo);
+    }
+    // one candidate; a NaN leaves every value unchanged
     __device__ __forceinline__ void take(int e, float w) {
         h2[e] = fmaxf(h2[e], fmin_nan(hv[e], w));
         hv[e] = fmaxf(hv[e], w);
         l2[e] = fminf(l2[e], fmax_nan(lv[e], w));
         lv[e] = fminf(lv[e], w);
     }
-    // Two candidates at once (5 ops a direction instead of 6): the pair's
-    // larger value against the leader, its smaller one straight into the
-    // runner-up.  A NaN in the pair drops out the same way.
-    __device__ __forceinline__ void take2(int e, float a, float b) {
-        const float hi = fmaxf(a, b), lo = fminf(a, b);
-        h2[e] = fmax3(h2[e], fmin_nan(a, b), fmin_nan(hv[e], hi));
-        hv[e] = fmaxf(hv[e], hi);
-        l2[e] = fmin3(l2[e], fmax_nan(a, b), fmax_nan(lv[e], lo));
-        lv[e] = fminf(lv[e], lo);
-    }
     // Certified: in f the winner beats the runner-up by more than 2 xi in both
     // directions (differences rounded down), so no g with |g - f| <= xi can
-    // change either winner.
+    // change either winner.  A NaN runner-up (a single value) never certifies.
     __device__ __forceinline__ bool certified(int e, float two_xi) const {
         return __fsub_rd(hv[e], h2[e]) > two_xi && __fsub_rd(l2[e], lv[e]) > two_xi;
     }
@@ -171,7 +178,6 @@ __device__ __forceinline__ Seg seg_right(const float *row, uint32_t lane) {
 __device__ __forceinline__ uint32_t cert4(const float *pm, const float *p0, const float *pp, int r, uint32_t lane,
                                           float two_xi) {
     Top2x4 x;
-    x.init();
     auto pair_left = [&](const float *row) {  // x-1 and x
         const Seg s = seg_left(row, lane);
 #pragma unroll
@@ -182,7 +188,11 @@ __device__ __forceinline__ uint32_t cert4(const float *pm, const float *p0, cons
 #pragma unroll
         for (int e = 0; e < 4; ++e) x.take2(e, s.v[e], s.v[e + 1]);
     };
-    pair_left(pm + (r - 1) * PW);
+    {
+        const Seg s = seg_left(pm + (r - 1) * PW, lane);  // (y-1, z-1): x-1, x
+#pragma unroll
+        for (int e = 0; e < 4; ++e) x.first2(e, s.v[e], s.v[e + 1]);
+    }
     pair_left(pm + r * PW);
     pair_left(p0 + (r - 1) * PW);
     {
