@@ -20,6 +20,7 @@ namespace msz {
 
 constexpr uint32_t kTileZ = 32;  // default planes per tile of the code pass
 constexpr int kDenseWord = 6;    // set bits from which a bitmap word is walked by the whole warp
+constexpr int kAhead = 4;        // bitmap chunks a walking warp has loaded ahead
 
 struct FieldView {
     GridDev G;
@@ -75,14 +76,29 @@ __device__ __forceinline__ void walk_bits(uint32_t *bm, const uint32_t *filter, 
     const uint32_t lane = lane_id();
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t base = gw * 32u; base < G.words; base += nw * 32u) {
+    const uint32_t chunks = (G.words + 31u) / 32u;
+    // the words of the next kAhead chunks are loaded ahead (a sparse walk is
+    // otherwise one dependent load after another)
+    uint32_t pre[kAhead];
+#pragma unroll
+    for (int u = 0; u < kAhead; ++u) {
+        const uint32_t wi = (gw + (uint32_t)u * nw) * 32u + lane;
+        pre[u] = wi < G.words ? bm[wi] : 0u;
+    }
+    for (uint32_t c = gw; c < chunks; c += nw) {
+        const uint32_t base = c * 32u;
         const uint32_t wi = base + lane;
-        uint32_t bits = 0;
-        if (wi < G.words) {
-            bits = bm[wi];
-            if (CLEAR && bits) bm[wi] = 0u;
+        uint32_t bits = pre[0];
+#pragma unroll
+        for (int u = 0; u + 1 < kAhead; ++u) pre[u] = pre[u + 1];
+        {
+            const uint32_t wn = (c + (uint32_t)kAhead * nw) * 32u + lane;
+            pre[kAhead - 1] = wn < G.words ? bm[wn] : 0u;
+        }
+        if (bits) {
+            if (CLEAR) bm[wi] = 0u;
             seen += (uint32_t)__popc(bits);
-            if (filter && bits) bits &= filter[wi];
+            if (filter) bits &= filter[wi];
         }
         // words with many set bits: the whole warp takes one word at a time,
         // lane l on vertex 32*word + l, so neighbour loads coalesce
@@ -122,14 +138,27 @@ __device__ __forceinline__ void walk_bits_pairs(uint32_t *bm, const uint32_t *fi
     const uint32_t lane = lane_id();
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t base = gw * 32u; base < G.words; base += nw * 32u) {
+    const uint32_t chunks = (G.words + 31u) / 32u;
+    uint32_t pre[kAhead];
+#pragma unroll
+    for (int u = 0; u < kAhead; ++u) {
+        const uint32_t wi = (gw + (uint32_t)u * nw) * 32u + lane;
+        pre[u] = wi < G.words ? bm[wi] : 0u;
+    }
+    for (uint32_t c = gw; c < chunks; c += nw) {
+        const uint32_t base = c * 32u;
         const uint32_t wi = base + lane;
-        uint32_t bits = 0;
-        if (wi < G.words) {
-            bits = bm[wi];
-            if (CLEAR && bits) bm[wi] = 0u;
+        uint32_t bits = pre[0];
+#pragma unroll
+        for (int u = 0; u + 1 < kAhead; ++u) pre[u] = pre[u + 1];
+        {
+            const uint32_t wn = (c + (uint32_t)kAhead * nw) * 32u + lane;
+            pre[kAhead - 1] = wn < G.words ? bm[wn] : 0u;
+        }
+        if (bits) {
+            if (CLEAR) bm[wi] = 0u;
             seen += (uint32_t)__popc(bits);
-            if (filter && bits) bits &= filter[wi];
+            if (filter) bits &= filter[wi];
             if (bits && !word_ok(wi)) bits = 0u;
         }
         const bool dense = __popc(bits) >= kDenseWord;
