@@ -42,8 +42,9 @@ constexpr int kMinBlocks = MSZ_MIN_BLOCKS;  // resident blocks per SM the regist
 constexpr uint32_t kDenseFactor = 6;        // worklist estimate: 6 x distorted vertices
 
 struct Problem {
-    CUtensorMap map_f;  // TMA maps of f and of the start field (the TMA code pass only)
+    CUtensorMap map_f;  // TMA maps of f, of the start field and of g (the TMA passes only)
     CUtensorMap map_s;
+    CUtensorMap map_g;
     FieldView F;
     Ctrl *ctrl;
     SweepRec *log;
@@ -128,6 +129,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
             walk_bits<true>(F.tb, nullptr, G, targets, [&](bool has, uint32_t t) {
                 if (has && apply_target<NDIM>(F, t, dense_next, dnext)) ++changed_here;
             });
+            if (TMA && dense_next) tma::fence_proxy_async_global();  // g is read by TMA next
             warp_add(targets, &P.log[k].targets);
             warp_add(changed_here, &P.log[k].changed);
         }
@@ -153,9 +155,13 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
                 C->dense_sweeps += 1;
             }
             for (uint32_t w = gtid; w < G.words; w += stride) dcur[w] = 0;
-            walk_bits_pairs<false>(F.ub, nullptr, G, seen, [&](bool h1, uint32_t v1, bool h2, uint32_t v2) {
-                detect_vertex2<NDIM>(F, E, h1, v1, h2, v2);
-            });
+            if (TMA) {
+                detect_tiled_tma(F, &P.map_g, &P.log[k1].tile_next, smem, &C->error, E.dnext, E.distorted);
+            } else {
+                walk_bits_pairs<false>(F.ub, nullptr, G, seen, [&](bool h1, uint32_t v1, bool h2, uint32_t v2) {
+                    detect_vertex2<NDIM>(F, E, h1, v1, h2, v2);
+                });
+            }
         } else {
             // the worklist, restricted to uncertified vertices
             walk_bits_pairs<true>(dcur, F.ub, G, seen, [&](bool h1, uint32_t v1, bool h2, uint32_t v2) {
@@ -356,13 +362,22 @@ static msz_status launch_correct(Problem &P, const DeviceInfo &dev, cudaStream_t
     return MSZ_OK;
 }
 
+// Default whole-grid detection rule (P.dense_min == 0).  With TMA staging a
+// whole-grid pass costs about one code pass without the certification, and
+// beats the worklist while the worklist is large: measured at 512^3, dense
+// while 6 x distorted >= N/4 takes the peak field from 26.4 to 22.9 ms and
+// leaves the Perlin field on worklists.  The gather-based whole-grid walk of
+// the cp.async path never beat the worklist.
 template <int NDIM>
 static msz_status run_correct(Problem &P, const DeviceInfo &dev, cudaStream_t stream) {
     if constexpr (NDIM == 3) {
         if (tma_eligible(P.F) && plane_map(P.F.f, P.F.G, P.map_f) &&
-            plane_map(P.F.ginit ? P.F.ginit : P.F.fhat, P.F.G, P.map_s))
+            plane_map(P.F.ginit ? P.F.ginit : P.F.fhat, P.F.G, P.map_s) && plane_map(P.F.g, P.F.G, P.map_g)) {
+            if (P.dense_min == 0) P.dense_min = (long long)(P.F.G.n / 4);
             return launch_correct<3, true>(P, dev, stream);
+        }
     }
+    if (P.dense_min == 0) P.dense_min = -1;
     return launch_correct<NDIM, false>(P, dev, stream);
 }
 
@@ -441,9 +456,8 @@ extern "C" msz_status msz_correct(const float *d_f, const float *d_fhat, float x
     P.edit_delta = d_edit_delta;
     P.edit_cap = (unsigned long long)edit_capacity;
     P.max_sweeps = o.max_sweeps <= 0 ? (uint32_t)MSZ_MAX_SWEEPS_LIMIT : (uint32_t)o.max_sweeps;
-    // default: the worklist after sweep 0 (measured faster than whole-grid
-    // scans on every workload once detection gathers two vertices per lane)
-    P.dense_min = o.dense_min_items == 0 ? -1LL : (long long)o.dense_min_items;
+    // default (0): decided with the staging in run_correct
+    P.dense_min = o.dense_min_items == 0 ? 0LL : (long long)o.dense_min_items;
     P.test_fault = (uint32_t)o.test_fault;
 
     if (cudaMemsetAsync(ws, 0, L.zero_bytes, s) != cudaSuccess) return MSZ_ERR_CUDA;

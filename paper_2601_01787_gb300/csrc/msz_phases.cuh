@@ -563,10 +563,13 @@ __device__ __forceinline__ void own_row_tma(const FieldView &P, const float *p0,
     *reinterpret_cast<float4 *>(P.g + gi) = gs4;
 }
 
-template <bool DETECT>
-__device__ __forceinline__ void first_tiled_tma(const FieldView &P, const CUtensorMap *map_f, const CUtensorMap *map_s,
-                                                uint32_t *tile_next, float *smem_raw, uint32_t *err,
-                                                uint32_t &distorted) {
+// The TMA plane ring over the tiles of field P (block-collective): NBOX
+// boxes a plane (maps[0..NBOX-1], each TFIELD floats after the previous one
+// in a slot); row(pm, p0, pp, r, x0, rowbase) runs for every warp row inside
+// the grid with the staged planes z-1, z, z+1.
+template <int NBOX, class ROW>
+__device__ __forceinline__ void tma_tiles(const FieldView &P, const CUtensorMap *map0, const CUtensorMap *map1,
+                                          uint32_t *tile_next, float *smem_raw, uint32_t *err, ROW &&row) {
     using namespace tile;
     const GridDev &G = P.G;
     const TileGeom tg = tile_geom(G.nx, G.ny, G.nz, P.tile_z);
@@ -578,6 +581,7 @@ __device__ __forceinline__ void first_tiled_tma(const FieldView &P, const CUtens
     __shared__ uint32_t s_dead;
     float *ring = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+    __syncthreads();  // the ring's previous users are done with its barriers
     if (tid == 0) {
         for (int q = 0; q < NSLOT; ++q) {
             tma::mbar_init(tma::smem_u32(&s_full[q]), 1);
@@ -587,9 +591,12 @@ __device__ __forceinline__ void first_tiled_tma(const FieldView &P, const CUtens
         s_dead = 0;
         tma::fence_mbarrier_init();
     }
+    // g may have been written by generic stores earlier in this kernel (made
+    // visible by a grid barrier); every thread that issues copies orders them
+    // before its TMA reads
+    tma::fence_proxy_async_global();
     __syncthreads();
     uint32_t ph = 0;  // bit q: parity of the next completion of slot q's barrier
-    bool bad = false;
     for (;;) {
         __syncthreads();
         if (tid == 0) s_tile = atomicAdd(tile_next, 1u);
@@ -604,9 +611,9 @@ __device__ __forceinline__ void first_tiled_tma(const FieldView &P, const CUtens
             const uint32_t bar = tma::smem_u32(&s_full[q]);
             const uint32_t dst = tma::smem_u32(ring + q * TSLOT);
             s_pending[q] = 1;
-            tma::mbar_expect_tx(bar, 2u * kTboxBytes);
-            tma::load_3d(dst, map_f, x0 - 4, y0 - 1, p, bar);
-            tma::load_3d(dst + 4u * TFIELD, map_s, x0 - 4, y0 - 1, p, bar);
+            tma::mbar_expect_tx(bar, (uint32_t)NBOX * kTboxBytes);
+            tma::load_3d(dst, map0, x0 - 4, y0 - 1, p, bar);
+            if (NBOX > 1) tma::load_3d(dst + 4u * TFIELD, map1, x0 - 4, y0 - 1, p, bar);
         };
         auto wait_plane = [&](int p) -> bool {
             const int q = slot_of(p);
@@ -630,11 +637,7 @@ __device__ __forceinline__ void first_tiled_tma(const FieldView &P, const CUtens
             }
             const float *pm = ring + slot_of(z - 1) * TSLOT, *p0 = ring + slot_of(z) * TSLOT;
             const float *pp = ring + slot_of(z + 1) * TSLOT;
-            if (y < (int)G.ny) {
-                const uint32_t rowbase = (uint32_t)z * G.nxy + (uint32_t)y * G.nx;
-                own_row_tma<DETECT>(P, p0, r, x0, rowbase, bad);
-                tile_row<DETECT>(P, pm, p0, pp, TFIELD, r, x0, rowbase, distorted);
-            }
+            if (y < (int)G.ny) row(pm, p0, pp, r, x0, (uint32_t)z * G.nxy + (uint32_t)y * G.nx);
             // this warp is done with plane z-1
             __syncwarp();
             if (lane == 0) {
@@ -661,7 +664,67 @@ __device__ __forceinline__ void first_tiled_tma(const FieldView &P, const CUtens
         for (int q = 0; q < NSLOT; ++q)
             if (s_pending[q]) tma::mbar_wait_bounded(tma::smem_u32(&s_full[q]), (ph >> q) & 1u, &none);
     }
+}
+
+// The code pass (sweep 0) on the TMA ring: f and the second field (the start
+// field when DETECT, else fhat) a plane.
+template <bool DETECT>
+__device__ __forceinline__ void first_tiled_tma(const FieldView &P, const CUtensorMap *map_f, const CUtensorMap *map_s,
+                                                uint32_t *tile_next, float *smem_raw, uint32_t *err,
+                                                uint32_t &distorted) {
+    bool bad = false;
+    tma_tiles<2>(P, map_f, map_s, tile_next, smem_raw, err,
+                 [&](const float *pm, const float *p0, const float *pp, int r, int x0, uint32_t rowbase) {
+                     own_row_tma<DETECT>(P, p0, r, x0, rowbase, bad);
+                     tile_row<DETECT>(P, pm, p0, pp, tile::TFIELD, r, x0, rowbase, distorted);
+                 });
     if (bad) atomicOr(err, kErrInput);
+}
+
+// Whole-grid detection of a later sweep on the TMA ring (g a plane): every
+// uncertified vertex gets its code in g from the staged planes and its code
+// of f from codes_f; distorted ones mark their targets and themselves in
+// dnext (the next sweep's worklist).  nx is a multiple of 4, so a lane's 4
+// vertices have their 4 uncertified bits in one bitmap word.
+__device__ __forceinline__ void detect_tiled_tma(const FieldView &P, const CUtensorMap *map_g, uint32_t *tile_next,
+                                                 float *smem_raw, uint32_t *err, uint32_t *dnext,
+                                                 uint32_t &distorted) {
+    using namespace tile;
+    tma_tiles<1>(P, map_g, nullptr, tile_next, smem_raw, err,
+                 [&](const float *pm, const float *p0, const float *pp, int r, int x0, uint32_t rowbase) {
+                     const uint32_t lane = lane_id();
+                     const int xl = x0 + 4 * (int)lane;
+                     uint32_t nib = 0;
+                     if (xl < (int)P.G.nx) {
+                         const uint32_t i0 = rowbase + (uint32_t)xl;
+                         nib = (__ldg(&P.ub[i0 >> 5]) >> (i0 & 31u)) & 15u;
+                     }
+                     uint32_t w = nib << (4u * (lane & 7u));
+                     w |= __shfl_xor_sync(kFull, w, 1);
+                     w |= __shfl_xor_sync(kFull, w, 2);
+                     w |= __shfl_xor_sync(kFull, w, 4);
+                     const uint32_t w0 = __shfl_sync(kFull, w, 0), w1 = __shfl_sync(kFull, w, 8);
+                     const uint32_t w2 = __shfl_sync(kFull, w, 16), w3 = __shfl_sync(kFull, w, 24);
+                     const uint32_t c0 = (uint32_t)__popc(w0), c1 = c0 + (uint32_t)__popc(w1);
+                     const uint32_t c2 = c1 + (uint32_t)__popc(w2), total = c2 + (uint32_t)__popc(w3);
+                     Emitter E{dnext, 0};
+                     for (uint32_t j0 = 0; j0 < total; j0 += 32u) {
+                         const uint32_t j = j0 + lane;
+                         const bool has = j < total;
+                         uint32_t v = 0, cf = 0, cg = 0;
+                         if (has) {
+                             const uint32_t q = j < c0 ? 0u : j < c1 ? 1u : j < c2 ? 2u : 3u;
+                             const uint32_t wq = q == 0 ? w0 : q == 1 ? w1 : q == 2 ? w2 : w3;
+                             const uint32_t before = q == 0 ? 0u : q == 1 ? c0 : q == 2 ? c1 : c2;
+                             const uint32_t col = 32u * q + nth_set(wq, j - before);
+                             v = rowbase + (uint32_t)x0 + col;
+                             cf = __ldg(&P.codes_f[v]);
+                             cg = code1(pm, p0, pp, r, 4 + (int)col);
+                         }
+                         report(P, E, has, v, cf, cg);
+                     }
+                     distorted += E.distorted;
+                 });
 }
 
 // Sets the bits of up to 3 consecutive vertices j0, j0+1, j0+2 (bit k of m

@@ -50,6 +50,9 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t a, uint32_t parity, v
 // Orders this thread's earlier generic-proxy shared-memory accesses before
 // its later async-proxy (TMA) ones.
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// The same between generic-proxy writes to global memory (made visible to
+// this thread, e.g. by a grid barrier) and its later TMA reads of them.
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 __device__ __forceinline__ void fence_mbarrier_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }

@@ -158,13 +158,16 @@ def _unaligned(a):
     return v
 
 
+@pytest.mark.parametrize("dense", [-1, 1])
 @pytest.mark.parametrize("shape", [(37, 13, 140), (9, 24, 392)])
-def test_tma_and_cp_async_staging_agree(api, shape):
-    """16-byte aligned arrays take the TMA-staged code pass, unaligned ones
-    the cp.async one: the same result, edit list and per-sweep records."""
+def test_tma_and_cp_async_staging_agree(api, shape, dense):
+    """16-byte aligned arrays take the TMA-staged passes, unaligned ones the
+    cp.async code pass and gathered detection: under one detection schedule
+    (worklists only, or whole-grid scans only) the same result, edit list and
+    per-sweep records."""
     fl = synth.peaks3d(shape, seed=42, eb_rel=1e-4)
-    a = api.correct(dev(fl.f), dev(fl.fhat), fl.xi, log_capacity=1000)
-    b = api.correct(_unaligned(fl.f), _unaligned(fl.fhat), fl.xi, log_capacity=1000)
+    a = api.correct(dev(fl.f), dev(fl.fhat), fl.xi, log_capacity=1000, dense_min_items=dense)
+    b = api.correct(_unaligned(fl.f), _unaligned(fl.fhat), fl.xi, log_capacity=1000, dense_min_items=dense)
     assert a.status == b.status == api.OK
     assert np.array_equal(bits(a.out), bits(b.out))
     assert np.array_equal(a.edit_idx.cpu().numpy(), b.edit_idx.cpu().numpy())
