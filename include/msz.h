@@ -176,6 +176,34 @@ msz_status msz_correct_host(const float *h_f, const float *h_fhat, float xi, msz
                             int64_t *h_edit_count, const msz_options *opt, msz_stats *h_stats,
                             void *d_workspace, size_t workspace_bytes, msz_stream_t stream);
 
+/* ---- Pipelined host-buffer correction (no counterpart in the paper: a
+ * serving path).  A sequence of fields of one grid -- time steps, say -- is
+ * corrected with the copies of consecutive fields overlapped: field k+1's
+ * inputs go up while field k is corrected and field k-1's result comes
+ * down.  Two slots of device buffers live in the caller's workspace
+ * (msz_pipeline_workspace_size bytes, 256-byte aligned); the pipeline owns
+ * three CUDA streams, six events and a few hundred bytes of pinned host
+ * memory.  Each field's results are those of msz_correct_host. */
+typedef struct msz_pipeline msz_pipeline;
+size_t msz_pipeline_workspace_size(msz_grid grid, int64_t edit_capacity);
+msz_status msz_pipeline_create(msz_grid grid, int64_t edit_capacity, void *d_workspace, size_t workspace_bytes,
+                               msz_pipeline **out);
+/* Enqueues one field (host buffers of N floats) and returns without waiting.
+ * h_out and, when the capacity is > 0, the edit arrays must stay valid until
+ * the field is collected.  At most two fields may be submitted and not yet
+ * collected (MSZ_ERR_INVALID_ARG otherwise).  opt: as msz_correct, without
+ * d_g_init, the sweep log or the test hook.  Pinned host buffers let the
+ * copies overlap; pageable ones work but serialize. */
+msz_status msz_pipeline_submit(msz_pipeline *pl, const float *h_f, const float *h_fhat, float xi, float *h_out,
+                               uint32_t *h_edit_idx, float *h_edit_delta, const msz_options *opt);
+/* Waits for the oldest submitted field and returns its status (as
+ * msz_correct_host), edit count and stats; its h_out and edit list are
+ * filled on return.  MSZ_ERR_INVALID_ARG when nothing is pending. */
+msz_status msz_pipeline_collect(msz_pipeline *pl, int64_t *h_edit_count, msz_stats *h_stats);
+/* Waits for the pipeline's work, then frees its streams, events and pinned
+ * memory (not the workspace). */
+void msz_pipeline_destroy(msz_pipeline *pl);
+
 /* Sec. III-A ascending/descending segmentations, for verification:
  * d_max_label[i] = index of the maximum reached by following n_max (the low
  * nibble of d_codes) from i; d_min_label[i] likewise through n_min.  Computed

@@ -127,6 +127,16 @@ def load(build_if_missing: bool = True):
         lib.msz_edits_encode.restype = st
         lib.msz_edits_decode.argtypes = [P, SZ, P, I64, ctypes.POINTER(I64), P, SZ, P]
         lib.msz_edits_decode.restype = st
+        lib.msz_pipeline_workspace_size.argtypes = [Grid, I64]
+        lib.msz_pipeline_workspace_size.restype = SZ
+        lib.msz_pipeline_create.argtypes = [Grid, I64, P, SZ, ctypes.POINTER(P)]
+        lib.msz_pipeline_create.restype = st
+        lib.msz_pipeline_submit.argtypes = [P, P, P, ctypes.c_float, P, P, P, ctypes.POINTER(Options)]
+        lib.msz_pipeline_submit.restype = st
+        lib.msz_pipeline_collect.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(Stats)]
+        lib.msz_pipeline_collect.restype = st
+        lib.msz_pipeline_destroy.argtypes = [P]
+        lib.msz_pipeline_destroy.restype = None
         lib.msz_status_str.argtypes = [st]
         lib.msz_status_str.restype = ctypes.c_char_p
         _lib = lib
@@ -327,6 +337,70 @@ def correct_host(f: np.ndarray | torch.Tensor, fhat, xi: float, *, out=None, edi
                               ctypes.byref(opt), ctypes.byref(stats), _dptr(ws), ws.numel(), _stream(stream))
     m = min(int(count.value), cap)
     return CorrectResult(int(st), out, edit_idx[:m], edit_delta[:m], int(count.value), stats.as_dict())
+
+
+def _host_ptr(a):
+    if isinstance(a, torch.Tensor):
+        assert not a.is_cuda and a.is_contiguous()
+        return a.data_ptr()
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data
+
+
+class Pipeline:
+    """msz_pipeline_*: a sequence of fields of one shape corrected from host
+    buffers with the copies of consecutive fields overlapped.  submit()
+    returns at once (at most two fields in flight); collect() returns the
+    oldest field's CorrectResult once its g and edit list are in its host
+    buffers.  Pinned host buffers (torch pin_memory) let the copies overlap."""
+
+    def __init__(self, shape, edit_capacity: int | None = None, device=None):
+        lib = load()
+        self.shape = tuple(int(v) for v in shape)
+        self.n = int(np.prod(self.shape))
+        self.cap = self.n if edit_capacity is None else int(edit_capacity)
+        g = grid_of(self.shape)
+        need = int(lib.msz_pipeline_workspace_size(g, self.cap))
+        dev = torch.device("cuda", torch.cuda.current_device() if device is None else torch.device(device).index)
+        self.ws = torch.empty(need, dtype=torch.uint8, device=dev)  # owned: the pipeline's two slots
+        h = ctypes.c_void_p()
+        st = lib.msz_pipeline_create(g, self.cap, _dptr(self.ws), self.ws.numel(), ctypes.byref(h))
+        if st != OK:
+            raise MszError(st, "msz_pipeline_create")
+        self._h = h
+        self._fifo = []
+
+    def submit(self, f, fhat, xi: float, out, edit_idx=None, edit_delta=None, *, rule="halve",
+               max_sweeps: int = 0, dense_min_items: int = 0):
+        if edit_idx is None:
+            edit_idx = np.empty(max(self.cap, 1), dtype=np.uint32)
+        if edit_delta is None:
+            edit_delta = np.empty(max(self.cap, 1), dtype=np.float32)
+        opt, _ = _options(rule, max_sweeps, dense_min_items, None, 0)
+        st = load().msz_pipeline_submit(self._h, _host_ptr(f), _host_ptr(fhat), ctypes.c_float(np.float32(xi)),
+                                        _host_ptr(out), _host_ptr(edit_idx), _host_ptr(edit_delta),
+                                        ctypes.byref(opt))
+        if st != OK:
+            raise MszError(st, "msz_pipeline_submit")
+        self._fifo.append((out, edit_idx, edit_delta))
+
+    def collect(self) -> CorrectResult:
+        stats = Stats()
+        count = ctypes.c_int64()
+        st = load().msz_pipeline_collect(self._h, ctypes.byref(count), ctypes.byref(stats))
+        if not self._fifo:
+            raise MszError(st, "msz_pipeline_collect")
+        out, idx, dl = self._fifo.pop(0)
+        m = min(int(count.value), self.cap)
+        return CorrectResult(int(st), out, idx[:m], dl[:m], int(count.value), stats.as_dict())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().msz_pipeline_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
 
 
 def segment(codes: torch.Tensor, ws: torch.Tensor | None = None, stream=None):

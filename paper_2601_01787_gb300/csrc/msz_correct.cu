@@ -406,17 +406,22 @@ extern "C" msz_status msz_directions(const float *d_v, msz_grid grid, uint8_t *d
     return cuda_status(cudaGetLastError());
 }
 
-extern "C" msz_status msz_correct(const float *d_f, const float *d_fhat, float xi, msz_grid grid, float *d_out,
+namespace msz {
+
+// msz_correct in three steps, shared with the pipeline below: the argument
+// checks and the kernel's problem, the launch, and the results from the
+// control block read back after it.
+static msz_status prepare_correct(const float *d_f, const float *d_fhat, float xi, msz_grid grid, float *d_out,
                                   uint32_t *d_edit_idx, float *d_edit_delta, int64_t edit_capacity,
-                                  int64_t *h_edit_count, const msz_options *opt, msz_stats *h_stats,
-                                  void *d_workspace, size_t workspace_bytes, msz_stream_t stream) {
-    if (!d_f || !d_fhat || !d_out || !h_edit_count) return MSZ_ERR_INVALID_ARG;
+                                  const msz_options *opt, void *d_workspace, size_t workspace_bytes, Problem &P,
+                                  msz_options &o) {
+    if (!d_f || !d_fhat || !d_out) return MSZ_ERR_INVALID_ARG;
     if (edit_capacity < 0 || (edit_capacity > 0 && (!d_edit_idx || !d_edit_delta))) return MSZ_ERR_INVALID_ARG;
     if (!(xi >= 0.0f) || isinf(xi)) return MSZ_ERR_INVALID_ARG;
     GridDev G;
     msz_status st = make_grid(grid, G);
     if (st != MSZ_OK) return st;
-    msz_options o{};
+    o = msz_options{};
     if (opt) o = *opt;
     if (o.rule != MSZ_RULE_HALVE && o.rule != MSZ_RULE_SNAP) return MSZ_ERR_INVALID_ARG;
     if (o.test_fault != 0 && o.test_fault != 1) return MSZ_ERR_INVALID_ARG;
@@ -427,12 +432,9 @@ extern "C" msz_status msz_correct(const float *d_f, const float *d_fhat, float x
     const Layout L = layout_for(G.n);
     if (!d_workspace || workspace_bytes < L.total) return MSZ_ERR_WORKSPACE;
     if ((uintptr_t)d_workspace % kAlign) return MSZ_ERR_INVALID_ARG;
-    DeviceInfo dev;
-    if ((st = current_device(dev)) != MSZ_OK) return st;
-    cudaStream_t s = (cudaStream_t)stream;
 
     char *ws = (char *)d_workspace;
-    Problem P{};
+    P = Problem{};
     FieldView &F = P.F;
     F.G = G;
     F.f = d_f;
@@ -459,16 +461,62 @@ extern "C" msz_status msz_correct(const float *d_f, const float *d_fhat, float x
     // default (0): decided with the staging in run_correct
     P.dense_min = o.dense_min_items == 0 ? 0LL : (long long)o.dense_min_items;
     P.test_fault = (uint32_t)o.test_fault;
+    return MSZ_OK;
+}
 
-    if (cudaMemsetAsync(ws, 0, L.zero_bytes, s) != cudaSuccess) return MSZ_ERR_CUDA;
-    st = G.ndim == 3 ? run_correct<3>(P, dev, s) : run_correct<2>(P, dev, s);
-    if (st != MSZ_OK) return st;
-    Ctrl hc;
-    if (cudaMemcpyAsync(&hc, P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MSZ_ERR_CUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return MSZ_ERR_CUDA;
+static msz_status enqueue_correct(Problem &P, const DeviceInfo &dev, cudaStream_t s) {
+    if (cudaMemsetAsync(P.ctrl, 0, layout_for(P.F.G.n).zero_bytes, s) != cudaSuccess) return MSZ_ERR_CUDA;
+    return P.F.G.ndim == 3 ? run_correct<3>(P, dev, s) : run_correct<2>(P, dev, s);
+}
+
+// Status, edit count and stats from the control block and the record of
+// sweep 0 read back after the kernel.
+static msz_status finish_correct(const Ctrl &hc, const SweepRec &r0, int64_t edit_capacity, int64_t *h_edit_count,
+                                 msz_stats *h_stats) {
     if (hc.error & kErrInput) return MSZ_ERR_INPUT_BOUND;
     if (hc.error & kErrTimeout) return MSZ_ERR_TIMEOUT;
     *h_edit_count = (int64_t)hc.edit_count;
+    if (h_stats) {
+        *h_stats = msz_stats{};
+        h_stats->sweeps = hc.sweeps;
+        h_stats->edits = (int64_t)hc.edits;
+        h_stats->edited = (int64_t)hc.edit_count;
+        h_stats->first_distorted = r0.distorted;
+        h_stats->left = hc.left;
+        h_stats->examined = (int64_t)hc.examined;
+        h_stats->dense_sweeps = hc.dense_sweeps;
+        h_stats->kernel_ns = hc.t_end > hc.t_start ? (int64_t)(hc.t_end - hc.t_start) : 0;
+        h_stats->codes_ns = hc.t_codes > hc.t_start ? (int64_t)(hc.t_codes - hc.t_start) : 0;
+        h_stats->uncertified = hc.uncertified;
+    }
+    const msz_status loop = (msz_status)hc.status;
+    if (loop == MSZ_OK && (int64_t)hc.edit_count > edit_capacity) return MSZ_ERR_CAPACITY;
+    return loop;
+}
+
+}  // namespace msz
+
+extern "C" msz_status msz_correct(const float *d_f, const float *d_fhat, float xi, msz_grid grid, float *d_out,
+                                  uint32_t *d_edit_idx, float *d_edit_delta, int64_t edit_capacity,
+                                  int64_t *h_edit_count, const msz_options *opt, msz_stats *h_stats,
+                                  void *d_workspace, size_t workspace_bytes, msz_stream_t stream) {
+    if (!h_edit_count) return MSZ_ERR_INVALID_ARG;
+    Problem P;
+    msz_options o;
+    msz_status st = prepare_correct(d_f, d_fhat, xi, grid, d_out, d_edit_idx, d_edit_delta, edit_capacity, opt,
+                                    d_workspace, workspace_bytes, P, o);
+    if (st != MSZ_OK) return st;
+    DeviceInfo dev;
+    if ((st = current_device(dev)) != MSZ_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = enqueue_correct(P, dev, s)) != MSZ_OK) return st;
+    Ctrl hc;
+    SweepRec r0;
+    if (cudaMemcpyAsync(&hc, P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MSZ_ERR_CUDA;
+    if (cudaMemcpyAsync(&r0, P.log, sizeof r0, cudaMemcpyDeviceToHost, s) != cudaSuccess) return MSZ_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return MSZ_ERR_CUDA;
+    st = finish_correct(hc, r0, edit_capacity, h_edit_count, h_stats);
+    if (st == MSZ_ERR_INPUT_BOUND || st == MSZ_ERR_TIMEOUT) return st;
     if (o.log_capacity > 0) {
         const int64_t nrec = (int64_t)hc.sweeps + 1 < o.log_capacity ? (int64_t)hc.sweeps + 1 : o.log_capacity;
         SweepRec tmp[256];
@@ -489,23 +537,7 @@ extern "C" msz_status msz_correct(const float *d_f, const float *d_fhat, float x
             }
         }
     }
-    if (h_stats) {
-        SweepRec r0;
-        if (cudaMemcpy(&r0, P.log, sizeof r0, cudaMemcpyDeviceToHost) != cudaSuccess) return MSZ_ERR_CUDA;
-        h_stats->sweeps = hc.sweeps;
-        h_stats->edits = (int64_t)hc.edits;
-        h_stats->edited = (int64_t)hc.edit_count;
-        h_stats->first_distorted = r0.distorted;
-        h_stats->left = hc.left;
-        h_stats->examined = (int64_t)hc.examined;
-        h_stats->dense_sweeps = hc.dense_sweeps;
-        h_stats->kernel_ns = hc.t_end > hc.t_start ? (int64_t)(hc.t_end - hc.t_start) : 0;
-        h_stats->codes_ns = hc.t_codes > hc.t_start ? (int64_t)(hc.t_codes - hc.t_start) : 0;
-        h_stats->uncertified = hc.uncertified;
-    }
-    const msz_status loop = (msz_status)hc.status;
-    if (loop == MSZ_OK && (int64_t)hc.edit_count > edit_capacity) return MSZ_ERR_CAPACITY;
-    return loop;
+    return st;
 }
 
 extern "C" size_t msz_host_workspace_size(msz_grid grid, int64_t edit_capacity) {
@@ -555,6 +587,177 @@ extern "C" msz_status msz_correct_host(const float *h_f, const float *h_fhat, fl
     }
     if (cudaStreamSynchronize(s) != cudaSuccess) return MSZ_ERR_CUDA;
     return st;
+}
+
+// ------------------------------------------------------------ pipeline
+// Two slots of device buffers (f, fhat, g, edit list, correction workspace)
+// and three streams: inputs up, correction, result down.  Field k+1's
+// inputs go up while field k is corrected and field k-1's result comes down;
+// events order each slot's reuse.
+struct msz_pipeline {
+    msz_grid grid;
+    GridDev G;
+    int64_t cap;
+    char *ws;
+    size_t slot_bytes, fld, capb, base;
+    cudaStream_t s_in, s_comp, s_out;
+    struct Slot {
+        cudaEvent_t in_done, comp_done, out_done;
+        bool used;
+        float *h_out;
+        uint32_t *h_idx;
+        float *h_del;
+        Problem P;
+        msz_status prep;
+    } slot[2];
+    msz::Ctrl *h_ctrl;    // pinned: the control block and sweep-0 record of each slot
+    msz::SweepRec *h_rec;
+    int head, tail, pending;
+};
+
+namespace msz {
+static size_t pipeline_slot_bytes(const GridDev &G, int64_t cap) {
+    return layout_for(G.n).total + 3 * align_up((size_t)G.n * 4) + 2 * align_up((size_t)cap * 4);
+}
+}  // namespace msz
+
+extern "C" size_t msz_pipeline_workspace_size(msz_grid grid, int64_t edit_capacity) {
+    GridDev G;
+    if (make_grid(grid, G) != MSZ_OK || edit_capacity < 0) return 0;
+    return 2 * pipeline_slot_bytes(G, edit_capacity);
+}
+
+extern "C" msz_status msz_pipeline_create(msz_grid grid, int64_t edit_capacity, void *d_workspace,
+                                          size_t workspace_bytes, msz_pipeline **out) {
+    if (!out || edit_capacity < 0) return MSZ_ERR_INVALID_ARG;
+    *out = nullptr;
+    GridDev G;
+    msz_status st = make_grid(grid, G);
+    if (st != MSZ_OK) return st;
+    const size_t need = 2 * pipeline_slot_bytes(G, edit_capacity);
+    if (!d_workspace || workspace_bytes < need) return MSZ_ERR_WORKSPACE;
+    if ((uintptr_t)d_workspace % kAlign) return MSZ_ERR_INVALID_ARG;
+    DeviceInfo dev;
+    if ((st = current_device(dev)) != MSZ_OK) return st;
+    msz_pipeline *pl = new msz_pipeline{};
+    pl->grid = grid;
+    pl->G = G;
+    pl->cap = edit_capacity;
+    pl->ws = (char *)d_workspace;
+    pl->slot_bytes = pipeline_slot_bytes(G, edit_capacity);
+    pl->base = layout_for(G.n).total;
+    pl->fld = align_up((size_t)G.n * 4);
+    pl->capb = align_up((size_t)edit_capacity * 4);
+    bool ok = cudaStreamCreateWithFlags(&pl->s_in, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&pl->s_comp, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&pl->s_out, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaHostAlloc((void **)&pl->h_ctrl, 2 * sizeof(Ctrl), cudaHostAllocDefault) == cudaSuccess &&
+              cudaHostAlloc((void **)&pl->h_rec, 2 * sizeof(SweepRec), cudaHostAllocDefault) == cudaSuccess;
+    for (int k = 0; ok && k < 2; ++k)
+        ok = cudaEventCreateWithFlags(&pl->slot[k].in_done, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&pl->slot[k].comp_done, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&pl->slot[k].out_done, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        msz_pipeline_destroy(pl);
+        return MSZ_ERR_CUDA;
+    }
+    *out = pl;
+    return MSZ_OK;
+}
+
+extern "C" msz_status msz_pipeline_submit(msz_pipeline *pl, const float *h_f, const float *h_fhat, float xi,
+                                          float *h_out, uint32_t *h_edit_idx, float *h_edit_delta,
+                                          const msz_options *opt) {
+    if (!pl || !h_f || !h_fhat || !h_out) return MSZ_ERR_INVALID_ARG;
+    if (pl->cap > 0 && (!h_edit_idx || !h_edit_delta)) return MSZ_ERR_INVALID_ARG;
+    if (pl->pending == 2) return MSZ_ERR_INVALID_ARG;  // collect the oldest field first
+    if (opt && (opt->d_g_init || opt->h_sweep_log || opt->log_capacity || opt->test_fault)) return MSZ_ERR_INVALID_ARG;
+    const int k = pl->head;
+    msz_pipeline::Slot &sl = pl->slot[k];
+    char *w = pl->ws + (size_t)k * pl->slot_bytes;
+    float *d_f = (float *)(w + pl->base), *d_fhat = (float *)(w + pl->base + pl->fld);
+    float *d_out = (float *)(w + pl->base + 2 * pl->fld);
+    uint32_t *d_idx = (uint32_t *)(w + pl->base + 3 * pl->fld);
+    float *d_del = (float *)(w + pl->base + 3 * pl->fld + pl->capb);
+    msz_options o;
+    msz_status st = prepare_correct(d_f, d_fhat, xi, pl->grid, d_out, pl->cap ? d_idx : nullptr,
+                                    pl->cap ? d_del : nullptr, pl->cap, opt, w, pl->base, sl.P, o);
+    if (st != MSZ_OK) return st;
+    DeviceInfo dev;
+    if ((st = current_device(dev)) != MSZ_OK) return st;
+    const size_t bytes = (size_t)pl->G.n * 4;
+    // inputs up, once the slot's previous correction has read its inputs
+    if (sl.used && cudaStreamWaitEvent(pl->s_in, sl.comp_done, 0) != cudaSuccess) return MSZ_ERR_CUDA;
+    if (cudaMemcpyAsync(d_f, h_f, bytes, cudaMemcpyHostToDevice, pl->s_in) != cudaSuccess ||
+        cudaMemcpyAsync(d_fhat, h_fhat, bytes, cudaMemcpyHostToDevice, pl->s_in) != cudaSuccess ||
+        cudaEventRecord(sl.in_done, pl->s_in) != cudaSuccess)
+        return MSZ_ERR_CUDA;
+    // the correction, once the inputs are up and the slot's previous result
+    // has come down
+    if (cudaStreamWaitEvent(pl->s_comp, sl.in_done, 0) != cudaSuccess) return MSZ_ERR_CUDA;
+    if (sl.used && cudaStreamWaitEvent(pl->s_comp, sl.out_done, 0) != cudaSuccess) return MSZ_ERR_CUDA;
+    if ((st = enqueue_correct(sl.P, dev, pl->s_comp)) != MSZ_OK) return st;
+    if (cudaMemcpyAsync(&pl->h_ctrl[k], sl.P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, pl->s_comp) != cudaSuccess ||
+        cudaMemcpyAsync(&pl->h_rec[k], sl.P.log, sizeof(SweepRec), cudaMemcpyDeviceToHost, pl->s_comp) !=
+            cudaSuccess ||
+        cudaEventRecord(sl.comp_done, pl->s_comp) != cudaSuccess)
+        return MSZ_ERR_CUDA;
+    // the corrected field down
+    if (cudaStreamWaitEvent(pl->s_out, sl.comp_done, 0) != cudaSuccess ||
+        cudaMemcpyAsync(h_out, d_out, bytes, cudaMemcpyDeviceToHost, pl->s_out) != cudaSuccess ||
+        cudaEventRecord(sl.out_done, pl->s_out) != cudaSuccess)
+        return MSZ_ERR_CUDA;
+    sl.used = true;
+    sl.h_out = h_out;
+    sl.h_idx = h_edit_idx;
+    sl.h_del = h_edit_delta;
+    pl->head ^= 1;
+    pl->pending += 1;
+    return MSZ_OK;
+}
+
+extern "C" msz_status msz_pipeline_collect(msz_pipeline *pl, int64_t *h_edit_count, msz_stats *h_stats) {
+    if (!pl || !h_edit_count) return MSZ_ERR_INVALID_ARG;
+    if (pl->pending == 0) return MSZ_ERR_INVALID_ARG;
+    const int k = pl->tail;
+    msz_pipeline::Slot &sl = pl->slot[k];
+    pl->tail ^= 1;
+    pl->pending -= 1;
+    if (cudaEventSynchronize(sl.comp_done) != cudaSuccess) return MSZ_ERR_CUDA;
+    int64_t count = 0;
+    const msz_status st = finish_correct(pl->h_ctrl[k], pl->h_rec[k], pl->cap, &count, h_stats);
+    *h_edit_count = count;
+    const int64_t ne = count < pl->cap ? count : pl->cap;
+    if (ne > 0 && st != MSZ_ERR_INPUT_BOUND && st != MSZ_ERR_TIMEOUT) {
+        // the edit list down, behind the field (its length is known now)
+        char *w = pl->ws + (size_t)k * pl->slot_bytes;
+        const uint32_t *d_idx = (const uint32_t *)(w + pl->base + 3 * pl->fld);
+        const float *d_del = (const float *)(w + pl->base + 3 * pl->fld + pl->capb);
+        if (cudaMemcpyAsync(sl.h_idx, d_idx, (size_t)ne * 4, cudaMemcpyDeviceToHost, pl->s_out) != cudaSuccess ||
+            cudaMemcpyAsync(sl.h_del, d_del, (size_t)ne * 4, cudaMemcpyDeviceToHost, pl->s_out) != cudaSuccess ||
+            cudaEventRecord(sl.out_done, pl->s_out) != cudaSuccess)
+            return MSZ_ERR_CUDA;
+    }
+    if (cudaEventSynchronize(sl.out_done) != cudaSuccess) return MSZ_ERR_CUDA;
+    return st;
+}
+
+extern "C" void msz_pipeline_destroy(msz_pipeline *pl) {
+    if (!pl) return;
+    if (pl->s_in) cudaStreamSynchronize(pl->s_in);
+    if (pl->s_comp) cudaStreamSynchronize(pl->s_comp);
+    if (pl->s_out) cudaStreamSynchronize(pl->s_out);
+    for (auto &sl : pl->slot) {
+        if (sl.in_done) cudaEventDestroy(sl.in_done);
+        if (sl.comp_done) cudaEventDestroy(sl.comp_done);
+        if (sl.out_done) cudaEventDestroy(sl.out_done);
+    }
+    if (pl->s_in) cudaStreamDestroy(pl->s_in);
+    if (pl->s_comp) cudaStreamDestroy(pl->s_comp);
+    if (pl->s_out) cudaStreamDestroy(pl->s_out);
+    if (pl->h_ctrl) cudaFreeHost(pl->h_ctrl);
+    if (pl->h_rec) cudaFreeHost(pl->h_rec);
+    delete pl;
 }
 
 extern "C" const char *msz_status_str(msz_status status) {

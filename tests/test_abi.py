@@ -161,3 +161,22 @@ def test_edit_encoding_sizes_and_arguments_on_host():
     assert dec(None, 64, fake, 10, ctypes.byref(cnt), fake, ws, None) == api.ERR_INVALID_ARG
     assert dec(fake, 15, fake, 10, ctypes.byref(cnt), fake, ws, None) == api.ERR_INVALID_ARG
     assert dec(ctypes.c_void_p(257), 64, fake, 10, ctypes.byref(cnt), fake, ws, None) == api.ERR_INVALID_ARG
+
+
+def test_pipeline_arguments_on_host():
+    from paper_2601_01787_gb300 import api
+    lib = api.load()
+    g = api.grid_of((6, 7, 8))
+    assert lib.msz_pipeline_workspace_size(g, 10) >= 2 * lib.msz_host_workspace_size(g, 10)
+    assert lib.msz_pipeline_workspace_size(api.Grid(4, 0, 1, 1, 1), 10) == 0
+    assert lib.msz_pipeline_workspace_size(g, -1) == 0
+    h = ctypes.c_void_p()
+    fake = ctypes.c_void_p(256)
+    assert lib.msz_pipeline_create(g, 10, fake, 1 << 30, None) == api.ERR_INVALID_ARG
+    assert lib.msz_pipeline_create(g, -1, fake, 1 << 30, ctypes.byref(h)) == api.ERR_INVALID_ARG
+    assert lib.msz_pipeline_create(g, 10, fake, 64, ctypes.byref(h)) == api.ERR_WORKSPACE
+    assert lib.msz_pipeline_create(g, 10, ctypes.c_void_p(260), 1 << 30, ctypes.byref(h)) == api.ERR_INVALID_ARG
+    cnt = ctypes.c_int64()
+    assert lib.msz_pipeline_submit(None, fake, fake, ctypes.c_float(0.1), fake, fake, fake, None) == api.ERR_INVALID_ARG
+    assert lib.msz_pipeline_collect(None, ctypes.byref(cnt), None) == api.ERR_INVALID_ARG
+    lib.msz_pipeline_destroy(None)  # a no-op
