@@ -30,7 +30,8 @@ Stream (little-endian), B = 256 edits per block, nb = ceil(count / B):
     payload       per block of c edits: the c values d_j packed wd bits each,
                   LSB first into 32-bit words (value j at bit j*wd of the
                   section), the section padded to whole words; then the c
-                  values m_j - 1 packed wm bits each the same way.
+                  values (m_j - 1) mod 2^32 packed wm bits each the same way
+                  (an index listed with g_i = fhat_i, m = 0, stays exact).
 with d_0 = 0 and d_j = i_j - i_{j-1} - 1, and the width of a section the bit
 length of its largest value (0 when every value is 0: the section is empty).
 """
@@ -109,13 +110,14 @@ def encode(idx: np.ndarray, m: np.ndarray) -> bytes:
         d = np.zeros(len(bi), dtype=np.uint64)
         d[1:] = bi[1:] - bi[:-1] - 1
         w1 = bit_width(int(d.max()))
-        w2 = bit_width(int((bm - 1).max()))
+        mq = (bm + 0xFFFFFFFF) & 0xFFFFFFFF  # (m - 1) mod 2^32
+        w2 = bit_width(int(mq.max()))
         first.append(int(bi[0]))
         start.append(len(payload))
         wd.append(w1)
         wm.append(w2)
         payload += pack(d, w1)
-        payload += pack(bm - 1, w2)
+        payload += pack(mq, w2)
     head = np.array([MAGIC, BLOCK], dtype="<u4").tobytes() + np.array([count], dtype="<u8").tobytes()
     table = (np.array(first, dtype="<u4").tobytes() + np.array(start, dtype="<u4").tobytes()
              + np.array(wd, dtype="u1").tobytes() + np.array(wm, dtype="u1").tobytes())
@@ -145,7 +147,7 @@ def decode(stream: bytes) -> tuple[np.ndarray, np.ndarray]:
         nd = (c * int(wd[k]) + 31) // 32
         nm = (c * int(wm[k]) + 31) // 32
         d = unpack(words[s:s + nd], c, int(wd[k]))
-        mm = unpack(words[s + nd:s + nd + nm], c, int(wm[k])) + 1
+        mm = (unpack(words[s + nd:s + nd + nm], c, int(wm[k])) + 1) & 0xFFFFFFFF
         i = int(first[k])
         for j in range(c):
             if j:
@@ -175,7 +177,7 @@ def encoded_size(idx: np.ndarray, m: np.ndarray) -> int:
         bm = m[k * BLOCK:(k + 1) * BLOCK]
         c = len(bi)
         w1 = bit_width(int((bi[1:] - bi[:-1] - 1).max())) if c > 1 else 0
-        w2 = bit_width(int((bm - 1).max()))
+        w2 = bit_width(int(((bm + 0xFFFFFFFF) & 0xFFFFFFFF).max()))
         words += (c * w1 + 31) // 32 + (c * w2 + 31) // 32
     table = 8 * nb + 2 * nb
     return 16 + table + (-table % 4) + 4 * words

@@ -108,3 +108,12 @@ def test_length_of_a_uniform_list():
     idx = np.arange(0, 3 * 256 * 3, 3, dtype=np.uint64)
     m = np.ones(idx.size, dtype=np.uint64)
     assert len(E.encode(idx, m)) == 16 + 32 + 3 * 16 * 4
+
+
+def test_zero_distance_wraps_to_the_widest_field():
+    # an index listed with g_i == fhat_i: m = 0, stored as (0 - 1) mod 2^32
+    idx, m = np.array([5, 6]), np.array([0, 3])
+    s = E.encode(idx, m)
+    assert s[16 + 8 + 1] == 32  # wm
+    i2, m2 = E.decode(s)
+    assert list(i2) == [5, 6] and list(m2) == [0, 3]
