@@ -285,10 +285,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
             // worklist is cleared as it is read (a word never straddles two
             // fields: bases are 1024-aligned).
             walk_words_pairs(
-                P.all,
-                [&](uint32_t wi) -> uint32_t {
+                P.all, [&](uint32_t wi) -> uint32_t { return dcur[wi]; },
+                [&](uint32_t wi, uint32_t wl) -> uint32_t {
                     const uint32_t f = field_of(P.bfield, wi * 32u);
-                    const uint32_t wl = dcur[wi];
                     if (wl) dcur[wi] = 0u;
                     if (!alive(f)) return 0u;
                     if (dense_next) return P.ub[wi];

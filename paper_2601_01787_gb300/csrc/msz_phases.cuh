@@ -194,16 +194,32 @@ __device__ __forceinline__ void walk_bits_pairs(uint32_t *bm, const uint32_t *fi
     }
 }
 
-// Like walk_bits_pairs, with the bits of word w supplied by load_word(w)
-// (which may read, clear and count whatever it needs).
-template <class LW, class F>
-__device__ __forceinline__ void walk_words_pairs(const GridDev &G, LW &&load_word, F &&fn) {
+// Like walk_bits_pairs, with the bits of word w given by finish(w, raw),
+// where raw = fetch(w) is loaded kAhead chunks ahead (fetch only loads;
+// finish may read, clear and count whatever else it needs).
+template <class FE, class FI, class F>
+__device__ __forceinline__ void walk_words_pairs(const GridDev &G, FE &&fetch, FI &&finish, F &&fn) {
     const uint32_t lane = lane_id();
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t base = gw * 32u; base < G.words; base += nw * 32u) {
+    const uint32_t chunks = (G.words + 31u) / 32u;
+    uint32_t pre[kAhead];
+#pragma unroll
+    for (int u = 0; u < kAhead; ++u) {
+        const uint32_t wi = (gw + (uint32_t)u * nw) * 32u + lane;
+        pre[u] = wi < G.words ? fetch(wi) : 0u;
+    }
+    for (uint32_t c = gw; c < chunks; c += nw) {
+        const uint32_t base = c * 32u;
         const uint32_t wi = base + lane;
-        uint32_t bits = wi < G.words ? load_word(wi) : 0u;
+        const uint32_t raw = pre[0];
+#pragma unroll
+        for (int u = 0; u + 1 < kAhead; ++u) pre[u] = pre[u + 1];
+        {
+            const uint32_t wn = (c + (uint32_t)kAhead * nw) * 32u + lane;
+            pre[kAhead - 1] = wn < G.words ? fetch(wn) : 0u;
+        }
+        uint32_t bits = wi < G.words ? finish(wi, raw) : 0u;
         const bool dense = __popc(bits) >= kDenseWord;
         uint32_t dm = __ballot_sync(kFull, dense);
         while (dm) {
