@@ -701,7 +701,8 @@ __device__ __forceinline__ void first_tiled_tma(const FieldView &P, const CUtens
 // uncertified vertex gets its code in g from the staged planes and its code
 // of f from codes_f; distorted ones mark their targets and themselves in
 // dnext (the next sweep's worklist).  nx is a multiple of 4, so a lane's 4
-// vertices have their 4 uncertified bits in one bitmap word.
+// vertices have their 4 uncertified bits in one bitmap word and their codes
+// of f in one aligned 32-bit word.
 __device__ __forceinline__ void detect_tiled_tma(const FieldView &P, const CUtensorMap *map_g, uint32_t *tile_next,
                                                  float *smem_raw, uint32_t *err, uint32_t *dnext,
                                                  uint32_t &distorted) {
@@ -710,10 +711,14 @@ __device__ __forceinline__ void detect_tiled_tma(const FieldView &P, const CUten
                  [&](const float *pm, const float *p0, const float *pp, int r, int x0, uint32_t rowbase) {
                      const uint32_t lane = lane_id();
                      const int xl = x0 + 4 * (int)lane;
-                     uint32_t nib = 0;
+                     // the row's uncertified bits and codes of f, both loaded
+                     // up front (coalesced); a vertex's code of f then comes
+                     // from the lane that loaded it
+                     uint32_t nib = 0, cfw = 0;
                      if (xl < (int)P.G.nx) {
                          const uint32_t i0 = rowbase + (uint32_t)xl;
                          nib = (__ldg(&P.ub[i0 >> 5]) >> (i0 & 31u)) & 15u;
+                         cfw = __ldg(reinterpret_cast<const uint32_t *>(P.codes_f + i0));
                      }
                      uint32_t w = nib << (4u * (lane & 7u));
                      w |= __shfl_xor_sync(kFull, w, 1);
@@ -727,17 +732,16 @@ __device__ __forceinline__ void detect_tiled_tma(const FieldView &P, const CUten
                      for (uint32_t j0 = 0; j0 < total; j0 += 32u) {
                          const uint32_t j = j0 + lane;
                          const bool has = j < total;
-                         uint32_t v = 0, cf = 0, cg = 0;
+                         uint32_t col = 0, cg = 0;
                          if (has) {
                              const uint32_t q = j < c0 ? 0u : j < c1 ? 1u : j < c2 ? 2u : 3u;
                              const uint32_t wq = q == 0 ? w0 : q == 1 ? w1 : q == 2 ? w2 : w3;
                              const uint32_t before = q == 0 ? 0u : q == 1 ? c0 : q == 2 ? c1 : c2;
-                             const uint32_t col = 32u * q + nth_set(wq, j - before);
-                             v = rowbase + (uint32_t)x0 + col;
-                             cf = __ldg(&P.codes_f[v]);
+                             col = 32u * q + nth_set(wq, j - before);
                              cg = code1(pm, p0, pp, r, 4 + (int)col);
                          }
-                         report(P, E, has, v, cf, cg);
+                         const uint32_t cf = (__shfl_sync(kFull, cfw, (int)(col >> 2)) >> (8u * (col & 3u))) & 0xffu;
+                         report(P, E, has, rowbase + (uint32_t)x0 + col, cf, cg);
                      }
                      distorted += E.distorted;
                  });
