@@ -584,11 +584,12 @@ __device__ __forceinline__ void own_row_tma(const FieldView &P, const float *p0,
 // in a slot); row(pm, p0, pp, r, x0, rowbase) runs for every warp row inside
 // the grid with the staged planes z-1, z, z+1.
 template <int NBOX, class ROW>
-__device__ __forceinline__ void tma_tiles(const FieldView &P, const CUtensorMap *map0, const CUtensorMap *map1,
-                                          uint32_t *tile_next, float *smem_raw, uint32_t *err, ROW &&row) {
+__device__ __forceinline__ void tma_tiles(const FieldView &P, uint32_t tile_z, const CUtensorMap *map0,
+                                          const CUtensorMap *map1, uint32_t *tile_next, float *smem_raw,
+                                          uint32_t *err, ROW &&row) {
     using namespace tile;
     const GridDev &G = P.G;
-    const TileGeom tg = tile_geom(G.nx, G.ny, G.nz, P.tile_z);
+    const TileGeom tg = tile_geom(G.nx, G.ny, G.nz, tile_z);
     constexpr uint32_t kWarps = THREADS / 32;
     __shared__ uint32_t s_tile;
     __shared__ __align__(8) uint64_t s_full[NSLOT];
@@ -689,7 +690,7 @@ __device__ __forceinline__ void first_tiled_tma(const FieldView &P, const CUtens
                                                 uint32_t *tile_next, float *smem_raw, uint32_t *err,
                                                 uint32_t &distorted) {
     bool bad = false;
-    tma_tiles<2>(P, map_f, map_s, tile_next, smem_raw, err,
+    tma_tiles<2>(P, P.tile_z, map_f, map_s, tile_next, smem_raw, err,
                  [&](const float *pm, const float *p0, const float *pp, int r, int x0, uint32_t rowbase) {
                      own_row_tma<DETECT>(P, p0, r, x0, rowbase, bad);
                      tile_row<DETECT>(P, pm, p0, pp, tile::TFIELD, r, x0, rowbase, distorted);
@@ -703,11 +704,11 @@ __device__ __forceinline__ void first_tiled_tma(const FieldView &P, const CUtens
 // dnext (the next sweep's worklist).  nx is a multiple of 4, so a lane's 4
 // vertices have their 4 uncertified bits in one bitmap word and their codes
 // of f in one aligned 32-bit word.
-__device__ __forceinline__ void detect_tiled_tma(const FieldView &P, const CUtensorMap *map_g, uint32_t *tile_next,
-                                                 float *smem_raw, uint32_t *err, uint32_t *dnext,
-                                                 uint32_t &distorted) {
+__device__ __forceinline__ void detect_tiled_tma(const FieldView &P, uint32_t tile_z, const CUtensorMap *map_g,
+                                                 uint32_t *tile_next, float *smem_raw, uint32_t *err,
+                                                 uint32_t *dnext, uint32_t &distorted) {
     using namespace tile;
-    tma_tiles<1>(P, map_g, nullptr, tile_next, smem_raw, err,
+    tma_tiles<1>(P, tile_z, map_g, nullptr, tile_next, smem_raw, err,
                  [&](const float *pm, const float *p0, const float *pp, int r, int x0, uint32_t rowbase) {
                      const uint32_t lane = lane_id();
                      const int xl = x0 + 4 * (int)lane;
