@@ -81,10 +81,13 @@ typedef enum { MSZ_RULE_HALVE = 0, MSZ_RULE_SNAP = 1 } msz_rule;
 
 typedef struct {
     int32_t rule;             /* msz_rule; default HALVE */
-    int32_t test_fault;       /* 0.  Test hook of the bounded waits: 1 makes block 0 of the
+    int32_t test_fault;       /* 0.  Test hooks of the bounded waits: 1 makes block 0 of the
                                  correction kernel wait at its first grid barrier without
                                  arriving, so every block's wait (shortened to 0.25 s) runs
-                                 out and the call returns MSZ_ERR_TIMEOUT with no output */
+                                 out; 2 (grids whose planes are staged by TMA) makes block 0
+                                 of the code pass withhold its first plane copy, so its
+                                 mbarrier wait (shortened to 0.25 s) runs out.  Either way
+                                 the call returns MSZ_ERR_TIMEOUT with no output */
     int64_t max_sweeps;       /* <= 0: MSZ_MAX_SWEEPS_LIMIT; else 1..MSZ_MAX_SWEEPS_LIMIT */
     int64_t dense_min_items;  /* > 0: the next sweep scans every uncertified vertex instead of
                                  the worklist when 6 x (vertices distorted in this sweep) >=

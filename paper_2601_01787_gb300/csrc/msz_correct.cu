@@ -60,7 +60,8 @@ struct Problem {
     unsigned long long edit_cap;
     uint32_t max_sweeps;
     long long dense_min;  // < 0: never scan densely after sweep 0
-    uint32_t test_fault;  // test hook: block 0 does not arrive at the first grid barrier
+    uint32_t test_fault;  // test hooks: 1: block 0 does not arrive at the first grid barrier;
+                          // 2: block 0 of the TMA code pass withholds its first plane copy
     uint32_t detect_tile_z;  // planes per tile of the whole-grid TMA detection
 };
 
@@ -89,16 +90,20 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
     bool ok;
     if (NDIM == 3) {
         uint32_t distorted = 0;
-        if (TMA) first_tiled_tma<true>(F, &P.map_f, &P.map_s, &P.log[0].tile_next, smem, &C->error, distorted);
+        if (TMA)
+            first_tiled_tma<true>(F, &P.map_f, &P.map_s, &P.log[0].tile_next, smem, &C->error, distorted,
+                                  P.test_fault == 2);
         else first_tiled<true>(F, &P.log[0].tile_next, smem, &C->error, distorted);
         warp_add(distorted, &P.log[0].distorted);
-        ok = P.test_fault ? grid_barrier(&C->bar_count, &C->bar_gen, &C->error, kTestBarrierNs, blockIdx.x == 0)
-                          : grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
+        ok = P.test_fault == 1
+                 ? grid_barrier(&C->bar_count, &C->bar_gen, &C->error, kTestBarrierNs, blockIdx.x == 0)
+                 : grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
         if (leader) C->t_codes = global_ns();
     } else {
         first_generic<NDIM>(F, &C->error);
-        ok = P.test_fault ? grid_barrier(&C->bar_count, &C->bar_gen, &C->error, kTestBarrierNs, blockIdx.x == 0)
-                          : grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
+        ok = P.test_fault == 1
+                 ? grid_barrier(&C->bar_count, &C->bar_gen, &C->error, kTestBarrierNs, blockIdx.x == 0)
+                 : grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
         if (leader) C->t_codes = global_ns();
         if (ok) {
             Emitter E{F.dm[1], 0};
@@ -432,7 +437,7 @@ static msz_status prepare_correct(const float *d_f, const float *d_fhat, float x
     o = msz_options{};
     if (opt) o = *opt;
     if (o.rule != MSZ_RULE_HALVE && o.rule != MSZ_RULE_SNAP) return MSZ_ERR_INVALID_ARG;
-    if (o.test_fault != 0 && o.test_fault != 1) return MSZ_ERR_INVALID_ARG;
+    if (o.test_fault < 0 || o.test_fault > 2) return MSZ_ERR_INVALID_ARG;
     if (o.max_sweeps > MSZ_MAX_SWEEPS_LIMIT || o.dense_min_items < -1 || o.log_capacity < 0 || o.tile_z < 0 ||
         o.tile_z > 1024 ||
         (o.log_capacity > 0 && !o.h_sweep_log))

@@ -582,11 +582,12 @@ __device__ __forceinline__ void own_row_tma(const FieldView &P, const float *p0,
 // The TMA plane ring over the tiles of field P (block-collective): NBOX
 // boxes a plane (maps[0..NBOX-1], each TFIELD floats after the previous one
 // in a slot); row(pm, p0, pp, r, x0, rowbase) runs for every warp row inside
-// the grid with the staged planes z-1, z, z+1.
+// the grid with the staged planes z-1, z, z+1.  withhold (a test hook): block
+// 0 never issues its first plane, so its waits run out after kTestWaitNs.
 template <int NBOX, class ROW>
 __device__ __forceinline__ void tma_tiles(const FieldView &P, uint32_t tile_z, const CUtensorMap *map0,
                                           const CUtensorMap *map1, uint32_t *tile_next, float *smem_raw,
-                                          uint32_t *err, ROW &&row) {
+                                          uint32_t *err, ROW &&row, bool withhold = false) {
     using namespace tile;
     const GridDev &G = P.G;
     const TileGeom tg = tile_geom(G.nx, G.ny, G.nz, tile_z);
@@ -614,6 +615,8 @@ __device__ __forceinline__ void tma_tiles(const FieldView &P, uint32_t tile_z, c
     tma::fence_proxy_async_global();
     __syncthreads();
     uint32_t ph = 0;  // bit q: parity of the next completion of slot q's barrier
+    const uint64_t limit = withhold ? tma::kTestWaitNs : tma::kWaitNs;
+    bool first_tile = true;
     for (;;) {
         __syncthreads();
         if (tid == 0) s_tile = atomicAdd(tile_next, 1u);
@@ -634,7 +637,7 @@ __device__ __forceinline__ void tma_tiles(const FieldView &P, uint32_t tile_z, c
         };
         auto wait_plane = [&](int p) -> bool {
             const int q = slot_of(p);
-            if (!tma::mbar_wait_bounded(tma::smem_u32(&s_full[q]), (ph >> q) & 1u, &s_dead)) return false;
+            if (!tma::mbar_wait_bounded(tma::smem_u32(&s_full[q]), (ph >> q) & 1u, &s_dead, limit)) return false;
             ph ^= 1u << q;
             if (tid == 0) s_pending[q] = 0;
             return true;
@@ -643,8 +646,10 @@ __device__ __forceinline__ void tma_tiles(const FieldView &P, uint32_t tile_z, c
         // plane NSLOT before it is released
         if (tid == 0) {
             tma::fence_proxy_async();  // the previous tile's reads of the ring come first
-            for (int q = 0; q < NSLOT && zb - 1 + q <= ze; ++q) issue(zb - 1 + q, q);
+            for (int q = 0; q < NSLOT && zb - 1 + q <= ze; ++q)
+                if (!(withhold && first_tile && blockIdx.x == 0 && q == 0)) issue(zb - 1 + q, q);
         }
+        first_tile = false;
         bool alive = wait_plane(zb - 1) && wait_plane(zb);
         const int y = y0 + (int)warp, r = (int)warp + 1;
         for (int z = zb; alive && z < ze; ++z) {
@@ -679,7 +684,7 @@ __device__ __forceinline__ void tma_tiles(const FieldView &P, uint32_t tile_z, c
         // copies still in flight land before the block leaves (bounded)
         uint32_t none = 0;
         for (int q = 0; q < NSLOT; ++q)
-            if (s_pending[q]) tma::mbar_wait_bounded(tma::smem_u32(&s_full[q]), (ph >> q) & 1u, &none);
+            if (s_pending[q]) tma::mbar_wait_bounded(tma::smem_u32(&s_full[q]), (ph >> q) & 1u, &none, limit);
     }
 }
 
@@ -688,13 +693,15 @@ __device__ __forceinline__ void tma_tiles(const FieldView &P, uint32_t tile_z, c
 template <bool DETECT>
 __device__ __forceinline__ void first_tiled_tma(const FieldView &P, const CUtensorMap *map_f, const CUtensorMap *map_s,
                                                 uint32_t *tile_next, float *smem_raw, uint32_t *err,
-                                                uint32_t &distorted) {
+                                                uint32_t &distorted, bool withhold = false) {
     bool bad = false;
-    tma_tiles<2>(P, P.tile_z, map_f, map_s, tile_next, smem_raw, err,
-                 [&](const float *pm, const float *p0, const float *pp, int r, int x0, uint32_t rowbase) {
-                     own_row_tma<DETECT>(P, p0, r, x0, rowbase, bad);
-                     tile_row<DETECT>(P, pm, p0, pp, tile::TFIELD, r, x0, rowbase, distorted);
-                 });
+    tma_tiles<2>(
+        P, P.tile_z, map_f, map_s, tile_next, smem_raw, err,
+        [&](const float *pm, const float *p0, const float *pp, int r, int x0, uint32_t rowbase) {
+            own_row_tma<DETECT>(P, p0, r, x0, rowbase, bad);
+            tile_row<DETECT>(P, pm, p0, pp, tile::TFIELD, r, x0, rowbase, distorted);
+        },
+        withhold);
     if (bad) atomicOr(err, kErrInput);
 }
 

@@ -11,7 +11,8 @@
 namespace msz {
 namespace tma {
 
-constexpr uint64_t kWaitNs = 2000000000ull;  // bound of one mbarrier wait (2 s of %globaltimer)
+constexpr uint64_t kWaitNs = 2000000000ull;      // bound of one mbarrier wait (2 s of %globaltimer)
+constexpr uint64_t kTestWaitNs = 250000000ull;   // ... under the test hook that withholds a copy
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -31,10 +32,11 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
     return done != 0;
 }
 
-// Waits for the phase of the given parity; gives up after kWaitNs, or as
+// Waits for the phase of the given parity; gives up after limit_ns, or as
 // soon as *dead is set by another thread of the block.  Returns whether the
 // phase completed.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t a, uint32_t parity, volatile uint32_t *dead) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t a, uint32_t parity, volatile uint32_t *dead,
+                                                  uint64_t limit_ns = kWaitNs) {
     uint64_t t0 = 0;
     for (uint32_t it = 0;; ++it) {
         if (mbar_try(a, parity)) return true;
@@ -42,7 +44,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t a, uint32_t parity, v
             if (*dead) return false;
             const uint64_t now = global_ns();
             if (!t0) t0 = now;
-            else if (now - t0 > kWaitNs) return false;
+            else if (now - t0 > limit_ns) return false;
         }
     }
 }

@@ -66,7 +66,7 @@ def test_invalid_arguments_rejected_on_host():
     st = lib.msz_correct(fake, fake, ctypes.c_float(0.1), g, fake, None, None, 0, ctypes.byref(cnt),
                          ctypes.byref(bad_opt), None, fake, 1 << 30, None)
     assert st == api.ERR_INVALID_ARG
-    bad_hook = api.Options(0, 2, 0, 0, None, None, 0)  # test_fault takes 0 or 1
+    bad_hook = api.Options(0, 3, 0, 0, None, None, 0)  # test_fault takes 0, 1 or 2
     st = lib.msz_correct(fake, fake, ctypes.c_float(0.1), g, fake, None, None, 0, ctypes.byref(cnt),
                          ctypes.byref(bad_hook), None, fake, 1 << 30, None)
     assert st == api.ERR_INVALID_ARG

@@ -1,8 +1,10 @@
 """Failure detection without a GPU fault: every device-side wait of the
-correction kernel is bounded.  The test hook makes block 0 wait at the first
-grid barrier without arriving, so every block's wait runs out (0.25 s); the
-kernel records the timeout and returns, the host reports MSZ_ERR_TIMEOUT, and
-the same context then corrects exactly as before."""
+correction kernel is bounded.  Test hook 1 makes block 0 wait at the first
+grid barrier without arriving, so every block's wait runs out (0.25 s); hook
+2 makes block 0 of the TMA-staged code pass withhold a plane copy, so its
+mbarrier wait runs out.  The kernel records the timeout and returns, the host
+reports MSZ_ERR_TIMEOUT, and the same context then corrects exactly as
+before."""
 import numpy as np
 import pytest
 import torch
@@ -60,3 +62,21 @@ def test_static_entry_point_reports_the_timeout_too(api):
     assert st in (api.OK, api.ERR_CAPACITY)
     ref = oracle.correct(fl.f, fl.fhat, fl.xi)
     assert np.array_equal(_bits(out), np.ascontiguousarray(ref.g).view(np.uint32))
+
+
+def test_withheld_plane_copy_times_out_the_tma_ring(api):
+    """Hook 2: block 0 of the TMA-staged code pass never issues its first plane
+    copy, so its mbarrier wait runs out (0.25 s): the block records the
+    timeout, waits for its other copies and leaves; the call reports
+    MSZ_ERR_TIMEOUT and the next correction on the same context is exact."""
+    fl = synth.perlin3d_prequant((256, 256, 256), seed=35, eb_rel=1e-4)
+    f, fh = torch.from_numpy(fl.f).cuda(), torch.from_numpy(fl.fhat).cuda()
+    bad = api.correct(f, fh, fl.xi, test_fault=2, edit_capacity=0)
+    assert bad.status == api.ERR_TIMEOUT
+    small = synth.perlin3d_prequant((24, 20, 140), seed=36, eb_rel=1e-4)  # also staged by TMA
+    g = api.correct(torch.from_numpy(small.f).cuda(), torch.from_numpy(small.fhat).cuda(), small.xi)
+    ref = oracle.correct(small.f, small.fhat, small.xi)
+    assert g.status == ref.status == api.OK
+    assert np.array_equal(_bits(g.out), np.ascontiguousarray(ref.g).view(np.uint32))
+    again = api.correct(f, fh, fl.xi, edit_capacity=0)
+    assert again.status in (api.OK, api.ERR_CAPACITY)
