@@ -577,6 +577,7 @@ def run_learned(dev, stream, reps: int = 3) -> dict:
     assert rp.status == api.OK, api.status_str(rp.status)
     vp = api.verify(f, out)
     stream_plain = edit_stream(fh, out, eidx, rp.edit_count, stream)
+    dense = dense_sweeps(api.correct(f, fh, fl.xi, log_capacity=1024, **kw), fl.n)
     timed(lambda: learned.correct_learned(f, fh, fl.xi, net, **kw))
     t_learned, rl = timed(lambda: learned.correct_learned(f, fh, fl.xi, net, **kw))
     assert rl.result.status == api.OK, api.status_str(rl.result.status)
@@ -592,7 +593,7 @@ def run_learned(dev, stream, reps: int = 3) -> dict:
                       "sweeps": rp.stats["sweeps"], "first_distorted": rp.stats["first_distorted"],
                       "edited": rp.edit_count, "kernel_ms": round(rp.stats["kernel_ns"] / 1e6, 4),
                       "verified": bool(vp["codes_equal"] and vp["wrong_labels"] == 0),
-                      "edit_stream": stream_plain},
+                      "edit_stream": stream_plain, "dense_sweeps": dense},
             "learned": {"ms": round(t_learned, 4), "value": round(n / (t_learned * 1e-3) / 1e9, 4),
                         "propose_ms": round(rl.propose_ms, 4),
                         "loop_kernel_ms": round(rl.from_g0.stats["kernel_ns"] / 1e6, 4),
@@ -606,6 +607,27 @@ def run_learned(dev, stream, reps: int = 3) -> dict:
             "training": {"recipe": learned.RECIPE | {"shape": list(learned.RECIPE["shape"])},
                          "cached": info["cached"], "train_s": None if info.get("train_s") is None else
                          round(info["train_s"], 2), "final_loss": info.get("final_loss")}}
+
+
+def dense_sweeps(res, n: int) -> dict | None:
+    """The whole-grid detection sweeps of a correction (from its sweep log
+    and device timeline): their mean device time and HBM rate.  Compulsory
+    bytes of one: read g (4 B/vertex, staged by TMA), read the uncertified
+    bitmap and clear the worklist bitmap (N/8 B each), read the codes of f of
+    the uncertified vertices (1 B each)."""
+    log, tl = res.sweep_log, res.timeline
+    ms = []
+    for k in range(1, len(log)):
+        if int(log[k, 0]) == n and tl[k][0] > 0 and tl[k - 1][1] > 0:
+            ms.append((tl[k][0] - tl[k - 1][1]) / 1e6)
+    if not ms:
+        return None
+    peak, kind = load_peaks()
+    nbytes = 4 * n + 2 * (n // 8) + int(res.stats["uncertified"])
+    mean = sum(ms) / len(ms)
+    gbs = nbytes / (mean * 1e-3) / 1e9
+    return {"count": len(ms), "ms_mean": round(mean, 4), "algorithmic_bytes": nbytes, "gbs": round(gbs, 1),
+            "frac_of_hbm": round(gbs / peak, 4), "peak_kind": kind}
 
 
 def edit_stream(fh, g, eidx, count: int, stream, reps: int = 3) -> dict:

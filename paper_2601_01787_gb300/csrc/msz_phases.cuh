@@ -19,7 +19,14 @@
 namespace msz {
 
 constexpr uint32_t kTileZ = 32;  // default planes per tile of the code pass
-constexpr int kDenseWord = 6;    // set bits from which a bitmap word is walked by the whole warp
+#ifndef MSZ_DENSE_WORD
+#define MSZ_DENSE_WORD 10
+#endif
+// set bits from which a bitmap word is walked by the whole warp (one vertex
+// a lane, coalesced neighbour loads) rather than bit by bit in its own lane
+// (measured on the 512^3 peak field: 3, 4, 6, 10, 14, 20, never -> 25.1,
+// 23.9, 22.2, 21.4, 21.5, 21.7, 21.6 ms; the Perlin field within 1 %)
+constexpr int kDenseWord = MSZ_DENSE_WORD;
 constexpr int kAhead = 4;        // bitmap chunks a walking warp has loaded ahead
 
 struct FieldView {
