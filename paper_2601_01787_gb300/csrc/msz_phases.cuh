@@ -27,7 +27,10 @@ constexpr uint32_t kTileZ = 32;  // default planes per tile of the code pass
 // (measured on the 512^3 peak field: 3, 4, 6, 10, 14, 20, never -> 25.1,
 // 23.9, 22.2, 21.4, 21.5, 21.7, 21.6 ms; the Perlin field within 1 %)
 constexpr int kDenseWord = MSZ_DENSE_WORD;
-constexpr int kAhead = 4;        // bitmap chunks a walking warp has loaded ahead
+#ifndef MSZ_WALK_AHEAD
+#define MSZ_WALK_AHEAD 4
+#endif
+constexpr int kAhead = MSZ_WALK_AHEAD;  // bitmap chunks a walking warp has loaded ahead
 
 struct FieldView {
     GridDev G;
