@@ -178,7 +178,9 @@ def test_tma_and_cp_async_staging_agree(api, shape, dense):
 
 # ----------------------------------------------------- edges and errors
 @pytest.mark.parametrize("shape", [(1, 1), (1, 1, 1), (1, 2), (2, 1), (1, 1, 5), (1, 7, 1), (3, 1, 1), (2, 2, 2),
-                                   (1, 33), (33, 1, 2)])
+                                   (1, 33), (33, 1, 2),
+                                   # thin grids staged by TMA: one or two planes, the smallest box
+                                   (1, 12, 140), (2, 10, 136), (1, 10, 264)])
 def test_degenerate_grids(api, shape):
     rng = np.random.default_rng(sum(shape))
     f = rng.integers(0, 3, size=shape).astype(np.float32) / np.float32(4)
