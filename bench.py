@@ -386,7 +386,7 @@ def run_ours(args, ws, rank, local):
         del f, fh, out, eidx, edel, hf, hfh, hout, hidx, hdel, hout2, hidx2, hdel2, sets
         api._ws_cache.clear()
         torch.cuda.empty_cache()
-        line["batch"] = run_batch(dev, stream)
+        line["batch"] = run_batch(dev, stream, sm_mhz=clk.get("sm_mhz"))
     if rank == 0 and args.large:
         f = fh = out = None  # drop the 512^3 buffers (if the batch leg has not already)
         api._ws_cache.clear()
@@ -478,7 +478,7 @@ def run_large(dev, stream, reps: int = 3) -> dict:
             "edited": r.edit_count, "kernel_ms": round(r.stats["kernel_ns"] / 1e6, 4)}
 
 
-def run_batch(dev, stream, reps: int = 5) -> dict:
+def run_batch(dev, stream, reps: int = 5, sm_mhz: float | None = None) -> dict:
     """Secondary workload: 64 prequantized Perlin fields, axes uniform in
     64..384, eb_rel in {1e-3, 1e-4, 1e-5} (seeds 1000+k), corrected by one
     msz_correct_batch launch (tile depths from the autotuner), against the same
@@ -531,13 +531,28 @@ def run_batch(dev, stream, reps: int = 5) -> dict:
 
     singles()
     t_single = timed(singles)
+    # roofline of the batch kernel: the same operation and byte counts as the
+    # single-field kernel, summed over the fields (their sweep logs and
+    # uncertified counts from one more launch)
+    rl = api.correct_batch(fs, fhs, xis, edit_capacities=caps, outs=outs, tile_z=tz, stream=stream,
+                           log_capacity=64)
+    ops = sum(algorithmic_alu_ops(fl.n, r.sweep_log, r.stats["uncertified"]) for fl, r in zip(fields, rl.fields))
+    nbytes = sum(algorithmic_bytes(fl.n, r.sweep_log, r.edit_count, r.stats["uncertified"])
+                 for fl, r in zip(fields, rl.fields))
+    alu_pk = alu_peak(sm_mhz or 2070.0) / 1e9
+    peak, peak_kind = load_peaks()
+    t_s = t_batch * 1e-3
+    roof = {"bound": "alu", "kernel": "k_batch", "ops": ops, "achieved": round(ops / t_s / 1e9, 1),
+            "peak": round(alu_pk, 1), "unit": "Gop/s", "frac": round(ops / t_s / 1e9 / alu_pk, 4),
+            "hbm": {"algorithmic_bytes": nbytes, "achieved": round(nbytes / t_s / 1e9, 1), "peak": peak,
+                    "unit": "GB/s", "frac": round(nbytes / t_s / 1e9 / peak, 4), "peak_kind": peak_kind}}
     return {"workload": "perlin3d_prequant batch of 64, axes U{64..384}, eb_rel in {1e-3,1e-4,1e-5}, seeds 1000+k",
             "n_vertices": n_tot, "unit": UNIT, "value": round(n_tot / (t_batch * 1e-3) / 1e9, 4),
             "ms": round(t_batch, 4), "graph_replay_ms": round(t_graph, 4),
             "graph_replay_value": round(n_tot / (t_graph * 1e-3) / 1e9, 4), "separate_calls_ms": round(t_single, 4),
             "separate_calls_value": round(n_tot / (t_single * 1e-3) / 1e9, 4),
             "max_sweeps_over_fields": max(r.stats["sweeps"] for r in res.fields),
-            "tile_z": sorted(set(tz)), "launches": 1}
+            "tile_z": sorted(set(tz)), "launches": 1, "roofline": roof}
 
 
 def run_learned(dev, stream, reps: int = 3) -> dict:
@@ -660,9 +675,21 @@ def edit_stream(fh, g, eidx, count: int, stream, reps: int = 3) -> dict:
     dec_ms, got = timed(dec)
     exact = got == count and torch.equal(field.view(torch.int32), g1.view(torch.int32))
     nbytes = int(s.numel())
+    # compulsory bytes: encoding reads the indices (4 B), fhat and g at them
+    # (8 B) and writes the stream; decoding reads the stream and rewrites the
+    # field at the indices (8 B) -- plus the copy of fhat the timing includes
+    enc_b = 12 * count + nbytes
+    dec_b = nbytes + 8 * count + 8 * fh1.numel()
+    peak, kind = load_peaks()
+    enc_gbs, dec_gbs = enc_b / (enc_ms * 1e-3) / 1e9, dec_b / (dec_ms * 1e-3) / 1e9
     return {"edits": count, "bytes": nbytes, "bytes_per_edit": round(nbytes / max(count, 1), 4),
             "raw_bytes_per_edit": 8, "ratio_vs_raw": round(8 * count / max(nbytes, 1), 3),
-            "encode_ms": round(enc_ms, 4), "decode_ms": round(dec_ms, 4), "decode_exact": bool(exact)}
+            "encode_ms": round(enc_ms, 4), "decode_ms": round(dec_ms, 4), "decode_exact": bool(exact),
+            "roofline": {"bound": "hbm", "unit": "GB/s", "peak": peak, "peak_kind": kind,
+                         "encode": {"algorithmic_bytes": enc_b, "achieved": round(enc_gbs, 1),
+                                    "frac": round(enc_gbs / peak, 4)},
+                         "decode_with_fhat_copy": {"algorithmic_bytes": dec_b, "achieved": round(dec_gbs, 1),
+                                                   "frac": round(dec_gbs / peak, 4)}}}
 
 
 def conv_flops_per_voxel(cin: int, cout: int) -> int:

@@ -125,7 +125,7 @@ typedef struct {
     int64_t codes_ns;         /* ... of its first phase: the codes of f and their certification
                                  (3D grids: with sweep 0's detection, done in the same pass) */
     int64_t uncertified;      /* vertices sweep 0 could not certify (only these can ever be
-                                 distorted); 0 in msz_correct_batch results */
+                                 distorted) */
     int64_t local_sweeps;     /* msz_correct_relaxed: local sweeps summed over tile runs */
     int64_t tile_runs;        /* msz_correct_relaxed: tile runs summed over iterations */
 } msz_stats;

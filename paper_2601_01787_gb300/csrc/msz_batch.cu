@@ -55,7 +55,7 @@ struct BatchRec {
 struct FieldRes {
     unsigned long long edit_count;
     uint32_t error;
-    uint32_t pad;
+    uint32_t uncertified;  // vertices the code pass could not certify
 };
 
 struct BatchProblem {
@@ -311,19 +311,28 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
     const uint32_t w0 = min(blockIdx.x * per, W), w1 = min(w0 + per, W);
     uint32_t cnt = 0;
     for (uint32_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) {
-        const uint32_t c = __popc(P.eb[w]);
+        const uint32_t c = __popc(P.eb[w]), u = __popc(P.ub[w]);
         cnt += c;
-        if (c) atomicAdd(&s_cnt[field_of(P.bfield, w * 32u)][0], c);
+        if (c | u) {
+            const uint32_t f = field_of(P.bfield, w * 32u);
+            if (c) atomicAdd(&s_cnt[f][0], c);
+            if (u) atomicAdd(&s_cnt[f][1], u);
+        }
     }
     uint32_t tot;
     block_exclusive_scan(cnt, sm, tot);
     if (threadIdx.x == 0) P.bsum[blockIdx.x] = tot;
     __syncthreads();
-    for (uint32_t f = threadIdx.x; f < nf; f += blockDim.x)
+    for (uint32_t f = threadIdx.x; f < nf; f += blockDim.x) {
         if (s_cnt[f][0]) {
             atomicAdd(&P.res[f].edit_count, (unsigned long long)s_cnt[f][0]);
             s_cnt[f][0] = 0;
         }
+        if (s_cnt[f][1]) {
+            atomicAdd(&P.res[f].uncertified, s_cnt[f][1]);
+            s_cnt[f][1] = 0;
+        }
+    }
     if (!grid_barrier(&C->bar_count, &C->bar_gen, &C->error)) return;
     uint32_t pre = 0;
     for (uint32_t b = threadIdx.x; b < blockIdx.x; b += blockDim.x) pre += ld_relaxed(&P.bsum[b]);
@@ -634,6 +643,7 @@ extern "C" msz_status msz_batch_collect(const msz_batch_plan *plan, msz_field *f
         }
         F.edit_count = (int64_t)res[k].edit_count;
         stt.edited = F.edit_count;
+        stt.uncertified = res[k].uncertified;
         if (fs == MSZ_OK && F.edit_count > F.edit_capacity) fs = MSZ_ERR_CAPACITY;
         F.status = fs;
     }
