@@ -97,7 +97,7 @@ def test_full_uneven_batch_matches_single_corrections(api):
         assert r.status == one.status == api.OK
         assert torch.equal(r.out.view(torch.int32), one.out.view(torch.int32))
         assert torch.equal(r.edit_idx, one.edit_idx)
-        for key in ("sweeps", "edits", "edited", "first_distorted"):
+        for key in ("sweeps", "edits", "edited", "first_distorted", "uncertified"):
             assert r.stats[key] == one.stats[key], key
         v = api.verify(f, r.out)
         assert v["codes_equal"] and v["wrong_labels"] == 0
