@@ -342,10 +342,40 @@ def run_ours(args, ws, rank, local):
     t0 = time.perf_counter()
     hr = run_pipeline(e2e_steps)
     torch.cuda.synchronize()
-    e2e_ms = max_over_ranks((time.perf_counter() - t0) / e2e_steps * 1e3, ws)
-    e2e_value = ws * n / (e2e_ms * 1e-3) / 1e9
+    field_ms = max_over_ranks((time.perf_counter() - t0) / e2e_steps * 1e3, ws)
     assert hr.edit_count == first.edit_count
     pl.close()
+    del pl
+
+    # ... and through the encoded pipeline: each step's result is the edit
+    # list's stream (what a compressor stores beside its data), encoded on
+    # the device, instead of g
+    ple = api.Pipeline(fl.shape, edit_capacity=cap, device=dev, encoded=True)
+    sbufs = [torch.empty(ple.stream_bound(), dtype=torch.uint8).pin_memory() for _ in range(2)]
+
+    def run_encoded(steps):
+        last = None
+        for i in range(steps):
+            if i >= 2:
+                last = ple.collect()
+                assert last.status == api.OK, api.status_str(last.status)
+            ple.submit(hf, hfh, fl.xi, sbufs[i % 2])
+        for _ in range(min(steps, 2)):
+            last = ple.collect()
+            assert last.status == api.OK, api.status_str(last.status)
+        return last
+
+    run_encoded(3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    he = run_encoded(e2e_steps)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) / e2e_steps * 1e3, ws)
+    e2e_value = ws * n / (e2e_ms * 1e-3) / 1e9
+    assert he.edit_count == first.edit_count
+    stream_len = int(he.stream.numel())
+    ple.close()
+    del ple, sbufs
 
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -369,9 +399,14 @@ def run_ours(args, ws, rank, local):
                   "snap": {"ms": round(snap_ms, 4), "sweeps": snap.stats["sweeps"], "edits": snap.stats["edits"],
                            "edited": snap.edit_count, "status": api.status_str(snap.status)}},
         "e2e": {"value": round(e2e_value, 4), "unit": UNIT, "h2d_bytes_per_step": 8 * n,
-                "d2h_bytes_per_step": 4 * n + 8 * hr.edit_count, "ms_per_step": round(e2e_ms, 4),
-                "api": "msz_pipeline_submit / msz_pipeline_collect (consecutive steps overlapped)",
-                "serial": {"api": "msz_correct_host (one call at a time)", "ms_per_step": round(serial_ms, 4),
+                "d2h_bytes_per_step": stream_len, "ms_per_step": round(e2e_ms, 4),
+                "api": "msz_pipeline_submit_encoded / msz_pipeline_collect_encoded (consecutive steps "
+                       "overlapped; result: the edit list's stream)",
+                "field": {"api": "msz_pipeline_submit / msz_pipeline_collect (result: g and the edit list)",
+                          "ms_per_step": round(field_ms, 4), "value": round(ws * n / (field_ms * 1e-3) / 1e9, 4),
+                          "d2h_bytes_per_step": 4 * n + 8 * hr.edit_count},
+                "serial": {"api": "msz_correct_host (one call at a time; result: g and the edit list)",
+                           "ms_per_step": round(serial_ms, 4),
                            "value": round(ws * n / (serial_ms * 1e-3) / 1e9, 4)}},
         "gpu_launches": args.steps,
         "clocks": clk,

@@ -207,6 +207,27 @@ msz_status msz_pipeline_collect(msz_pipeline *pl, int64_t *h_edit_count, msz_sta
  * memory (not the workspace). */
 void msz_pipeline_destroy(msz_pipeline *pl);
 
+/* The same pipeline returning, per field, the edit list as a stream in the
+ * msz_edits_encode format instead of g and the list: what a compressor
+ * stores beside its compressed data (g = fhat with the stream applied, see
+ * msz_edits_decode).  The stream is encoded on the device behind the
+ * correction and only its bytes come down.  Workspace:
+ * msz_pipeline_workspace_size_encoded bytes (the two slots plus a stream
+ * buffer of msz_edits_encoded_bound(edit_capacity) bytes and its encoder's
+ * workspace each).  submit_encoded: h_stream (stream_capacity bytes) must
+ * stay valid until the field is collected.  collect_encoded: *h_stream_bytes
+ * = the stream's length; MSZ_ERR_CAPACITY when the edits exceed the
+ * pipeline's edit capacity or the stream exceeds stream_capacity (then
+ * *h_stream_bytes = the length needed, nothing copied).  The field-mode
+ * calls reject an encoded pipeline and the other way round. */
+size_t msz_pipeline_workspace_size_encoded(msz_grid grid, int64_t edit_capacity);
+msz_status msz_pipeline_create_encoded(msz_grid grid, int64_t edit_capacity, void *d_workspace,
+                                       size_t workspace_bytes, msz_pipeline **out);
+msz_status msz_pipeline_submit_encoded(msz_pipeline *pl, const float *h_f, const float *h_fhat, float xi,
+                                       uint8_t *h_stream, size_t stream_capacity, const msz_options *opt);
+msz_status msz_pipeline_collect_encoded(msz_pipeline *pl, int64_t *h_edit_count, size_t *h_stream_bytes,
+                                        msz_stats *h_stats);
+
 /* Sec. III-A ascending/descending segmentations, for verification:
  * d_max_label[i] = index of the maximum reached by following n_max (the low
  * nibble of d_codes) from i; d_min_label[i] likewise through n_min.  Computed

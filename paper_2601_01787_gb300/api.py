@@ -137,6 +137,14 @@ def load(build_if_missing: bool = True):
         lib.msz_pipeline_collect.restype = st
         lib.msz_pipeline_destroy.argtypes = [P]
         lib.msz_pipeline_destroy.restype = None
+        lib.msz_pipeline_workspace_size_encoded.argtypes = [Grid, I64]
+        lib.msz_pipeline_workspace_size_encoded.restype = SZ
+        lib.msz_pipeline_create_encoded.argtypes = [Grid, I64, P, SZ, ctypes.POINTER(P)]
+        lib.msz_pipeline_create_encoded.restype = st
+        lib.msz_pipeline_submit_encoded.argtypes = [P, P, P, ctypes.c_float, P, SZ, ctypes.POINTER(Options)]
+        lib.msz_pipeline_submit_encoded.restype = st
+        lib.msz_pipeline_collect_encoded.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(SZ), ctypes.POINTER(Stats)]
+        lib.msz_pipeline_collect_encoded.restype = st
         lib.msz_status_str.argtypes = [st]
         lib.msz_status_str.restype = ctypes.c_char_p
         _lib = lib
@@ -347,47 +355,84 @@ def _host_ptr(a):
     return a.ctypes.data
 
 
+@dataclass
+class EncodedResult:
+    status: int
+    stream: object  # the host buffer, cut to the stream's length
+    edit_count: int
+    stats: dict
+
+
 class Pipeline:
     """msz_pipeline_*: a sequence of fields of one shape corrected from host
     buffers with the copies of consecutive fields overlapped.  submit()
     returns at once (at most two fields in flight); collect() returns the
-    oldest field's CorrectResult once its g and edit list are in its host
-    buffers.  Pinned host buffers (torch pin_memory) let the copies overlap."""
+    oldest field's result once it is in its host buffers: a CorrectResult (g
+    and the edit list), or with encoded=True an EncodedResult holding the edit
+    list's stream (msz_edits_encode format) instead.  Pinned host buffers
+    (torch pin_memory) let the copies overlap."""
 
-    def __init__(self, shape, edit_capacity: int | None = None, device=None):
+    def __init__(self, shape, edit_capacity: int | None = None, device=None, encoded: bool = False):
         lib = load()
         self.shape = tuple(int(v) for v in shape)
         self.n = int(np.prod(self.shape))
         self.cap = self.n if edit_capacity is None else int(edit_capacity)
+        self.encoded = bool(encoded)
         g = grid_of(self.shape)
-        need = int(lib.msz_pipeline_workspace_size(g, self.cap))
+        size = lib.msz_pipeline_workspace_size_encoded if encoded else lib.msz_pipeline_workspace_size
+        need = int(size(g, self.cap))
         dev = torch.device("cuda", torch.cuda.current_device() if device is None else torch.device(device).index)
         self.ws = torch.empty(need, dtype=torch.uint8, device=dev)  # owned: the pipeline's two slots
         h = ctypes.c_void_p()
-        st = lib.msz_pipeline_create(g, self.cap, _dptr(self.ws), self.ws.numel(), ctypes.byref(h))
+        create = lib.msz_pipeline_create_encoded if encoded else lib.msz_pipeline_create
+        st = create(g, self.cap, _dptr(self.ws), self.ws.numel(), ctypes.byref(h))
         if st != OK:
             raise MszError(st, "msz_pipeline_create")
         self._h = h
         self._fifo = []
 
+    def stream_bound(self) -> int:
+        """Bytes a host stream buffer needs for any field (encoded pipelines)."""
+        return int(load().msz_edits_encoded_bound(self.cap))
+
     def submit(self, f, fhat, xi: float, out, edit_idx=None, edit_delta=None, *, rule="halve",
                max_sweeps: int = 0, dense_min_items: int = 0):
+        """One field; `out` is g's host buffer, or for an encoded pipeline the
+        stream's host buffer (uint8, stream_bound() bytes suffice)."""
+        opt, _ = _options(rule, max_sweeps, dense_min_items, None, 0)
+        lib = load()
+        if self.encoded:
+            nbytes = out.numel() if isinstance(out, torch.Tensor) else out.nbytes
+            st = lib.msz_pipeline_submit_encoded(self._h, _host_ptr(f), _host_ptr(fhat),
+                                                 ctypes.c_float(np.float32(xi)), _host_ptr(out), nbytes,
+                                                 ctypes.byref(opt))
+            if st != OK:
+                raise MszError(st, "msz_pipeline_submit_encoded")
+            self._fifo.append((out,))
+            return
         if edit_idx is None:
             edit_idx = np.empty(max(self.cap, 1), dtype=np.uint32)
         if edit_delta is None:
             edit_delta = np.empty(max(self.cap, 1), dtype=np.float32)
-        opt, _ = _options(rule, max_sweeps, dense_min_items, None, 0)
-        st = load().msz_pipeline_submit(self._h, _host_ptr(f), _host_ptr(fhat), ctypes.c_float(np.float32(xi)),
-                                        _host_ptr(out), _host_ptr(edit_idx), _host_ptr(edit_delta),
-                                        ctypes.byref(opt))
+        st = lib.msz_pipeline_submit(self._h, _host_ptr(f), _host_ptr(fhat), ctypes.c_float(np.float32(xi)),
+                                     _host_ptr(out), _host_ptr(edit_idx), _host_ptr(edit_delta), ctypes.byref(opt))
         if st != OK:
             raise MszError(st, "msz_pipeline_submit")
         self._fifo.append((out, edit_idx, edit_delta))
 
-    def collect(self) -> CorrectResult:
+    def collect(self):
         stats = Stats()
         count = ctypes.c_int64()
-        st = load().msz_pipeline_collect(self._h, ctypes.byref(count), ctypes.byref(stats))
+        lib = load()
+        if self.encoded:
+            nbytes = ctypes.c_size_t(0)
+            st = lib.msz_pipeline_collect_encoded(self._h, ctypes.byref(count), ctypes.byref(nbytes),
+                                                  ctypes.byref(stats))
+            if not self._fifo:
+                raise MszError(st, "msz_pipeline_collect_encoded")
+            (buf,) = self._fifo.pop(0)
+            return EncodedResult(int(st), buf[:nbytes.value], int(count.value), stats.as_dict())
+        st = lib.msz_pipeline_collect(self._h, ctypes.byref(count), ctypes.byref(stats))
         if not self._fifo:
             raise MszError(st, "msz_pipeline_collect")
         out, idx, dl = self._fifo.pop(0)

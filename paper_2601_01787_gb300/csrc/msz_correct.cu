@@ -28,6 +28,7 @@
 
 #include "msz.h"
 #include "msz_device.cuh"
+#include "msz_edits_async.h"
 #include "msz_phases.cuh"
 #include "msz_tile.cuh"
 #include "msz_workspace.h"
@@ -604,16 +605,18 @@ extern "C" msz_status msz_correct_host(const float *h_f, const float *h_fhat, fl
 }
 
 // ------------------------------------------------------------ pipeline
-// Two slots of device buffers (f, fhat, g, edit list, correction workspace)
-// and three streams: inputs up, correction, result down.  Field k+1's
-// inputs go up while field k is corrected and field k-1's result comes down;
-// events order each slot's reuse.
+// Two slots of device buffers (f, fhat, g, edit list, correction workspace,
+// and for an encoded pipeline the edit-list stream and its workspace) and
+// three streams: inputs up, correction, result down.  Field k+1's inputs go
+// up while field k is corrected and field k-1's result comes down; events
+// order each slot's reuse.
 struct msz_pipeline {
     msz_grid grid;
     GridDev G;
     int64_t cap;
+    bool encoded;  // results: the edit list's stream (msz_edits_encode format) instead of g
     char *ws;
-    size_t slot_bytes, fld, capb, base;
+    size_t slot_bytes, fld, capb, base, stream_cap;
     cudaStream_t s_in, s_comp, s_out;
     struct Slot {
         cudaEvent_t in_done, comp_done, out_done;
@@ -621,34 +624,39 @@ struct msz_pipeline {
         float *h_out;
         uint32_t *h_idx;
         float *h_del;
+        uint8_t *h_stream;
+        size_t h_stream_cap;
         Problem P;
-        msz_status prep;
     } slot[2];
-    msz::Ctrl *h_ctrl;    // pinned: the control block and sweep-0 record of each slot
+    struct EncCtrl {
+        uint32_t error, pad;
+        unsigned long long total_words;
+    };
+    msz::Ctrl *h_ctrl;  // pinned: the control block, sweep-0 record and encoder state of each slot
     msz::SweepRec *h_rec;
+    EncCtrl *h_enc;
     int head, tail, pending;
 };
 
 namespace msz {
-static size_t pipeline_slot_bytes(const GridDev &G, int64_t cap) {
-    return layout_for(G.n).total + 3 * align_up((size_t)G.n * 4) + 2 * align_up((size_t)cap * 4);
+// Bytes of one slot: correction workspace, f, fhat, g, the edit list, and
+// when encoded the stream and its workspace.
+static size_t pipeline_slot_bytes(const GridDev &G, int64_t cap, bool encoded, size_t *stream_cap = nullptr) {
+    size_t b = layout_for(G.n).total + 3 * align_up((size_t)G.n * 4) + 2 * align_up((size_t)cap * 4);
+    const size_t sc = encoded ? align_up(msz_edits_encoded_bound(cap)) : 0;
+    if (stream_cap) *stream_cap = sc;
+    if (encoded) b += sc + align_up(encode_async_workspace((uint64_t)cap));
+    return b;
 }
-}  // namespace msz
 
-extern "C" size_t msz_pipeline_workspace_size(msz_grid grid, int64_t edit_capacity) {
-    GridDev G;
-    if (make_grid(grid, G) != MSZ_OK || edit_capacity < 0) return 0;
-    return 2 * pipeline_slot_bytes(G, edit_capacity);
-}
-
-extern "C" msz_status msz_pipeline_create(msz_grid grid, int64_t edit_capacity, void *d_workspace,
-                                          size_t workspace_bytes, msz_pipeline **out) {
+static msz_status pipeline_create(msz_grid grid, int64_t edit_capacity, bool encoded, void *d_workspace,
+                                  size_t workspace_bytes, msz_pipeline **out) {
     if (!out || edit_capacity < 0) return MSZ_ERR_INVALID_ARG;
     *out = nullptr;
     GridDev G;
     msz_status st = make_grid(grid, G);
     if (st != MSZ_OK) return st;
-    const size_t need = 2 * pipeline_slot_bytes(G, edit_capacity);
+    const size_t need = 2 * pipeline_slot_bytes(G, edit_capacity, encoded);
     if (!d_workspace || workspace_bytes < need) return MSZ_ERR_WORKSPACE;
     if ((uintptr_t)d_workspace % kAlign) return MSZ_ERR_INVALID_ARG;
     DeviceInfo dev;
@@ -657,8 +665,9 @@ extern "C" msz_status msz_pipeline_create(msz_grid grid, int64_t edit_capacity, 
     pl->grid = grid;
     pl->G = G;
     pl->cap = edit_capacity;
+    pl->encoded = encoded;
     pl->ws = (char *)d_workspace;
-    pl->slot_bytes = pipeline_slot_bytes(G, edit_capacity);
+    pl->slot_bytes = pipeline_slot_bytes(G, edit_capacity, encoded, &pl->stream_cap);
     pl->base = layout_for(G.n).total;
     pl->fld = align_up((size_t)G.n * 4);
     pl->capb = align_up((size_t)edit_capacity * 4);
@@ -666,7 +675,9 @@ extern "C" msz_status msz_pipeline_create(msz_grid grid, int64_t edit_capacity, 
               cudaStreamCreateWithFlags(&pl->s_comp, cudaStreamNonBlocking) == cudaSuccess &&
               cudaStreamCreateWithFlags(&pl->s_out, cudaStreamNonBlocking) == cudaSuccess &&
               cudaHostAlloc((void **)&pl->h_ctrl, 2 * sizeof(Ctrl), cudaHostAllocDefault) == cudaSuccess &&
-              cudaHostAlloc((void **)&pl->h_rec, 2 * sizeof(SweepRec), cudaHostAllocDefault) == cudaSuccess;
+              cudaHostAlloc((void **)&pl->h_rec, 2 * sizeof(SweepRec), cudaHostAllocDefault) == cudaSuccess &&
+              cudaHostAlloc((void **)&pl->h_enc, 2 * sizeof(msz_pipeline::EncCtrl), cudaHostAllocDefault) ==
+                  cudaSuccess;
     for (int k = 0; ok && k < 2; ++k)
         ok = cudaEventCreateWithFlags(&pl->slot[k].in_done, cudaEventDisableTiming) == cudaSuccess &&
              cudaEventCreateWithFlags(&pl->slot[k].comp_done, cudaEventDisableTiming) == cudaSuccess &&
@@ -679,31 +690,49 @@ extern "C" msz_status msz_pipeline_create(msz_grid grid, int64_t edit_capacity, 
     return MSZ_OK;
 }
 
-extern "C" msz_status msz_pipeline_submit(msz_pipeline *pl, const float *h_f, const float *h_fhat, float xi,
-                                          float *h_out, uint32_t *h_edit_idx, float *h_edit_delta,
-                                          const msz_options *opt) {
-    if (!pl || !h_f || !h_fhat || !h_out) return MSZ_ERR_INVALID_ARG;
-    if (pl->cap > 0 && (!h_edit_idx || !h_edit_delta)) return MSZ_ERR_INVALID_ARG;
+// The device buffers of slot k.
+struct SlotBufs {
+    float *f, *fhat, *g;
+    uint32_t *idx;
+    float *del;
+    uint8_t *stream;
+    void *enc_ws;
+};
+static SlotBufs slot_bufs(const msz_pipeline *pl, int k) {
+    char *w = pl->ws + (size_t)k * pl->slot_bytes;
+    SlotBufs b;
+    b.f = (float *)(w + pl->base);
+    b.fhat = (float *)(w + pl->base + pl->fld);
+    b.g = (float *)(w + pl->base + 2 * pl->fld);
+    b.idx = (uint32_t *)(w + pl->base + 3 * pl->fld);
+    b.del = (float *)(w + pl->base + 3 * pl->fld + pl->capb);
+    b.stream = (uint8_t *)(w + pl->base + 3 * pl->fld + 2 * pl->capb);
+    b.enc_ws = (void *)(w + pl->base + 3 * pl->fld + 2 * pl->capb + pl->stream_cap);
+    return b;
+}
+
+// Queues one field into the head slot: inputs up, the correction (and, when
+// encoded, the edit list's stream), the result down.
+static msz_status pipeline_submit(msz_pipeline *pl, const float *h_f, const float *h_fhat, float xi, float *h_out,
+                                  uint32_t *h_idx, float *h_del, uint8_t *h_stream, size_t h_stream_cap,
+                                  const msz_options *opt) {
     if (pl->pending == 2) return MSZ_ERR_INVALID_ARG;  // collect the oldest field first
     if (opt && (opt->d_g_init || opt->h_sweep_log || opt->log_capacity || opt->test_fault)) return MSZ_ERR_INVALID_ARG;
     const int k = pl->head;
     msz_pipeline::Slot &sl = pl->slot[k];
+    const SlotBufs b = slot_bufs(pl, k);
     char *w = pl->ws + (size_t)k * pl->slot_bytes;
-    float *d_f = (float *)(w + pl->base), *d_fhat = (float *)(w + pl->base + pl->fld);
-    float *d_out = (float *)(w + pl->base + 2 * pl->fld);
-    uint32_t *d_idx = (uint32_t *)(w + pl->base + 3 * pl->fld);
-    float *d_del = (float *)(w + pl->base + 3 * pl->fld + pl->capb);
     msz_options o;
-    msz_status st = prepare_correct(d_f, d_fhat, xi, pl->grid, d_out, pl->cap ? d_idx : nullptr,
-                                    pl->cap ? d_del : nullptr, pl->cap, opt, w, pl->base, sl.P, o);
+    msz_status st = prepare_correct(b.f, b.fhat, xi, pl->grid, b.g, pl->cap ? b.idx : nullptr,
+                                    pl->cap ? b.del : nullptr, pl->cap, opt, w, pl->base, sl.P, o);
     if (st != MSZ_OK) return st;
     DeviceInfo dev;
     if ((st = current_device(dev)) != MSZ_OK) return st;
     const size_t bytes = (size_t)pl->G.n * 4;
     // inputs up, once the slot's previous correction has read its inputs
     if (sl.used && cudaStreamWaitEvent(pl->s_in, sl.comp_done, 0) != cudaSuccess) return MSZ_ERR_CUDA;
-    if (cudaMemcpyAsync(d_f, h_f, bytes, cudaMemcpyHostToDevice, pl->s_in) != cudaSuccess ||
-        cudaMemcpyAsync(d_fhat, h_fhat, bytes, cudaMemcpyHostToDevice, pl->s_in) != cudaSuccess ||
+    if (cudaMemcpyAsync(b.f, h_f, bytes, cudaMemcpyHostToDevice, pl->s_in) != cudaSuccess ||
+        cudaMemcpyAsync(b.fhat, h_fhat, bytes, cudaMemcpyHostToDevice, pl->s_in) != cudaSuccess ||
         cudaEventRecord(sl.in_done, pl->s_in) != cudaSuccess)
         return MSZ_ERR_CUDA;
     // the correction, once the inputs are up and the slot's previous result
@@ -711,27 +740,40 @@ extern "C" msz_status msz_pipeline_submit(msz_pipeline *pl, const float *h_f, co
     if (cudaStreamWaitEvent(pl->s_comp, sl.in_done, 0) != cudaSuccess) return MSZ_ERR_CUDA;
     if (sl.used && cudaStreamWaitEvent(pl->s_comp, sl.out_done, 0) != cudaSuccess) return MSZ_ERR_CUDA;
     if ((st = enqueue_correct(sl.P, dev, pl->s_comp)) != MSZ_OK) return st;
+    if (pl->encoded) {
+        st = encode_async(b.fhat, b.g, pl->G.n, b.idx, &sl.P.ctrl->edit_count, (uint64_t)pl->cap, b.stream,
+                          pl->stream_cap, b.enc_ws, dev, pl->s_comp);
+        if (st != MSZ_OK) return st;
+        if (cudaMemcpyAsync(&pl->h_enc[k], b.enc_ws, sizeof(msz_pipeline::EncCtrl), cudaMemcpyDeviceToHost,
+                            pl->s_comp) != cudaSuccess)
+            return MSZ_ERR_CUDA;
+    }
     if (cudaMemcpyAsync(&pl->h_ctrl[k], sl.P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, pl->s_comp) != cudaSuccess ||
         cudaMemcpyAsync(&pl->h_rec[k], sl.P.log, sizeof(SweepRec), cudaMemcpyDeviceToHost, pl->s_comp) !=
             cudaSuccess ||
         cudaEventRecord(sl.comp_done, pl->s_comp) != cudaSuccess)
         return MSZ_ERR_CUDA;
-    // the corrected field down
-    if (cudaStreamWaitEvent(pl->s_out, sl.comp_done, 0) != cudaSuccess ||
-        cudaMemcpyAsync(h_out, d_out, bytes, cudaMemcpyDeviceToHost, pl->s_out) != cudaSuccess ||
-        cudaEventRecord(sl.out_done, pl->s_out) != cudaSuccess)
+    // the corrected field down (an encoded pipeline's stream comes down at
+    // collect, when its length is known)
+    if (cudaStreamWaitEvent(pl->s_out, sl.comp_done, 0) != cudaSuccess) return MSZ_ERR_CUDA;
+    if (!pl->encoded && cudaMemcpyAsync(h_out, b.g, bytes, cudaMemcpyDeviceToHost, pl->s_out) != cudaSuccess)
         return MSZ_ERR_CUDA;
+    if (cudaEventRecord(sl.out_done, pl->s_out) != cudaSuccess) return MSZ_ERR_CUDA;
     sl.used = true;
     sl.h_out = h_out;
-    sl.h_idx = h_edit_idx;
-    sl.h_del = h_edit_delta;
+    sl.h_idx = h_idx;
+    sl.h_del = h_del;
+    sl.h_stream = h_stream;
+    sl.h_stream_cap = h_stream_cap;
     pl->head ^= 1;
     pl->pending += 1;
     return MSZ_OK;
 }
 
-extern "C" msz_status msz_pipeline_collect(msz_pipeline *pl, int64_t *h_edit_count, msz_stats *h_stats) {
-    if (!pl || !h_edit_count) return MSZ_ERR_INVALID_ARG;
+// Waits for the oldest field: its status, edit count, stats and (encoded)
+// stream length; its host results are complete on return.
+static msz_status pipeline_collect(msz_pipeline *pl, int64_t *h_edit_count, size_t *h_stream_bytes,
+                                   msz_stats *h_stats) {
     if (pl->pending == 0) return MSZ_ERR_INVALID_ARG;
     const int k = pl->tail;
     msz_pipeline::Slot &sl = pl->slot[k];
@@ -739,21 +781,86 @@ extern "C" msz_status msz_pipeline_collect(msz_pipeline *pl, int64_t *h_edit_cou
     pl->pending -= 1;
     if (cudaEventSynchronize(sl.comp_done) != cudaSuccess) return MSZ_ERR_CUDA;
     int64_t count = 0;
-    const msz_status st = finish_correct(pl->h_ctrl[k], pl->h_rec[k], pl->cap, &count, h_stats);
+    msz_status st = finish_correct(pl->h_ctrl[k], pl->h_rec[k], pl->cap, &count, h_stats);
     *h_edit_count = count;
-    const int64_t ne = count < pl->cap ? count : pl->cap;
-    if (ne > 0 && st != MSZ_ERR_INPUT_BOUND && st != MSZ_ERR_TIMEOUT) {
-        // the edit list down, behind the field (its length is known now)
-        char *w = pl->ws + (size_t)k * pl->slot_bytes;
-        const uint32_t *d_idx = (const uint32_t *)(w + pl->base + 3 * pl->fld);
-        const float *d_del = (const float *)(w + pl->base + 3 * pl->fld + pl->capb);
-        if (cudaMemcpyAsync(sl.h_idx, d_idx, (size_t)ne * 4, cudaMemcpyDeviceToHost, pl->s_out) != cudaSuccess ||
-            cudaMemcpyAsync(sl.h_del, d_del, (size_t)ne * 4, cudaMemcpyDeviceToHost, pl->s_out) != cudaSuccess ||
-            cudaEventRecord(sl.out_done, pl->s_out) != cudaSuccess)
-            return MSZ_ERR_CUDA;
+    const bool listed = st != MSZ_ERR_INPUT_BOUND && st != MSZ_ERR_TIMEOUT;
+    const SlotBufs b = slot_bufs(pl, k);
+    if (pl->encoded) {
+        if (h_stream_bytes) *h_stream_bytes = 0;
+        if (listed && st != MSZ_ERR_CAPACITY) {
+            const msz_pipeline::EncCtrl e = pl->h_enc[k];
+            const uint64_t len = encoded_length((uint64_t)count, e.total_words);
+            if (h_stream_bytes) *h_stream_bytes = (size_t)len;
+            if (e.error & 1u) return MSZ_ERR_INVALID_ARG;  // not expected: the loop lists edits in order
+            if (e.error || len > sl.h_stream_cap) {
+                st = MSZ_ERR_CAPACITY;
+            } else if (cudaMemcpyAsync(sl.h_stream, b.stream, (size_t)len, cudaMemcpyDeviceToHost, pl->s_out) !=
+                           cudaSuccess ||
+                       cudaEventRecord(sl.out_done, pl->s_out) != cudaSuccess) {
+                return MSZ_ERR_CUDA;
+            }
+        }
+    } else {
+        const int64_t ne = count < pl->cap ? count : pl->cap;
+        if (ne > 0 && listed) {
+            // the edit list down, behind the field (its length is known now)
+            if (cudaMemcpyAsync(sl.h_idx, b.idx, (size_t)ne * 4, cudaMemcpyDeviceToHost, pl->s_out) != cudaSuccess ||
+                cudaMemcpyAsync(sl.h_del, b.del, (size_t)ne * 4, cudaMemcpyDeviceToHost, pl->s_out) != cudaSuccess ||
+                cudaEventRecord(sl.out_done, pl->s_out) != cudaSuccess)
+                return MSZ_ERR_CUDA;
+        }
     }
     if (cudaEventSynchronize(sl.out_done) != cudaSuccess) return MSZ_ERR_CUDA;
     return st;
+}
+}  // namespace msz
+
+extern "C" size_t msz_pipeline_workspace_size(msz_grid grid, int64_t edit_capacity) {
+    GridDev G;
+    if (make_grid(grid, G) != MSZ_OK || edit_capacity < 0) return 0;
+    return 2 * pipeline_slot_bytes(G, edit_capacity, false);
+}
+
+extern "C" size_t msz_pipeline_workspace_size_encoded(msz_grid grid, int64_t edit_capacity) {
+    GridDev G;
+    if (make_grid(grid, G) != MSZ_OK || edit_capacity < 0) return 0;
+    return 2 * pipeline_slot_bytes(G, edit_capacity, true);
+}
+
+extern "C" msz_status msz_pipeline_create(msz_grid grid, int64_t edit_capacity, void *d_workspace,
+                                          size_t workspace_bytes, msz_pipeline **out) {
+    return pipeline_create(grid, edit_capacity, false, d_workspace, workspace_bytes, out);
+}
+
+extern "C" msz_status msz_pipeline_create_encoded(msz_grid grid, int64_t edit_capacity, void *d_workspace,
+                                                  size_t workspace_bytes, msz_pipeline **out) {
+    return pipeline_create(grid, edit_capacity, true, d_workspace, workspace_bytes, out);
+}
+
+extern "C" msz_status msz_pipeline_submit(msz_pipeline *pl, const float *h_f, const float *h_fhat, float xi,
+                                          float *h_out, uint32_t *h_edit_idx, float *h_edit_delta,
+                                          const msz_options *opt) {
+    if (!pl || pl->encoded || !h_f || !h_fhat || !h_out) return MSZ_ERR_INVALID_ARG;
+    if (pl->cap > 0 && (!h_edit_idx || !h_edit_delta)) return MSZ_ERR_INVALID_ARG;
+    return pipeline_submit(pl, h_f, h_fhat, xi, h_out, h_edit_idx, h_edit_delta, nullptr, 0, opt);
+}
+
+extern "C" msz_status msz_pipeline_submit_encoded(msz_pipeline *pl, const float *h_f, const float *h_fhat, float xi,
+                                                  uint8_t *h_stream, size_t stream_capacity,
+                                                  const msz_options *opt) {
+    if (!pl || !pl->encoded || !h_f || !h_fhat || !h_stream) return MSZ_ERR_INVALID_ARG;
+    return pipeline_submit(pl, h_f, h_fhat, xi, nullptr, nullptr, nullptr, h_stream, stream_capacity, opt);
+}
+
+extern "C" msz_status msz_pipeline_collect(msz_pipeline *pl, int64_t *h_edit_count, msz_stats *h_stats) {
+    if (!pl || pl->encoded || !h_edit_count) return MSZ_ERR_INVALID_ARG;
+    return pipeline_collect(pl, h_edit_count, nullptr, h_stats);
+}
+
+extern "C" msz_status msz_pipeline_collect_encoded(msz_pipeline *pl, int64_t *h_edit_count, size_t *h_stream_bytes,
+                                                   msz_stats *h_stats) {
+    if (!pl || !pl->encoded || !h_edit_count || !h_stream_bytes) return MSZ_ERR_INVALID_ARG;
+    return pipeline_collect(pl, h_edit_count, h_stream_bytes, h_stats);
 }
 
 extern "C" void msz_pipeline_destroy(msz_pipeline *pl) {
@@ -771,6 +878,7 @@ extern "C" void msz_pipeline_destroy(msz_pipeline *pl) {
     if (pl->s_out) cudaStreamDestroy(pl->s_out);
     if (pl->h_ctrl) cudaFreeHost(pl->h_ctrl);
     if (pl->h_rec) cudaFreeHost(pl->h_rec);
+    if (pl->h_enc) cudaFreeHost(pl->h_enc);
     delete pl;
 }
 

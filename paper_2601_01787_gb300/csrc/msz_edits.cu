@@ -25,12 +25,21 @@ constexpr uint32_t B = MSZ_EDIT_BLOCK;
 constexpr uint32_t PER_LANE = B / 32;  // 8 edits per lane, contiguous
 constexpr int kWarps = 8;              // warps (blocks of the stream) per thread block
 constexpr uint32_t kErrArg = 1u;
+constexpr uint32_t kErrCap = 2u;  // the stream would exceed the output buffer (nothing written)
 
 struct Ctrl {
     uint32_t error;
     uint32_t pad;
     unsigned long long total_words;
 };
+
+// The number of edits: count_cap, or, when d_count is given (an encode queued
+// behind the correction that lists them), min(*d_count, count_cap).
+__device__ __forceinline__ uint64_t edit_count(const unsigned long long *d_count, uint64_t count_cap) {
+    if (!d_count) return count_cap;
+    const unsigned long long c = *d_count;
+    return c < count_cap ? c : count_cap;
+}
 
 __device__ __forceinline__ uint32_t ord_key(float v) {
     const uint32_t b = __float_as_uint(v);
@@ -83,9 +92,11 @@ __device__ __forceinline__ uint32_t unpacked(const uint32_t *sec, uint32_t w, ui
 
 // ---- encode 1: per block, gaps and distances, their widths and word count
 __global__ void __launch_bounds__(kWarps * 32) k_widths(const float *fhat, const float *g, uint32_t n,
-                                                        const uint32_t *idx, uint64_t count, uint32_t *words,
-                                                        uint8_t *wd_out, uint8_t *wm_out, Ctrl *C) {
+                                                        const uint32_t *idx, const unsigned long long *d_count,
+                                                        uint64_t count_cap, uint32_t *words, uint8_t *wd_out,
+                                                        uint8_t *wm_out, Ctrl *C) {
     const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t count = edit_count(d_count, count_cap);
     const uint64_t nb = (count + B - 1) / B;
     for (uint64_t k = ((uint64_t)blockIdx.x * kWarps + (threadIdx.x >> 5)); k < nb; k += (uint64_t)gridDim.x * kWarps) {
         const uint64_t base = k * B;
@@ -118,7 +129,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_widths(const float *fhat, const
 
 // ---- encode 2: exclusive scan of the block word counts (one thread block)
 constexpr int kScanThreads = 1024;
-__global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t *words, uint64_t nb, uint32_t *start, Ctrl *C) {
+__global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t *words, const unsigned long long *d_count,
+                                                      uint64_t count_cap, uint32_t *start, Ctrl *C) {
+    const uint64_t nb = (edit_count(d_count, count_cap) + B - 1) / B;
     __shared__ unsigned long long s_warp[kScanThreads / 32];
     __shared__ unsigned long long s_carry;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
@@ -154,12 +167,21 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t *words, ui
 
 // ---- encode 3: header, table and payload
 __global__ void __launch_bounds__(kWarps * 32) k_pack(const float *fhat, const float *g, const uint32_t *idx,
-                                                      uint64_t count, const uint32_t *start, const uint8_t *wd_in,
-                                                      const uint8_t *wm_in, uint8_t *out) {
+                                                      const unsigned long long *d_count, uint64_t count_cap,
+                                                      const uint32_t *start, const uint8_t *wd_in,
+                                                      const uint8_t *wm_in, uint8_t *out, uint64_t capacity,
+                                                      Ctrl *C) {
     __shared__ uint32_t s_d[kWarps][B], s_m[kWarps][B];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint64_t count = edit_count(d_count, count_cap);
     const uint64_t nb = (count + B - 1) / B;
     const Layout L = layout_of(nb);
+    // an error found by the widths pass, or a stream longer than the buffer:
+    // nothing is written
+    if (ld_relaxed(&C->error) || L.payload + 4ull * C->total_words > capacity) {
+        if (blockIdx.x == 0 && threadIdx.x == 0 && !C->error) atomicOr(&C->error, kErrCap);
+        return;
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         uint32_t *h = reinterpret_cast<uint32_t *>(out);
         h[0] = MSZ_EDIT_MAGIC;
@@ -306,6 +328,33 @@ inline int grid_for(const DeviceInfo &dev, uint64_t nb) {
 }
 
 }  // namespace edits
+
+// The encode queued on a stream behind the correction that lists the edits
+// (the pipeline's encoded output): the count is read on the device from
+// d_count (capped at count_cap); no host synchronization.  The workspace's
+// first 16 bytes then hold {error, pad, total_words}: the stream is
+// encoded_length(count, total_words) bytes unless error is set.
+size_t encode_async_workspace(uint64_t count_cap) { return edits::work_bytes(edits::blocks_of((int64_t)count_cap)); }
+
+uint64_t encoded_length(uint64_t count, uint64_t total_words) {
+    return edits::layout_of(edits::blocks_of((int64_t)count)).payload + 4ull * total_words;
+}
+
+msz_status encode_async(const float *d_fhat, const float *d_g, uint32_t n, const uint32_t *d_idx,
+                        const unsigned long long *d_count, uint64_t count_cap, uint8_t *d_stream, size_t capacity,
+                        void *d_ws, const DeviceInfo &dev, cudaStream_t s) {
+    const uint64_t nb = edits::blocks_of((int64_t)count_cap);
+    const edits::Work w = edits::work_of(d_ws, nb);
+    if (cudaMemsetAsync(w.ctrl, 0, sizeof(edits::Ctrl), s) != cudaSuccess) return MSZ_ERR_CUDA;
+    const int grid = edits::grid_for(dev, nb);
+    edits::k_widths<<<grid, edits::kWarps * 32, 0, s>>>(d_fhat, d_g, n, d_idx, d_count, count_cap, w.words, w.wd,
+                                                        w.wm, w.ctrl);
+    edits::k_scan<<<1, edits::kScanThreads, 0, s>>>(w.words, d_count, count_cap, w.start, w.ctrl);
+    edits::k_pack<<<grid, edits::kWarps * 32, 0, s>>>(d_fhat, d_g, d_idx, d_count, count_cap, w.start, w.wd, w.wm,
+                                                      d_stream, capacity, w.ctrl);
+    return cudaGetLastError() == cudaSuccess ? MSZ_OK : MSZ_ERR_CUDA;
+}
+
 }  // namespace msz
 
 using namespace msz;
@@ -338,10 +387,9 @@ extern "C" msz_status msz_edits_encode(const float *d_fhat, const float *d_g, in
     const edits::Layout L = edits::layout_of(nb);
     if (cudaMemsetAsync(w.ctrl, 0, sizeof(edits::Ctrl), s) != cudaSuccess) return MSZ_ERR_CUDA;
     if (nb > 0) {
-        edits::k_widths<<<edits::grid_for(dev, nb), edits::kWarps * 32, 0, s>>>(d_fhat, d_g, (uint32_t)n, d_idx,
-                                                                             (uint64_t)count, w.words, w.wd, w.wm,
-                                                                             w.ctrl);
-        edits::k_scan<<<1, edits::kScanThreads, 0, s>>>(w.words, nb, w.start, w.ctrl);
+        edits::k_widths<<<edits::grid_for(dev, nb), edits::kWarps * 32, 0, s>>>(
+            d_fhat, d_g, (uint32_t)n, d_idx, nullptr, (uint64_t)count, w.words, w.wd, w.wm, w.ctrl);
+        edits::k_scan<<<1, edits::kScanThreads, 0, s>>>(w.words, nullptr, (uint64_t)count, w.start, w.ctrl);
     }
     edits::Ctrl hc;
     if (cudaMemcpyAsync(&hc, w.ctrl, sizeof hc, cudaMemcpyDeviceToHost, s) != cudaSuccess) return MSZ_ERR_CUDA;
@@ -350,8 +398,8 @@ extern "C" msz_status msz_edits_encode(const float *d_fhat, const float *d_g, in
     const uint64_t bytes = L.payload + 4ull * hc.total_words;
     *h_bytes = (size_t)bytes;
     if (bytes > capacity) return MSZ_ERR_CAPACITY;
-    edits::k_pack<<<edits::grid_for(dev, nb), edits::kWarps * 32, 0, s>>>(d_fhat, d_g, d_idx, (uint64_t)count,
-                                                                       w.start, w.wd, w.wm, d_stream);
+    edits::k_pack<<<edits::grid_for(dev, nb), edits::kWarps * 32, 0, s>>>(
+        d_fhat, d_g, d_idx, nullptr, (uint64_t)count, w.start, w.wd, w.wm, d_stream, capacity, w.ctrl);
     if (cudaGetLastError() != cudaSuccess) return MSZ_ERR_CUDA;
     return cuda_status(cudaStreamSynchronize(s));
 }

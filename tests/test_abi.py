@@ -180,3 +180,19 @@ def test_pipeline_arguments_on_host():
     assert lib.msz_pipeline_submit(None, fake, fake, ctypes.c_float(0.1), fake, fake, fake, None) == api.ERR_INVALID_ARG
     assert lib.msz_pipeline_collect(None, ctypes.byref(cnt), None) == api.ERR_INVALID_ARG
     lib.msz_pipeline_destroy(None)  # a no-op
+
+
+def test_encoded_pipeline_arguments_on_host():
+    from paper_2601_01787_gb300 import api
+    lib = api.load()
+    g = api.grid_of((6, 7, 8))
+    assert lib.msz_pipeline_workspace_size_encoded(g, 10) > lib.msz_pipeline_workspace_size(g, 10)
+    assert lib.msz_pipeline_workspace_size_encoded(g, -1) == 0
+    h = ctypes.c_void_p()
+    fake = ctypes.c_void_p(256)
+    assert lib.msz_pipeline_create_encoded(g, 10, fake, 64, ctypes.byref(h)) == api.ERR_WORKSPACE
+    assert lib.msz_pipeline_create_encoded(g, 10, fake, 1 << 30, None) == api.ERR_INVALID_ARG
+    cnt, nb = ctypes.c_int64(), ctypes.c_size_t()
+    assert lib.msz_pipeline_submit_encoded(None, fake, fake, ctypes.c_float(0.1), fake, 64, None) == \
+        api.ERR_INVALID_ARG
+    assert lib.msz_pipeline_collect_encoded(None, ctypes.byref(cnt), ctypes.byref(nb), None) == api.ERR_INVALID_ARG

@@ -84,3 +84,47 @@ def test_capacity_reported(api):
     pl.close()
     assert r.status == api.ERR_CAPACITY and r.edit_count == ref.edit_count
     assert np.array_equal(out.numpy().view(np.uint32), ref.g.view(np.uint32))
+
+
+def test_encoded_sequence_matches_the_oracle(api):
+    """The encoded pipeline returns each field's edit list as a stream: byte
+    for byte the oracle's encoding of the oracle's edits, and applied to fhat
+    it gives the oracle's g."""
+    from oracle import edits as E
+    shape = (18, 21, 140)
+    fields = [synth.perlin3d_prequant(shape, seed=80 + k, eb_rel=1e-4) if k % 2 else
+              synth.peaks3d(shape, seed=80 + k, eb_rel=1e-4) for k in range(4)]
+    refs = [oracle.correct(fl.f, fl.fhat, fl.xi) for fl in fields]
+    pl = api.Pipeline(shape, encoded=True)
+    bufs = [(_pinned(fl.f), _pinned(fl.fhat), torch.empty(pl.stream_bound(), dtype=torch.uint8).pin_memory())
+            for fl in fields]
+    got = []
+    for k, (fl, b) in enumerate(zip(fields, bufs)):
+        if k >= 2:
+            got.append(pl.collect())
+        pl.submit(b[0], b[1], fl.xi, b[2])
+    got += [pl.collect(), pl.collect()]
+    for fl, ref, res in zip(fields, refs, got):
+        assert res.status == api.OK and res.edit_count == ref.edit_count
+        want = E.encode(*E.edits_of(fl.fhat, ref.g))
+        assert res.stream.numpy().tobytes() == want
+        field = torch.from_numpy(fl.fhat.copy()).cuda().reshape(-1)
+        assert api.decode_edits(res.stream.cuda(), field) == ref.edit_count
+        assert np.array_equal(field.cpu().numpy().view(np.uint32), ref.g.reshape(-1).view(np.uint32))
+    # a field-mode call on an encoded pipeline is rejected
+    import ctypes
+    assert api.load().msz_pipeline_collect(pl._h, ctypes.byref(ctypes.c_int64()), None) == api.ERR_INVALID_ARG
+    pl.close()
+
+
+def test_encoded_stream_capacity(api):
+    shape = (12, 14, 136)
+    fl = synth.peaks3d(shape, seed=90, eb_rel=1e-4)
+    ref = oracle.correct(fl.f, fl.fhat, fl.xi)
+    assert ref.edit_count > 100
+    pl = api.Pipeline(shape, encoded=True)
+    small = torch.empty(64, dtype=torch.uint8).pin_memory()
+    pl.submit(_pinned(fl.f), _pinned(fl.fhat), fl.xi, small)
+    r = pl.collect()
+    assert r.status == api.ERR_CAPACITY and r.edit_count == ref.edit_count
+    pl.close()
