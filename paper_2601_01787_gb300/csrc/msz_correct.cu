@@ -525,11 +525,19 @@ extern "C" msz_status msz_correct(const float *d_f, const float *d_fhat, float x
     if ((st = current_device(dev)) != MSZ_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = enqueue_correct(P, dev, s)) != MSZ_OK) return st;
+    // the control block and sweep 0's record in one read-back (the log
+    // follows the control block in the workspace)
+    static_assert(offsetof(Layout, ctrl) == 0, "layout order");
+    const size_t head = (size_t)((const char *)P.log - (const char *)P.ctrl) + sizeof(SweepRec);
+    alignas(16) unsigned char hb[1024];
+    static_assert(sizeof(Ctrl) + sizeof(SweepRec) <= sizeof hb, "read-back buffer");
+    if (head > sizeof hb) return MSZ_ERR_CUDA;
+    if (cudaMemcpyAsync(hb, P.ctrl, head, cudaMemcpyDeviceToHost, s) != cudaSuccess) return MSZ_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return MSZ_ERR_CUDA;
     Ctrl hc;
     SweepRec r0;
-    if (cudaMemcpyAsync(&hc, P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MSZ_ERR_CUDA;
-    if (cudaMemcpyAsync(&r0, P.log, sizeof r0, cudaMemcpyDeviceToHost, s) != cudaSuccess) return MSZ_ERR_CUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return MSZ_ERR_CUDA;
+    memcpy(&hc, hb, sizeof hc);
+    memcpy(&r0, hb + (head - sizeof(SweepRec)), sizeof r0);
     st = finish_correct(hc, r0, edit_capacity, h_edit_count, h_stats);
     if (st == MSZ_ERR_INPUT_BOUND || st == MSZ_ERR_TIMEOUT) return st;
     if (o.log_capacity > 0) {

@@ -577,10 +577,12 @@ __device__ __forceinline__ void own_row_tma(const FieldView &P, const float *p0,
     uint32_t differs = 0;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
+        // with f finite, L and U are finite, so L <= v <= U already rules out
+        // a NaN or infinite v
         const float L = floor_bound(fv[e], P.xi), U = ceil_bound(fv[e], P.xi);
-        bool ok = isfinite(fv[e]) && isfinite(hv[e]) && hv[e] >= L && hv[e] <= U;
+        bool ok = isfinite(fv[e]) && hv[e] >= L && hv[e] <= U;
         if (P.ginit) {
-            ok = ok && isfinite(gv[e]) && gv[e] >= L && gv[e] <= U;
+            ok = ok && gv[e] >= L && gv[e] <= U;
             differs |= (uint32_t)(__float_as_uint(hv[e]) != __float_as_uint(gv[e])) << e;
         }
         bad = bad || !ok;

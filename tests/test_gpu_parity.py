@@ -232,16 +232,23 @@ def test_max_sweeps_and_capacity(api):
     assert none.status == api.ERR_CAPACITY and none.edit_count == full.edit_count
 
 
-def test_input_bound_violations(api):
-    fl = synth.perlin2d((20, 30), seed=7)
+@pytest.mark.parametrize("shape", [(20, 30), (6, 12, 60), (6, 12, 140)])  # 2D, cp.async, TMA staging
+def test_input_bound_violations(api, shape):
+    fl = synth.perlin2d(shape, seed=7) if len(shape) == 2 else synth.perlin3d_prequant(shape, seed=7, eb_rel=1e-3)
+    at = (3, 4) if len(shape) == 2 else (2, 3, 4)
     bad = fl.fhat.copy()
-    bad[3, 4] = fl.f[3, 4] + np.float32(3) * fl.xi
+    bad[at] = fl.f[at] + np.float32(3) * fl.xi
     assert api.correct(dev(fl.f), dev(bad), fl.xi).status == api.ERR_INPUT_BOUND
-    nan = fl.fhat.copy()
-    nan[0, 0] = np.nan
-    assert api.correct(dev(fl.f), dev(nan), fl.xi).status == api.ERR_INPUT_BOUND
+    for value in (np.nan, np.inf, -np.inf):
+        odd = fl.fhat.copy()
+        odd[at] = value
+        assert api.correct(dev(fl.f), dev(odd), fl.xi).status == api.ERR_INPUT_BOUND
+        if len(shape) == 3:
+            g0 = fl.fhat.copy()
+            g0[at] = value  # an unusable proposed start
+            assert api.correct(dev(fl.f), dev(fl.fhat), fl.xi, g_init=dev(g0)).status == api.ERR_INPUT_BOUND
     inf = fl.f.copy()
-    inf[1, 1] = np.inf
+    inf[at] = np.inf
     assert api.correct(dev(inf), dev(fl.fhat), fl.xi).status == api.ERR_INPUT_BOUND
     # exactly at the floor and ceiling is valid
     lo = np.array([oracle.floor_bound(a, fl.xi) for a in fl.f.reshape(-1)], dtype=np.float32).reshape(fl.shape)
