@@ -388,6 +388,42 @@ __device__ __forceinline__ void tile_row(const FieldView &P, const float *pm, co
     distorted += E.distorted;
 }
 
+// The warp's row of plane p0 in the cp.async ring (row r, x0 .. x0+127, any
+// x extent): bound check and g = start value, 4 vertices a lane.  The
+// second field (fhat, or the start field when DETECT) sits PLANE floats
+// after f.
+template <bool DETECT>
+__device__ __forceinline__ void own_row_cp(const FieldView &P, const float *p0, int r, int x0, uint32_t rowbase,
+                                           bool &bad) {
+    using namespace tile;
+    const uint32_t lane = lane_id();
+    const int xl = x0 + 4 * (int)lane;
+    if (xl >= (int)P.G.nx) return;
+    const float4 f4 = *reinterpret_cast<const float4 *>(p0 + r * PW + 4 + 4 * (int)lane);
+    const float4 s4 = *reinterpret_cast<const float4 *>(p0 + PLANE + r * PW + 4 + 4 * (int)lane);
+    const float fv[4] = {f4.x, f4.y, f4.z, f4.w}, sv[4] = {s4.x, s4.y, s4.z, s4.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        if (xl + e >= (int)P.G.nx) break;
+        const uint32_t gi = rowbase + (uint32_t)(xl + e);
+        float fh = sv[e], gs = sv[e];
+        if (P.ginit) {
+            if (DETECT) fh = P.fhat[gi];
+            else gs = P.ginit[gi];
+        }
+        // with f finite, L and U are finite, so L <= v <= U rules out a NaN
+        // or infinite v
+        const float L = floor_bound(fv[e], P.xi), U = ceil_bound(fv[e], P.xi);
+        bool ok = isfinite(fv[e]) && fh >= L && fh <= U;
+        if (P.ginit) {
+            ok = ok && gs >= L && gs <= U;
+            if (__float_as_uint(fh) != __float_as_uint(gs)) red_or(&P.eb[gi >> 5], 1u << (gi & 31u));
+        }
+        bad = bad || !ok;
+        P.g[gi] = gs;
+    }
+}
+
 // ------------------------------------------------ tiled (3D) codes of f
 // One tile (x0, y0, planes zb .. ze-1) of field P: certification of every
 // vertex, codes of f at the uncertified ones, g = start value, bound check
@@ -472,33 +508,6 @@ __device__ __forceinline__ void first_tile(const FieldView &P, int x0, int y0, i
         }
         cp_async_commit();
     };
-    // owned vertices of plane p: bound check and g = start value
-    auto own = [&](int p) {
-        const int slot = (p - zb + 1) % NSLOT;
-        const uint32_t pb = (uint32_t)p * G.nxy;
-#pragma unroll
-        for (int j = 0; j < PER_THREAD; ++j) {
-            if (!(ownm >> j & 1u)) continue;
-            const int e = (int)tid + j * THREADS;
-            const int r = e / LOADW, c = e - r * LOADW;
-            const int so = slot * SLOT + r * PW + c + 3;
-            const uint32_t gi = pb + (uint32_t)(gbase + r * (int)G.nx + c);
-            const float fi = smem[so], sv = smem[so + PLANE];
-            float fh = sv, gs = sv;
-            if (P.ginit) {
-                if (DETECT) fh = P.fhat[gi];
-                else gs = P.ginit[gi];
-            }
-            const float L = floor_bound(fi, P.xi), U = ceil_bound(fi, P.xi);
-            bool ok = isfinite(fi) && isfinite(fh) && fh >= L && fh <= U;
-            if (P.ginit) {
-                ok = ok && isfinite(gs) && gs >= L && gs <= U;
-                if (__float_as_uint(fh) != __float_as_uint(gs)) red_or(&P.eb[gi >> 5], 1u << (gi & 31u));
-            }
-            bad = bad || !ok;
-            P.g[gi] = gs;
-        }
-    };
     issue(zb - 1);
     issue(zb);
     issue(zb + 1);
@@ -508,11 +517,11 @@ __device__ __forceinline__ void first_tile(const FieldView &P, int x0, int y0, i
         cp_async_wait<1>();  // planes up to z+1 of this thread have landed (z+2 may be in flight)
         __syncthreads();     // ... of every thread; the slot of z-2 is free
         issue(z + 3);
-        own(z);
         if (y >= (int)G.ny) continue;
         auto plane = [&](int p) { return smem + ((p - zb + 1) % NSLOT) * SLOT; };
-        tile_row<DETECT>(P, plane(z - 1), plane(z), plane(z + 1), PLANE, r, x0,
-                         (uint32_t)z * G.nxy + (uint32_t)y * G.nx, distorted);
+        const uint32_t rowbase = (uint32_t)z * G.nxy + (uint32_t)y * G.nx;
+        own_row_cp<DETECT>(P, plane(z), r, x0, rowbase, bad);
+        tile_row<DETECT>(P, plane(z - 1), plane(z), plane(z + 1), PLANE, r, x0, rowbase, distorted);
     }
     cp_async_wait<0>();
 }
