@@ -471,6 +471,16 @@ __device__ __forceinline__ void first_tile(const FieldView &P, int x0, int y0, i
             if (DETECT) smem[sl * SLOT + PLANE + r * PW + c + 3] = qnan;
         }
     }
+    // this thread's staged elements: shared-memory word within a slot and
+    // offset within a grid plane, computed once a tile
+    uint32_t soff[PER_THREAD], goff[PER_THREAD];
+#pragma unroll
+    for (int j = 0; j < PER_THREAD; ++j) {
+        const int e = (int)tid + j * THREADS;
+        const int r = e / LOADW, c = e - r * LOADW;
+        soff[j] = (uint32_t)(r * PW + c + 3);
+        goff[j] = (uint32_t)(gbase + r * (int)G.nx + c);
+    }
     // asynchronous copy of plane p (f over the staged region, the second
     // field over its region) into its ring slot; planes outside the grid
     // become NaN
@@ -479,21 +489,19 @@ __device__ __forceinline__ void first_tile(const FieldView &P, int x0, int y0, i
             const int slot = (p - zb + 1) % NSLOT;
             const bool inside = p < (int)G.nz;
             const uint32_t pb = (uint32_t)p * G.nxy;
+            const float *sec = DETECT && P.ginit ? P.ginit : P.fhat;
 #pragma unroll
             for (int j = 0; j < PER_THREAD; ++j) {
                 if (!(inm >> j & 1u)) continue;
-                const int e = (int)tid + j * THREADS;
-                const int r = e / LOADW, c = e - r * LOADW;
-                const uint32_t so = (uint32_t)(slot * SLOT + r * PW + c + 3);
+                const uint32_t so = (uint32_t)(slot * SLOT) + soff[j];
                 if (!inside) {
                     smem[so] = qnan;
                     if (DETECT) smem[so + PLANE] = qnan;
                     continue;
                 }
-                const uint32_t gi = pb + (uint32_t)(gbase + r * (int)G.nx + c);
+                const uint32_t gi = pb + goff[j];
                 cp_async4(sbase + 4u * so, P.f + gi);
-                if (secm >> j & 1u)
-                    cp_async4(sbase + 4u * (so + (uint32_t)PLANE), (DETECT && P.ginit ? P.ginit : P.fhat) + gi);
+                if (secm >> j & 1u) cp_async4(sbase + 4u * (so + (uint32_t)PLANE), sec + gi);
             }
         } else if (p < 0) {
             const int slot = (p - zb + 1) % NSLOT;
