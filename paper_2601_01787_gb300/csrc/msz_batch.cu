@@ -280,17 +280,40 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
                     rec1[f].worklist = P.fields[f].F.G.n;
                     rec1[f].dense = 1;
                 }
-            // per word: in a whole-field sweep every uncertified vertex of a
-            // live field, else those of its worklist; done fields none.  The
-            // worklist is cleared as it is read (a word never straddles two
-            // fields: bases are 1024-aligned).
+            if (dense_next) {
+                // whole-field scans: every uncertified vertex of a live field,
+                // tile by tile over the shared tile queue (g staged in shared
+                // memory); the worklist bitmap is cleared for the next sweep
+                for (uint32_t w = gtid; w < P.all.words; w += stride) dcur[w] = 0u;
+                uint32_t *counter = &rec1[0].pad[0];
+                for (;;) {
+                    __syncthreads();
+                    if (threadIdx.x == 0) s_next = atomicAdd(counter, 1u);
+                    __syncthreads();
+                    const uint32_t t = s_next;
+                    if (t >= P.ntiles) break;
+                    const uint32_t f = find_field(s_tile, nf, t);
+                    if (!alive(f)) continue;
+                    const FieldView &F = P.fields[f].F;
+                    const tile::TileGeom tg = tile::tile_geom(F.G.nx, F.G.ny, F.G.nz, F.tile_z);
+                    const uint32_t lt = t - s_tile[f];
+                    const uint32_t txi = lt % tg.tx, tyi = (lt / tg.tx) % tg.ty, tzi = lt / (tg.tx * tg.ty);
+                    const int zb = (int)(tzi * tg.bz);
+                    uint32_t dist = 0;
+                    detect_tile_cp(F, (int)(txi * tile::BX), (int)(tyi * tile::BY), zb,
+                                   min(zb + (int)tg.bz, (int)F.G.nz), smem, F.dm[(k1 + 1) & 1], dist);
+                    warp_add(dist, &s_cnt[f][1]);
+                }
+            } else
+            // per word: the uncertified vertices of a live field's worklist;
+            // done fields none.  The worklist is cleared as it is read (a
+            // word never straddles two fields: bases are 1024-aligned).
             walk_words_pairs(
                 P.all, [&](uint32_t wi) -> uint32_t { return dcur[wi]; },
                 [&](uint32_t wi, uint32_t wl) -> uint32_t {
                     const uint32_t f = field_of(P.bfield, wi * 32u);
                     if (wl) dcur[wi] = 0u;
                     if (!alive(f)) return 0u;
-                    if (dense_next) return P.ub[wi];
                     if (!wl) return 0u;
                     atomicAdd(&s_cnt[f][0], (uint32_t)__popc(wl));
                     return wl & P.ub[wi];

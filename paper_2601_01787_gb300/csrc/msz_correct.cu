@@ -171,6 +171,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
             if (TMA) {
                 detect_tiled_tma(F, P.detect_tile_z, &P.map_g, &P.log[k1].tile_next, smem, &C->error, E.dnext,
                                  E.distorted);
+            } else if (NDIM == 3) {
+                detect_tiled_cp(F, P.detect_tile_z, &P.log[k1].tile_next, smem, E.dnext, E.distorted);
             } else {
                 walk_bits_pairs<false>(F.ub, nullptr, G, seen, [&](bool h1, uint32_t v1, bool h2, uint32_t v2) {
                     detect_vertex2<NDIM>(F, E, h1, v1, h2, v2);
@@ -376,12 +378,13 @@ static msz_status launch_correct(Problem &P, const DeviceInfo &dev, cudaStream_t
     return MSZ_OK;
 }
 
-// Default whole-grid detection rule (P.dense_min == 0).  With TMA staging a
-// whole-grid pass costs about one code pass without the certification, and
-// beats the worklist while the worklist is large: measured at 512^3, dense
-// while 6 x distorted >= N/4 takes the peak field from 26.4 to 22.9 ms and
-// leaves the Perlin field on worklists.  The gather-based whole-grid walk of
-// the cp.async path never beat the worklist.
+// Default whole-grid detection rule (P.dense_min == 0).  A tiled whole-grid
+// pass (g staged by TMA, or by cp.async on grids the TMA ring cannot stage)
+// costs about one code pass without the certification, and beats the
+// worklist while the worklist is large: measured at 512^3, dense while
+// 6 x distorted >= N/4 takes the peak field from 26.4 to 22.9 ms (TMA) and
+// from 24.5 to 23.6 ms (cp.async), and leaves the Perlin field on worklists.
+// 2D grids keep worklists (their whole-grid walk gathers).
 template <int NDIM>
 static msz_status run_correct(Problem &P, const DeviceInfo &dev, cudaStream_t stream) {
     if constexpr (NDIM == 3) {
@@ -391,7 +394,7 @@ static msz_status run_correct(Problem &P, const DeviceInfo &dev, cudaStream_t st
             return launch_correct<3, true>(P, dev, stream);
         }
     }
-    if (P.dense_min == 0) P.dense_min = -1;
+    if (P.dense_min == 0) P.dense_min = NDIM == 3 ? (long long)(P.F.G.n / 4) : -1;
     return launch_correct<NDIM, false>(P, dev, stream);
 }
 

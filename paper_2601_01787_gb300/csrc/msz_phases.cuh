@@ -534,6 +534,132 @@ __device__ __forceinline__ void first_tile(const FieldView &P, int x0, int y0, i
     cp_async_wait<0>();
 }
 
+// ------------------------------------------- tiled whole-grid detection (cp.async)
+// One tile (x0, y0, planes zb .. ze-1) of field P in a whole-grid detection
+// of a later sweep, for grids the TMA ring cannot stage: g is staged plane by
+// plane through the cp.async ring (NaN outside the grid; field slot 0 only),
+// and each warp examines its row's uncertified vertices 32 at a time, their
+// codes of g from shared memory and of f from codes_f.  Distorted vertices
+// mark their targets and themselves in dnext and add to `distorted`.
+// Block-collective; the caller synchronizes the block before the next tile.
+__device__ __forceinline__ void detect_tile_cp(const FieldView &P, int x0, int y0, int zb, int ze, float *smem,
+                                               uint32_t *dnext, uint32_t &distorted) {
+    using namespace tile;
+    const GridDev &G = P.G;
+    const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+    uint32_t inm = 0, soff[PER_THREAD], goff[PER_THREAD];
+    const int gbase = (y0 - 1) * (int)G.nx + (x0 - 1);
+#pragma unroll
+    for (int j = 0; j < PER_THREAD; ++j) {
+        const int e = (int)tid + j * THREADS;
+        const int r = e / LOADW, c = e - r * LOADW;
+        const int gx = x0 - 1 + c, gy = y0 - 1 + r;
+        inm |= (uint32_t)(e < ELEMS && gx >= 0 && gx < (int)G.nx && gy >= 0 && gy < (int)G.ny) << j;
+        soff[j] = (uint32_t)(r * PW + c + 3);
+        goff[j] = (uint32_t)(gbase + r * (int)G.nx + c);
+    }
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
+    const float qnan = __int_as_float(0x7fffffff);
+#pragma unroll
+    for (int j = 0; j < PER_THREAD; ++j) {
+        const int e = (int)tid + j * THREADS;
+        if (e >= ELEMS || (inm >> j & 1u)) continue;
+        for (int sl = 0; sl < NSLOT; ++sl) smem[sl * SLOT + soff[j]] = qnan;
+    }
+    auto issue = [&](int p) {
+        if (p >= 0 && p <= ze) {
+            const uint32_t so0 = (uint32_t)(((p - zb + 1) % NSLOT) * SLOT);
+            const bool inside = p < (int)G.nz;
+            const uint32_t pb = (uint32_t)p * G.nxy;
+#pragma unroll
+            for (int j = 0; j < PER_THREAD; ++j) {
+                if (!(inm >> j & 1u)) continue;
+                if (!inside) smem[so0 + soff[j]] = qnan;
+                else cp_async4(sbase + 4u * (so0 + soff[j]), P.g + pb + goff[j]);
+            }
+        } else if (p < 0) {
+            const uint32_t so0 = (uint32_t)(((p - zb + 1) % NSLOT) * SLOT);
+#pragma unroll
+            for (int j = 0; j < PER_THREAD; ++j)
+                if (inm >> j & 1u) smem[so0 + soff[j]] = qnan;
+        }
+        cp_async_commit();
+    };
+    issue(zb - 1);
+    issue(zb);
+    issue(zb + 1);
+    issue(zb + 2);
+    const int y = y0 + (int)warp, r = (int)warp + 1;
+    const int xl = x0 + 4 * (int)lane;
+    Emitter E{dnext, 0};
+    for (int z = zb; z < ze; ++z) {
+        cp_async_wait<1>();
+        __syncthreads();
+        issue(z + 3);
+        if (y >= (int)G.ny) continue;
+        auto plane = [&](int p) { return smem + ((p - zb + 1) % NSLOT) * SLOT; };
+        const uint32_t rowbase = (uint32_t)z * G.nxy + (uint32_t)y * G.nx;
+        // this lane's 4 uncertified bits (they may straddle two words) and
+        // codes of f
+        uint32_t nib = 0, cfw = 0;
+        if (xl < (int)G.nx) {
+            const uint32_t i0 = rowbase + (uint32_t)xl, sh = i0 & 31u;
+            uint32_t bits = __ldg(&P.ub[i0 >> 5]) >> sh;
+            if (sh > 28u && (i0 >> 5) + 1u < G.words) bits |= __ldg(&P.ub[(i0 >> 5) + 1u]) << (32u - sh);
+            const uint32_t valid = (int)G.nx - xl >= 4 ? 15u : (1u << ((int)G.nx - xl)) - 1u;
+            nib = bits & valid;
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if ((nib >> e) & 1u) cfw |= (uint32_t)__ldg(&P.codes_f[i0 + e]) << (8 * e);
+        }
+        uint32_t w = nib << (4u * (lane & 7u));
+        w |= __shfl_xor_sync(kFull, w, 1);
+        w |= __shfl_xor_sync(kFull, w, 2);
+        w |= __shfl_xor_sync(kFull, w, 4);
+        const uint32_t w0 = __shfl_sync(kFull, w, 0), w1 = __shfl_sync(kFull, w, 8);
+        const uint32_t w2 = __shfl_sync(kFull, w, 16), w3 = __shfl_sync(kFull, w, 24);
+        const uint32_t c0 = (uint32_t)__popc(w0), c1 = c0 + (uint32_t)__popc(w1);
+        const uint32_t c2 = c1 + (uint32_t)__popc(w2), total = c2 + (uint32_t)__popc(w3);
+        for (uint32_t j0 = 0; j0 < total; j0 += 32u) {
+            const uint32_t j = j0 + lane;
+            const bool has = j < total;
+            uint32_t col = 0, cg = 0;
+            if (has) {
+                const uint32_t q = j < c0 ? 0u : j < c1 ? 1u : j < c2 ? 2u : 3u;
+                const uint32_t wq = q == 0 ? w0 : q == 1 ? w1 : q == 2 ? w2 : w3;
+                const uint32_t before = q == 0 ? 0u : q == 1 ? c0 : q == 2 ? c1 : c2;
+                col = 32u * q + nth_set(wq, j - before);
+                cg = code1(plane(z - 1), plane(z), plane(z + 1), r, 4 + (int)col);
+            }
+            const uint32_t cf = (__shfl_sync(kFull, cfw, (int)(col >> 2)) >> (8u * (col & 3u))) & 0xffu;
+            report(P, E, has, rowbase + (uint32_t)x0 + col, cf, cg);
+        }
+    }
+    cp_async_wait<0>();
+    distorted += E.distorted;
+}
+
+// Whole-grid detection of a later sweep over the tiles of one field (the
+// cp.async form; block-collective).
+__device__ __forceinline__ void detect_tiled_cp(const FieldView &P, uint32_t tile_z, uint32_t *tile_next, float *smem,
+                                                uint32_t *dnext, uint32_t &distorted) {
+    using namespace tile;
+    const GridDev &G = P.G;
+    const TileGeom tg = tile_geom(G.nx, G.ny, G.nz, tile_z);
+    __shared__ uint32_t s_tile;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_tile = atomicAdd(tile_next, 1u);
+        __syncthreads();
+        const uint32_t t = s_tile;
+        if (t >= tg.count) break;
+        const uint32_t txi = t % tg.tx, tyi = (t / tg.tx) % tg.ty, tzi = t / (tg.tx * tg.ty);
+        const int zb = (int)(tzi * tg.bz);
+        detect_tile_cp(P, (int)(txi * BX), (int)(tyi * BY), zb, min(zb + (int)tg.bz, (int)G.nz), smem, dnext,
+                       distorted);
+    }
+}
+
 // Tiles of one field handed out by an atomic counter (block-collective).
 // DETECT: the pass also runs sweep 0's detection (distorted vertices counted
 // in `distorted`).
