@@ -149,10 +149,14 @@ __device__ __forceinline__ void detect_pair(const BatchProblem &P, const uint32_
     const uint32_t cf2 = l2 ? __ldg(&F2.codes_f[i2]) : 0u;
     Emitter E1{F1.dm[next_parity], 0};
     report(F1, E1, l1, i1, cf1, code_of_closed<3>(a));
-    if (E1.distorted) atomicAdd(&s_cnt[f1][1], 1u);
     Emitter E2{F2.dm[next_parity], 0};
     report(F2, E2, l2, i2, cf2, code_of_closed<3>(b));
-    if (E2.distorted) atomicAdd(&s_cnt[f2][1], 1u);
+    // distorted counts per field, aggregated over the warp's lanes of one field
+    const uint32_t lane = lane_id();
+    const uint32_t p1 = __match_any_sync(kFull, E1.distorted ? f1 : 0xffffffffu);
+    if (E1.distorted && lane == (uint32_t)(__ffs(p1) - 1)) atomicAdd(&s_cnt[f1][1], (uint32_t)__popc(p1));
+    const uint32_t p2 = __match_any_sync(kFull, E2.distorted ? f2 : 0xffffffffu);
+    if (E2.distorted && lane == (uint32_t)(__ffs(p2) - 1)) atomicAdd(&s_cnt[f2][1], (uint32_t)__popc(p2));
 }
 
 __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant__ const BatchProblem P) {
@@ -246,12 +250,20 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
         {
             uint32_t targets = 0;
             walk_bits<true>(P.tb, nullptr, P.all, targets, [&](bool has, uint32_t t) {
-                if (!has) return;
-                const uint32_t f = field_of(P.bfield, t);
-                if (!alive(f)) return;
-                const FieldView &F = P.fields[f].F;
-                atomicAdd(&s_cnt[f][2], 1u);
-                if (apply_target<3>(F, t - s_base[f], dense_next, F.dm[(k + 1) & 1])) atomicAdd(&s_cnt[f][3], 1u);
+                const uint32_t f = has ? field_of(P.bfield, t) : 0u;
+                const bool live = has && alive(f);
+                bool changed = false;
+                if (live) {
+                    const FieldView &F = P.fields[f].F;
+                    changed = apply_target<3>(F, t - s_base[f], dense_next, F.dm[(k + 1) & 1]);
+                }
+                // counts per field, aggregated over the warp's lanes of one field
+                const uint32_t peers = __match_any_sync(kFull, live ? f : 0xffffffffu);
+                const uint32_t nch = (uint32_t)__popc(peers & __ballot_sync(kFull, changed));
+                if (live && lane_id() == (uint32_t)(__ffs(peers) - 1)) {
+                    atomicAdd(&s_cnt[f][2], (uint32_t)__popc(peers));
+                    if (nch) atomicAdd(&s_cnt[f][3], nch);
+                }
             });
             (void)targets;
             flush_counts(s_cnt, nf, rec);
