@@ -596,7 +596,8 @@ def run_learned(dev, stream, reps: int = 3) -> dict:
     seed 7; relative bound 1e-4; uniform noise): wall time on the device from
     f and fhat resident to a corrected field and its edit list, sweeps, and
     the verification of both results.  The network is trained first by its
-    recipe (200 seeded 128^3 triples) unless this build already has it."""
+    recipe (200 seeded 128^3 triples) unless the library's cache
+    already holds it."""
     import torch
 
     from paper_2601_01787_gb300 import api, learned, synth

@@ -5,7 +5,7 @@ channels, ReLU between) classifies each vertex by k = 0..15, the number of
 HALVE edits the plain correction loop applies to it (15: fifteen or more).
 The start g0 = fhat edited k times by that same rule goes to msz_correct as
 its initial field and the exact loop finishes from there, so the result is
-judged by the same loop and the same invariant check as the plain method; a
+checked by the same loop and the same invariant check as the plain method; a
 vertex whose class is right starts at exactly the plain loop's final value.
 
 Every tensor operation of the network -- features, the conv layers on tcgen05,
@@ -375,8 +375,8 @@ def _cache_path(recipe: dict) -> str:
 
 
 def default_net(device=None, train_if_missing: bool = True, recipe: dict | None = None, verbose: bool = False):
-    """The network trained by `recipe` (default RECIPE) with this build's
-    kernels, cached next to the library; returns (net, info)."""
+    """The network trained by `recipe` (default RECIPE) with the compiled
+    library's kernels, cached next to the library; returns (net, info)."""
     import os
     recipe = dict(RECIPE if recipe is None else recipe)
     path = _cache_path(recipe)
