@@ -207,6 +207,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
     const uint32_t gw = blockIdx.x * wpb + warp;
     const uint32_t w0 = min(gw * per, W), w1 = min(w0 + per, W);
     uint32_t cnt = 0, unc = 0;
+#pragma unroll 4
     for (uint32_t w = w0 + lane; w < w1; w += 32) {
         cnt += __popc(F.eb[w]);
         unc += __popc(F.ub[w]);
@@ -229,9 +230,13 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
     block_exclusive_scan(all, sm, all);
     if (leader) C->edit_count = all;
     unsigned long long prefix = (unsigned long long)bpre + warp_pre;
+    // each bitmap word is loaded one round ahead: its latency overlaps the
+    // previous round's gathers and stores
+    uint32_t ahead = w0 + lane < w1 ? F.eb[w0 + lane] : 0u;
     for (uint32_t r = w0; r < w1; r += 32) {
         const uint32_t w = r + lane;
-        const uint32_t word = w < w1 ? F.eb[w] : 0u;
+        const uint32_t word = ahead;
+        ahead = r + 32u + lane < w1 ? F.eb[r + 32u + lane] : 0u;
         const uint32_t c = (uint32_t)__popc(word);
         uint32_t incl = c;
 #pragma unroll

@@ -19,14 +19,6 @@
 namespace msz {
 
 constexpr uint32_t kTileZ = 32;  // default planes per tile of the code pass
-#ifndef MSZ_DENSE_WORD
-#define MSZ_DENSE_WORD 10
-#endif
-// set bits from which a bitmap word is walked by the whole warp (one vertex
-// a lane, coalesced neighbour loads) rather than bit by bit in its own lane
-// (measured on the 512^3 peak field: 3, 4, 6, 10, 14, 20, never -> 25.1,
-// 23.9, 22.2, 21.4, 21.5, 21.7, 21.6 ms; the Perlin field within 1 %)
-constexpr int kDenseWord = MSZ_DENSE_WORD;
 #ifndef MSZ_WALK_AHEAD
 #define MSZ_WALK_AHEAD 4
 #endif
@@ -75,11 +67,74 @@ __device__ __forceinline__ bool report(const FieldView &P, Emitter &E, bool vali
     return dist;
 }
 
+// The set bits of one chunk of 32 bitmap words (lane l holds word base + l
+// in `bits`), handed out to the warp's lanes in index order: the chunk's
+// j-th set bit goes to lane j mod 32.  pick(j, has, v) gives the vertex of
+// the j-th bit (warp-collective: every lane calls it, with its own j).
+struct ChunkBits {
+    uint32_t base, bits, cnt, incl, total;
+    __device__ __forceinline__ ChunkBits(uint32_t b, uint32_t w) : base(b), bits(w) {
+        const uint32_t lane = lane_id();
+        cnt = (uint32_t)__popc(w);
+        incl = cnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, incl, d);
+            if (lane >= (uint32_t)d) incl += y;
+        }
+        total = __shfl_sync(kFull, incl, 31);
+    }
+    __device__ __forceinline__ void pick(uint32_t j, bool &has, uint32_t &v) const {
+        // the lane whose word holds bit j: the first whose inclusive count
+        // exceeds j
+        uint32_t owner = 0;
+#pragma unroll
+        for (uint32_t s = 16; s >= 1; s >>= 1) {
+            const uint32_t c = __shfl_sync(kFull, incl, (int)(owner + s - 1u));
+            if (c <= j) owner += s;
+        }
+        owner &= 31u;
+        const uint32_t word = __shfl_sync(kFull, bits, (int)owner);
+        const uint32_t before = __shfl_sync(kFull, incl - cnt, (int)owner);
+        has = j < total;
+        v = has ? (base + owner) * 32u + tile::nth_set(word, j - before) : 0u;
+    }
+};
+
+// fn(has, v) once per round with one set bit of the chunk a lane.
+template <class F>
+__device__ __forceinline__ void chunk_each(uint32_t base, uint32_t bits, F &&fn) {
+    const ChunkBits cb(base, bits);
+    for (uint32_t j0 = 0; j0 < cb.total; j0 += 32u) {
+        bool h;
+        uint32_t v;
+        cb.pick(j0 + lane_id(), h, v);
+        fn(h, v);
+    }
+}
+
+// fn(has1, v1, has2, v2) once per round with two set bits of the chunk a
+// lane (bits j and j + 32 of a round of 64), so that each lane has the
+// loads of both in flight at once.
+template <class F>
+__device__ __forceinline__ void chunk_pairs(uint32_t base, uint32_t bits, F &&fn) {
+    const ChunkBits cb(base, bits);
+    for (uint32_t j0 = 0; j0 < cb.total; j0 += 64u) {
+        bool h1, h2;
+        uint32_t v1, v2;
+        cb.pick(j0 + lane_id(), h1, v1);
+        cb.pick(j0 + 32u + lane_id(), h2, v2);
+        fn(h1, v1, h2, v2);
+    }
+}
+
 // Warp-collective walk over the set bits of a bitmap: each warp takes 32
 // consecutive words (1024 vertices) at a time, grid-stride.  CLEAR zeroes the
 // visited words; `seen` counts their set bits; a non-null filter restricts the
 // calls to the vertices also set there.  fn(valid, v) runs once per round
-// with one vertex per lane.
+// with one vertex per lane, the chunk's bits handed out in index order
+// (chunk_each), so that a round's loads are in flight together however the
+// bits fall on the words.
 template <bool CLEAR, class F>
 __device__ __forceinline__ void walk_bits(uint32_t *bm, const uint32_t *filter, const GridDev &G, uint32_t &seen,
                                           F &&fn) {
@@ -110,34 +165,14 @@ __device__ __forceinline__ void walk_bits(uint32_t *bm, const uint32_t *filter, 
             seen += (uint32_t)__popc(bits);
             if (filter) bits &= filter[wi];
         }
-        // words with many set bits: the whole warp takes one word at a time,
-        // lane l on vertex 32*word + l, so neighbour loads coalesce
-        const bool dense = __popc(bits) >= kDenseWord;
-        uint32_t dm = __ballot_sync(kFull, dense);
-        while (dm) {
-            const int j = __ffs(dm) - 1;
-            dm &= dm - 1u;
-            const uint32_t word = __shfl_sync(kFull, bits, j);
-            fn(((word >> lane) & 1u) != 0u, (base + (uint32_t)j) * 32u + lane);
-        }
-        if (dense) bits = 0u;
-        // the remaining sparse words: each lane walks its own word's bits
-        while (__any_sync(kFull, bits != 0u)) {
-            const bool has = bits != 0u;
-            uint32_t v = 0;
-            if (has) {
-                v = wi * 32u + (uint32_t)(__ffs(bits) - 1);
-                bits &= bits - 1u;
-            }
-            fn(has, v);
-        }
+        chunk_each(base, bits, fn);
     }
 }
 
-// walk_bits for detection: two vertices per lane per step (two dense words,
-// or two bits of a lane's sparse word), so that each lane has the neighbour
-// loads of both in flight at once.  fn(has1, v1, has2, v2).  word_ok(w)
-// false drops word w (after counting it in `seen`).
+// walk_bits for detection: two vertices per lane per round (chunk_pairs), so
+// that each lane has the neighbour loads of both in flight at once.
+// fn(has1, v1, has2, v2).  word_ok(w) false drops word w (after counting it
+// in `seen`).  The filter's words are loaded one chunk ahead.
 struct AllWords {
     __device__ __forceinline__ bool operator()(uint32_t) const { return true; }
 };
@@ -155,52 +190,33 @@ __device__ __forceinline__ void walk_bits_pairs(uint32_t *bm, const uint32_t *fi
         const uint32_t wi = (gw + (uint32_t)u * nw) * 32u + lane;
         pre[u] = wi < G.words ? bm[wi] : 0u;
     }
+    uint32_t fnext = 0;  // the filter's word for the warp's next chunk
+    if (filter) {
+        const uint32_t wi = gw * 32u + lane;
+        fnext = pre[0] && wi < G.words ? filter[wi] : 0u;
+    }
     for (uint32_t c = gw; c < chunks; c += nw) {
         const uint32_t base = c * 32u;
         const uint32_t wi = base + lane;
         uint32_t bits = pre[0];
+        const uint32_t fcur = fnext;
 #pragma unroll
         for (int u = 0; u + 1 < kAhead; ++u) pre[u] = pre[u + 1];
         {
             const uint32_t wn = (c + (uint32_t)kAhead * nw) * 32u + lane;
             pre[kAhead - 1] = wn < G.words ? bm[wn] : 0u;
         }
+        if (filter) {
+            const uint32_t wn = (c + nw) * 32u + lane;
+            fnext = pre[0] && wn < G.words ? filter[wn] : 0u;
+        }
         if (bits) {
             if (CLEAR) bm[wi] = 0u;
             seen += (uint32_t)__popc(bits);
-            if (filter) bits &= filter[wi];
+            if (filter) bits &= fcur;
             if (bits && !word_ok(wi)) bits = 0u;
         }
-        const bool dense = __popc(bits) >= kDenseWord;
-        uint32_t dm = __ballot_sync(kFull, dense);
-        while (dm) {
-            const int j1 = __ffs(dm) - 1;
-            dm &= dm - 1u;
-            const uint32_t w1 = __shfl_sync(kFull, bits, j1);
-            int j2 = -1;
-            if (dm) {
-                j2 = __ffs(dm) - 1;
-                dm &= dm - 1u;
-            }
-            const uint32_t w2 = __shfl_sync(kFull, bits, j2 < 0 ? 0 : j2);
-            fn(((w1 >> lane) & 1u) != 0u, (base + (uint32_t)j1) * 32u + lane,
-               j2 >= 0 && ((w2 >> lane) & 1u) != 0u, (base + (uint32_t)(j2 < 0 ? 0 : j2)) * 32u + lane);
-        }
-        if (dense) bits = 0u;
-        while (__any_sync(kFull, bits != 0u)) {
-            const bool h1 = bits != 0u;
-            uint32_t v1 = 0, v2 = 0;
-            if (h1) {
-                v1 = wi * 32u + (uint32_t)(__ffs(bits) - 1);
-                bits &= bits - 1u;
-            }
-            const bool h2 = bits != 0u;
-            if (h2) {
-                v2 = wi * 32u + (uint32_t)(__ffs(bits) - 1);
-                bits &= bits - 1u;
-            }
-            fn(h1, v1, h2, v2);
-        }
+        chunk_pairs(base, bits, fn);
     }
 }
 
@@ -229,37 +245,8 @@ __device__ __forceinline__ void walk_words_pairs(const GridDev &G, FE &&fetch, F
             const uint32_t wn = (c + (uint32_t)kAhead * nw) * 32u + lane;
             pre[kAhead - 1] = wn < G.words ? fetch(wn) : 0u;
         }
-        uint32_t bits = wi < G.words ? finish(wi, raw) : 0u;
-        const bool dense = __popc(bits) >= kDenseWord;
-        uint32_t dm = __ballot_sync(kFull, dense);
-        while (dm) {
-            const int j1 = __ffs(dm) - 1;
-            dm &= dm - 1u;
-            const uint32_t w1 = __shfl_sync(kFull, bits, j1);
-            int j2 = -1;
-            if (dm) {
-                j2 = __ffs(dm) - 1;
-                dm &= dm - 1u;
-            }
-            const uint32_t w2 = __shfl_sync(kFull, bits, j2 < 0 ? 0 : j2);
-            fn(((w1 >> lane) & 1u) != 0u, (base + (uint32_t)j1) * 32u + lane,
-               j2 >= 0 && ((w2 >> lane) & 1u) != 0u, (base + (uint32_t)(j2 < 0 ? 0 : j2)) * 32u + lane);
-        }
-        if (dense) bits = 0u;
-        while (__any_sync(kFull, bits != 0u)) {
-            const bool h1 = bits != 0u;
-            uint32_t v1 = 0, v2 = 0;
-            if (h1) {
-                v1 = wi * 32u + (uint32_t)(__ffs(bits) - 1);
-                bits &= bits - 1u;
-            }
-            const bool h2 = bits != 0u;
-            if (h2) {
-                v2 = wi * 32u + (uint32_t)(__ffs(bits) - 1);
-                bits &= bits - 1u;
-            }
-            fn(h1, v1, h2, v2);
-        }
+        const uint32_t bits = wi < G.words ? finish(wi, raw) : 0u;
+        chunk_pairs(base, bits, fn);
     }
 }
 
@@ -591,6 +578,26 @@ __device__ __forceinline__ void detect_tile_cp(const FieldView &P, int x0, int y
     issue(zb + 2);
     const int y = y0 + (int)warp, r = (int)warp + 1;
     const int xl = x0 + 4 * (int)lane;
+    const bool in = y < (int)G.ny && xl < (int)G.nx;
+    const uint32_t valid = !in ? 0u : (int)G.nx - xl >= 4 ? 15u : (1u << ((int)G.nx - xl)) - 1u;
+    // this lane's 4 uncertified bits (they may straddle two words) and codes
+    // of f, loaded one plane ahead as raw values and combined where used, so
+    // that their latency overlaps the examination of the plane before
+    uint32_t ua = 0, ua1 = 0, cb[4] = {0u, 0u, 0u, 0u};
+    auto fetch = [&](int z) {
+        ua = 0;
+        ua1 = 0;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) cb[e] = 0;
+        if (!in || z >= ze) return;
+        const uint32_t i0 = (uint32_t)z * G.nxy + (uint32_t)y * G.nx + (uint32_t)xl, wi = i0 >> 5;
+        ua = __ldg(&P.ub[wi]);
+        if ((i0 & 31u) > 28u && wi + 1u < G.words) ua1 = __ldg(&P.ub[wi + 1u]);
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if ((valid >> e) & 1u) cb[e] = __ldg(&P.codes_f[i0 + e]);
+    };
+    fetch(zb);
     Emitter E{dnext, 0};
     for (int z = zb; z < ze; ++z) {
         cp_async_wait<1>();
@@ -599,19 +606,16 @@ __device__ __forceinline__ void detect_tile_cp(const FieldView &P, int x0, int y
         if (y >= (int)G.ny) continue;
         auto plane = [&](int p) { return smem + ((p - zb + 1) % NSLOT) * SLOT; };
         const uint32_t rowbase = (uint32_t)z * G.nxy + (uint32_t)y * G.nx;
-        // this lane's 4 uncertified bits (they may straddle two words) and
-        // codes of f
         uint32_t nib = 0, cfw = 0;
-        if (xl < (int)G.nx) {
-            const uint32_t i0 = rowbase + (uint32_t)xl, sh = i0 & 31u;
-            uint32_t bits = __ldg(&P.ub[i0 >> 5]) >> sh;
-            if (sh > 28u && (i0 >> 5) + 1u < G.words) bits |= __ldg(&P.ub[(i0 >> 5) + 1u]) << (32u - sh);
-            const uint32_t valid = (int)G.nx - xl >= 4 ? 15u : (1u << ((int)G.nx - xl)) - 1u;
+        if (in) {
+            const uint32_t sh = (rowbase + (uint32_t)xl) & 31u;
+            uint32_t bits = ua >> sh;
+            if (sh > 28u) bits |= ua1 << (32u - sh);
             nib = bits & valid;
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                if ((nib >> e) & 1u) cfw |= (uint32_t)__ldg(&P.codes_f[i0 + e]) << (8 * e);
+            // codes of certified vertices are never written and never used
+            cfw = cb[0] | cb[1] << 8 | cb[2] << 16 | cb[3] << 24;
         }
+        fetch(z + 1);
         uint32_t w = nib << (4u * (lane & 7u));
         w |= __shfl_xor_sync(kFull, w, 1);
         w |= __shfl_xor_sync(kFull, w, 2);
@@ -865,24 +869,46 @@ __device__ __forceinline__ void first_tiled_tma(const FieldView &P, const CUtens
 // of f from codes_f; distorted ones mark their targets and themselves in
 // dnext (the next sweep's worklist).  nx is a multiple of 4, so a lane's 4
 // vertices have their 4 uncertified bits in one bitmap word and their codes
-// of f in one aligned 32-bit word.
+// of f in one aligned 32-bit word.  Both are loaded one plane ahead (the
+// warp's row of plane z+1 while it examines plane z), so their latency
+// overlaps the examination and the wait for the next staged plane.
 __device__ __forceinline__ void detect_tiled_tma(const FieldView &P, uint32_t tile_z, const CUtensorMap *map_g,
                                                  uint32_t *tile_next, float *smem_raw, uint32_t *err,
                                                  uint32_t *dnext, uint32_t &distorted) {
     using namespace tile;
+    const GridDev &G = P.G;
+    // the prefetched row: index of the tile row's first vertex (x0, y, z),
+    // this lane's raw bitmap word and codes
+    uint32_t pf_row = 0xffffffffu, pf_ubw = 0, pf_cfw = 0;
     tma_tiles<1>(P, tile_z, map_g, nullptr, tile_next, smem_raw, err,
                  [&](const float *pm, const float *p0, const float *pp, int r, int x0, uint32_t rowbase) {
                      const uint32_t lane = lane_id();
                      const int xl = x0 + 4 * (int)lane;
-                     // the row's uncertified bits and codes of f, both loaded
-                     // up front (coalesced); a vertex's code of f then comes
-                     // from the lane that loaded it
-                     uint32_t nib = 0, cfw = 0;
-                     if (xl < (int)P.G.nx) {
+                     const bool in = xl < (int)G.nx;
+                     // the row's uncertified bits and codes of f (coalesced);
+                     // a vertex's code of f then comes from the lane that
+                     // loaded it
+                     uint32_t ubw = 0, cfw = 0;
+                     if (pf_row == rowbase + (uint32_t)x0) {
+                         ubw = pf_ubw;
+                         cfw = pf_cfw;
+                     } else if (in) {
                          const uint32_t i0 = rowbase + (uint32_t)xl;
-                         nib = (__ldg(&P.ub[i0 >> 5]) >> (i0 & 31u)) & 15u;
+                         ubw = __ldg(&P.ub[i0 >> 5]);
                          cfw = __ldg(reinterpret_cast<const uint32_t *>(P.codes_f + i0));
                      }
+                     // the same tile row of the next plane (a whole grid row
+                     // lies in the grid when its first vertex does)
+                     const uint32_t next = rowbase + G.nxy;
+                     pf_row = next + (uint32_t)x0;
+                     pf_ubw = 0;
+                     pf_cfw = 0;
+                     if (in && next < G.n) {
+                         const uint32_t i1 = next + (uint32_t)xl;
+                         pf_ubw = __ldg(&P.ub[i1 >> 5]);
+                         pf_cfw = __ldg(reinterpret_cast<const uint32_t *>(P.codes_f + i1));
+                     }
+                     const uint32_t nib = in ? (ubw >> ((rowbase + (uint32_t)xl) & 31u)) & 15u : 0u;
                      uint32_t w = nib << (4u * (lane & 7u));
                      w |= __shfl_xor_sync(kFull, w, 1);
                      w |= __shfl_xor_sync(kFull, w, 2);
@@ -950,16 +976,23 @@ __device__ __forceinline__ void mark_closed(const GridDev &G, uint32_t t, uint32
     }
 }
 
-// Eq. 1 on target t of field P (once per sweep); a changed target marks the
-// edited bitmap and, unless the next sweep scans densely, its closed
-// neighbourhood in the next worklist.  Returns whether g_t decreased.
-template <int NDIM>
-__device__ __forceinline__ bool apply_target(const FieldView &P, uint32_t t, bool dense_next, uint32_t *dnext) {
+// Eq. 1 on target t of field P (once per sweep).  Returns whether g_t
+// decreased.
+__device__ __forceinline__ bool edit_target(const FieldView &P, uint32_t t) {
     const float gt = P.g[t];
     const float L = floor_bound(__ldg(&P.f[t]), P.xi);
     float h;
     if (!edit_value(gt, L, P.rule, h)) return false;
     P.g[t] = h;
+    return true;
+}
+
+// Eq. 1 on target t of field P (once per sweep); a changed target marks the
+// edited bitmap and, unless the next sweep scans densely, its closed
+// neighbourhood in the next worklist.  Returns whether g_t decreased.
+template <int NDIM>
+__device__ __forceinline__ bool apply_target(const FieldView &P, uint32_t t, bool dense_next, uint32_t *dnext) {
+    if (!edit_target(P, t)) return false;
     red_or(&P.eb[t >> 5], 1u << (t & 31u));
     if (dense_next) return true;
     mark_closed<NDIM>(P.G, t, dnext);
