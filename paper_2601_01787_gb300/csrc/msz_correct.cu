@@ -385,21 +385,23 @@ static msz_status launch_correct(Problem &P, const DeviceInfo &dev, cudaStream_t
 
 // Default whole-grid detection rule (P.dense_min == 0).  A tiled whole-grid
 // pass (g staged by TMA, or by cp.async on grids the TMA ring cannot stage)
-// costs about one code pass without the certification, and beats the
-// worklist while the worklist is large: measured at 512^3, dense while
-// 6 x distorted >= N/4 takes the peak field from 26.4 to 22.9 ms (TMA) and
-// from 24.5 to 23.6 ms (cp.async), and leaves the Perlin field on worklists.
-// 2D grids keep worklists (their whole-grid walk gathers).
+// costs about one code pass without the certification; the worklist walk,
+// which hands each chunk's vertices to the lanes in index order, is as fast
+// or faster down to the largest worklists: measured at 512^3, dense while
+// 6 x distorted >= N/4, N/16 or N takes the peak field 18.4, 24.2 or 16.2 ms
+// (never dense: 16.3 ms; TMA) and leaves the Perlin field on worklists.  The
+// default is N: the whole-grid pass only when nearly every vertex is on the
+// worklist anyway.  2D grids keep worklists (their whole-grid walk gathers).
 template <int NDIM>
 static msz_status run_correct(Problem &P, const DeviceInfo &dev, cudaStream_t stream) {
     if constexpr (NDIM == 3) {
         if (tma_eligible(P.F) && plane_map(P.F.f, P.F.G, P.map_f) &&
             plane_map(P.F.ginit ? P.F.ginit : P.F.fhat, P.F.G, P.map_s) && plane_map(P.F.g, P.F.G, P.map_g)) {
-            if (P.dense_min == 0) P.dense_min = (long long)(P.F.G.n / 4);
+            if (P.dense_min == 0) P.dense_min = (long long)P.F.G.n;
             return launch_correct<3, true>(P, dev, stream);
         }
     }
-    if (P.dense_min == 0) P.dense_min = NDIM == 3 ? (long long)(P.F.G.n / 4) : -1;
+    if (P.dense_min == 0) P.dense_min = NDIM == 3 ? (long long)P.F.G.n : -1;
     return launch_correct<NDIM, false>(P, dev, stream);
 }
 
