@@ -230,33 +230,49 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
     block_exclusive_scan(all, sm, all);
     if (leader) C->edit_count = all;
     unsigned long long prefix = (unsigned long long)bpre + warp_pre;
-    // each bitmap word is loaded one round ahead: its latency overlaps the
-    // previous round's gathers and stores
-    uint32_t ahead = w0 + lane < w1 ? F.eb[w0 + lane] : 0u;
-    for (uint32_t r = w0; r < w1; r += 32) {
-        const uint32_t w = r + lane;
-        const uint32_t word = ahead;
-        ahead = r + 32u + lane < w1 ? F.eb[r + 32u + lane] : 0u;
-        const uint32_t c = (uint32_t)__popc(word);
-        uint32_t incl = c;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t y = __shfl_up_sync(kFull, incl, d);
-            if (lane >= (uint32_t)d) incl += y;
+    // Rounds of 32 words; a round's edits go to the lanes in index order
+    // (ChunkBits), so its stores coalesce.  Software-pipelined: the words of
+    // round r+2 are loaded and the first 32 edits of round r+1 gathered (g
+    // and fhat) before round r is stored.
+    auto word_at = [&](uint32_t w) -> uint32_t { return w < w1 ? F.eb[w] : 0u; };
+    uint32_t wsoon = word_at(w0 + 32u + lane);
+    ChunkBits nxt(w0, word_at(w0 + lane));
+    bool hn;
+    uint32_t vn;
+    float gn = 0.f, fn = 0.f;
+    nxt.pick(lane, hn, vn);
+    if (hn) {
+        gn = F.g[vn];
+        fn = __ldg(&F.fhat[vn]);
+    }
+    for (uint32_t r = w0; r < w1; r += 32u) {
+        const ChunkBits cur = nxt;
+        const bool hc = hn;
+        const uint32_t vc = vn;
+        const float gc = gn, fc = fn;
+        const uint32_t wr = wsoon;
+        wsoon = word_at(r + 64u + lane);
+        nxt = ChunkBits(r + 32u, wr);
+        nxt.pick(lane, hn, vn);
+        if (hn) {
+            gn = F.g[vn];
+            fn = __ldg(&F.fhat[vn]);
         }
-        unsigned long long pos = prefix + incl - c;
-        uint32_t bits = word;
-        while (bits) {
-            const uint32_t b = (uint32_t)(__ffs(bits) - 1);
-            bits &= bits - 1;
-            const uint32_t i = w * 32u + b;
-            if (pos < P.edit_cap) {
-                P.edit_idx[pos] = i;
-                P.edit_delta[pos] = __fsub_rn(F.g[i], __ldg(&F.fhat[i]));
+        if (hc && prefix + lane < P.edit_cap) {
+            P.edit_idx[prefix + lane] = vc;
+            P.edit_delta[prefix + lane] = __fsub_rn(gc, fc);
+        }
+        for (uint32_t j0 = 32u; j0 < cur.total; j0 += 32u) {
+            bool h;
+            uint32_t v;
+            cur.pick(j0 + lane, h, v);
+            const unsigned long long pos = prefix + j0 + lane;
+            if (h && pos < P.edit_cap) {
+                P.edit_idx[pos] = v;
+                P.edit_delta[pos] = __fsub_rn(F.g[v], __ldg(&F.fhat[v]));
             }
-            ++pos;
         }
-        prefix += __shfl_sync(kFull, incl, 31);
+        prefix += cur.total;
     }
     if (!grid_barrier(&C->bar_count, &C->bar_gen, &C->error)) return;
     if (leader) C->t_end = global_ns();

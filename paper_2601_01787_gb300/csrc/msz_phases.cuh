@@ -104,6 +104,7 @@ struct ChunkBits {
 // fn(has, v) once per round with one set bit of the chunk a lane.
 template <class F>
 __device__ __forceinline__ void chunk_each(uint32_t base, uint32_t bits, F &&fn) {
+    if (!__any_sync(kFull, bits != 0u)) return;
     const ChunkBits cb(base, bits);
     for (uint32_t j0 = 0; j0 < cb.total; j0 += 32u) {
         bool h;
@@ -118,6 +119,7 @@ __device__ __forceinline__ void chunk_each(uint32_t base, uint32_t bits, F &&fn)
 // loads of both in flight at once.
 template <class F>
 __device__ __forceinline__ void chunk_pairs(uint32_t base, uint32_t bits, F &&fn) {
+    if (!__any_sync(kFull, bits != 0u)) return;
     const ChunkBits cb(base, bits);
     for (uint32_t j0 = 0; j0 < cb.total; j0 += 64u) {
         bool h1, h2;
