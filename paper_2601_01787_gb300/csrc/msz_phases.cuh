@@ -76,6 +76,11 @@ struct ChunkBits {
     __device__ __forceinline__ ChunkBits(uint32_t b, uint32_t w) : base(b), bits(w) {
         const uint32_t lane = lane_id();
         cnt = (uint32_t)__popc(w);
+        if (!__any_sync(kFull, w != 0u)) {  // an empty chunk (most, in late sweeps)
+            incl = 0u;
+            total = 0u;
+            return;
+        }
         incl = cnt;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -104,7 +109,6 @@ struct ChunkBits {
 // fn(has, v) once per round with one set bit of the chunk a lane.
 template <class F>
 __device__ __forceinline__ void chunk_each(uint32_t base, uint32_t bits, F &&fn) {
-    if (!__any_sync(kFull, bits != 0u)) return;
     const ChunkBits cb(base, bits);
     for (uint32_t j0 = 0; j0 < cb.total; j0 += 32u) {
         bool h;
@@ -119,7 +123,6 @@ __device__ __forceinline__ void chunk_each(uint32_t base, uint32_t bits, F &&fn)
 // loads of both in flight at once.
 template <class F>
 __device__ __forceinline__ void chunk_pairs(uint32_t base, uint32_t bits, F &&fn) {
-    if (!__any_sync(kFull, bits != 0u)) return;
     const ChunkBits cb(base, bits);
     for (uint32_t j0 = 0; j0 < cb.total; j0 += 64u) {
         bool h1, h2;
