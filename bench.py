@@ -258,16 +258,7 @@ def run_ours(args, ws, rank, local):
     alg = algorithmic_bytes(n, log, first.edit_count, first.stats["uncertified"])
     kernel_ms = statistics.mean(kernel_ns) / 1e6
     achieved = alg / (ms_local * 1e-3) / 1e9
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "k_correct_perlin512_traffic.json")
-    if os.path.exists(tfile):
-        try:
-            with open(tfile) as fh_:
-                tj = json.load(fh_)
-            if tj.get("unit_hash") == api_source_hash():
-                traffic = tj.get("traffic_bytes")
-        except Exception:
-            traffic = None
+    traffic = traffic_record("k_correct_perlin512_traffic.json", "msz_correct.cu")
 
     # the same kernel against the ALU-pipe peak (the pipe that bounds it)
     alu_ops = algorithmic_alu_ops(n, log, first.stats["uncertified"])
@@ -580,7 +571,8 @@ def run_batch(dev, stream, reps: int = 5, sm_mhz: float | None = None) -> dict:
     roof = {"bound": "alu", "kernel": "k_batch", "ops": ops, "achieved": round(ops / t_s / 1e9, 1),
             "peak": round(alu_pk, 1), "unit": "Gop/s", "frac": round(ops / t_s / 1e9 / alu_pk, 4),
             "hbm": {"algorithmic_bytes": nbytes, "achieved": round(nbytes / t_s / 1e9, 1), "peak": peak,
-                    "unit": "GB/s", "frac": round(nbytes / t_s / 1e9 / peak, 4), "peak_kind": peak_kind}}
+                    "unit": "GB/s", "frac": round(nbytes / t_s / 1e9 / peak, 4), "peak_kind": peak_kind,
+                    "traffic": traffic_record("k_batch_perlin64_traffic.json", "msz_batch.cu")}}
     return {"workload": "perlin3d_prequant batch of 64, axes U{64..384}, eb_rel in {1e-3,1e-4,1e-5}, seeds 1000+k",
             "n_vertices": n_tot, "unit": UNIT, "value": round(n_tot / (t_batch * 1e-3) / 1e9, 4),
             "ms": round(t_batch, 4), "graph_replay_ms": round(t_graph, 4),
@@ -789,6 +781,20 @@ def api_source_hash() -> str:
     record applies only while it is unchanged)."""
     from paper_2601_01787_gb300 import _build
     return _build.unit_hash("msz_correct.cu")
+
+
+def traffic_record(name: str, unit: str):
+    """DRAM bytes (read + write) of one launch from the ncu record
+    profiles/<name>, or None unless the record was taken of the kernels
+    translation unit `unit` builds now (same code hash)."""
+    from paper_2601_01787_gb300 import _build
+    path = os.path.join(ROOT, "profiles", name)
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    return rec.get("traffic_bytes") if rec.get("unit_hash") == _build.unit_hash(unit) else None
 
 
 # ------------------------------------------------------------ CPU oracle
