@@ -380,6 +380,105 @@ __device__ __forceinline__ void tile_row(const FieldView &P, const float *pm, co
     distorted += E.distorted;
 }
 
+// The uncertified columns of one warp row, kept in three registers: the
+// lane-distributed word w (lanes 8q .. 8q+7 hold word q: columns 32q ..
+// 32q+31), the running counts of words 0, 0-1 and 0-2 (a byte each) and the
+// total.
+struct RowBits {
+    uint32_t w, counts, total;
+    __device__ __forceinline__ void from(uint32_t word) {
+        w = word;
+        const uint32_t c0 = (uint32_t)__popc(__shfl_sync(kFull, word, 0));
+        const uint32_t c1 = c0 + (uint32_t)__popc(__shfl_sync(kFull, word, 8));
+        const uint32_t c2 = c1 + (uint32_t)__popc(__shfl_sync(kFull, word, 16));
+        total = c2 + (uint32_t)__popc(__shfl_sync(kFull, word, 24));
+        counts = c0 | c1 << 8 | c2 << 16;
+    }
+};
+
+// Which of the 4 words of a row (RowBits::counts) holds its j-th uncertified
+// vertex, and how many come before that word.
+__device__ __forceinline__ void row_word_of(uint32_t counts, uint32_t j, uint32_t &q, uint32_t &before) {
+    const uint32_t c0 = counts & 0xffu, c1 = (counts >> 8) & 0xffu, c2 = counts >> 16;
+    q = j < c0 ? 0u : j < c1 ? 1u : j < c2 ? 2u : 3u;
+    before = q == 0 ? 0u : q == 1 ? c0 : q == 2 ? c1 : c2;
+}
+
+// Certification of one warp row (planes pm / p0 / pp, row r): marks its
+// uncertified vertices in P.ub and returns them as RowBits.  rowbase = the
+// linear index of (0, y, z).
+__device__ __forceinline__ RowBits certify_row(const FieldView &P, const float *pm, const float *p0, const float *pp,
+                                               int r, int x0, uint32_t rowbase) {
+    using namespace tile;
+    const GridDev &G = P.G;
+    const uint32_t lane = lane_id();
+    const int xl = x0 + 4 * (int)lane;
+    const uint32_t cert = cert4(pm, p0, pp, r, lane, P.two_xi);
+    const uint32_t i0 = rowbase + (uint32_t)xl;
+    uint32_t nib = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) nib |= (uint32_t)(xl + e < (int)G.nx && !((cert >> e) & 1u)) << e;
+    uint32_t w = nib << (4u * (lane & 7u));
+    w |= __shfl_xor_sync(kFull, w, 1);
+    w |= __shfl_xor_sync(kFull, w, 2);
+    w |= __shfl_xor_sync(kFull, w, 4);
+    const bool words_ok = ((rowbase + (uint32_t)x0) & 31u) == 0 && x0 + BX <= (int)G.nx;
+    if (words_ok) {
+        if ((lane & 7u) == 0) P.ub[i0 >> 5] = w;
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if ((nib >> e) & 1u) red_or(&P.ub[(i0 + e) >> 5], 1u << ((i0 + e) & 31u));
+    }
+    RowBits b;
+    b.from(w);
+    return b;
+}
+
+// The code pass on two warp rows at once (warp-collective): row r of plane
+// z (staged planes pm / p0 / pp) and, when `two`, of plane z+1 (p0 / pp /
+// pq); the second field soff floats after each plane.  Both rows are
+// certified first; their uncertified vertices then share rounds of 32 (one a
+// lane), so a round's exact codes -- of f, written to codes_f, and, when
+// DETECT, of the second field, compared with it -- serve up to 32 vertices
+// of either row instead of the dozen or so that one row of a smooth field
+// holds.
+template <bool DETECT>
+__device__ __forceinline__ void tile_rows2(const FieldView &P, const float *pm, const float *p0, const float *pp,
+                                           const float *pq, int soff, int r, int x0, uint32_t rowbase, bool two,
+                                           uint32_t &distorted) {
+    const uint32_t lane = lane_id();
+    const uint32_t nxy = P.G.nxy;
+    const RowBits A = certify_row(P, pm, p0, pp, r, x0, rowbase);
+    RowBits B;
+    B.w = B.counts = B.total = 0u;
+    if (two) B = certify_row(P, p0, pp, pq, r, x0, rowbase + nxy);
+    const uint32_t total = A.total + B.total;
+    Emitter E{P.dm[1], 0};
+    for (uint32_t j0 = 0; j0 < total; j0 += 32u) {
+        const uint32_t j = j0 + lane;
+        const bool has = j < total;
+        const bool sec = j >= A.total;  // a vertex of the second row
+        const uint32_t base = (sec ? rowbase + nxy : rowbase) + (uint32_t)x0;
+        // the word of each row the lane's vertex would be in (every lane
+        // shuffles both rows' words), then the one row's column
+        uint32_t qa, ba, qb, bb;
+        row_word_of(A.counts, j, qa, ba);
+        row_word_of(B.counts, j - A.total, qb, bb);
+        const uint32_t wa = __shfl_sync(kFull, A.w, (int)(8u * qa)), wb = __shfl_sync(kFull, B.w, (int)(8u * qb));
+        uint32_t col = 0, cf = 0, cg = 0;
+        if (has) {
+            col = 32u * (sec ? qb : qa) + tile::nth_set(sec ? wb : wa, sec ? j - A.total - bb : j - ba);
+            const float *qm = sec ? p0 : pm, *q0 = sec ? pp : p0, *qp = sec ? pq : pp;
+            cf = tile::code1(qm, q0, qp, r, 4 + (int)col);
+            P.codes_f[base + col] = (uint8_t)cf;
+            if (DETECT) cg = tile::code1(qm + soff, q0 + soff, qp + soff, r, 4 + (int)col);
+        }
+        if (DETECT) report(P, E, has, base + col, cf, cg);
+    }
+    distorted += E.distorted;
+}
+
 // The warp's row of plane p0 in the cp.async ring (row r, x0 .. x0+127, any
 // x extent): bound check and g = start value, 4 vertices a lane.  The
 // second field (fhat, or the start field when DETECT) sits PLANE floats
@@ -702,8 +801,8 @@ __device__ __forceinline__ void first_tiled(const FieldView &P, uint32_t *tile_n
 // slot's mbarrier, and out-of-grid positions arrive as NaN from the maps'
 // fill mode.  Warps never wait for one another inside a tile: each waits only
 // for the planes it needs, and the last warp to finish with a plane refills
-// its slot with the plane NSLOT further on, so fast warps run up to three
-// planes ahead of slow ones.  Every wait is bounded; a wait that runs out
+// its slot with the plane TSLOTS further on, so fast warps run ahead of slow
+// ones by up to the planes in flight.  Every wait is bounded; a wait that runs out
 // records kErrTimeout, stops the block's tiles and, before leaving, waits
 // (bounded) for the block's copies still in flight.
 
@@ -745,10 +844,14 @@ __device__ __forceinline__ void own_row_tma(const FieldView &P, const float *p0,
 
 // The TMA plane ring over the tiles of field P (block-collective): NBOX
 // boxes a plane (maps[0..NBOX-1], each TFIELD floats after the previous one
-// in a slot); row(pm, p0, pp, r, x0, rowbase) runs for every warp row inside
-// the grid with the staged planes z-1, z, z+1.  withhold (a test hook): block
-// 0 never issues its first plane, so its waits run out after kTestWaitNs.
-template <int NBOX, class ROW>
+// in a slot).  STEP 1: row(pm, p0, pp, pq, r, x0, rowbase, two) runs for
+// every warp row inside the grid with the staged planes z-1, z, z+1 (two
+// false, pq unused); STEP 2: once for the rows of planes z and z+1 (two
+// true; rowbase the linear index of (0, y, z)), pq staging plane z+2, or for
+// row z alone (two false) when the tile's last plane is z.  withhold (a test
+// hook): block 0 never issues its first plane, so its waits run out after
+// kTestWaitNs.
+template <int NBOX, int STEP, class ROW>
 __device__ __forceinline__ void tma_tiles(const FieldView &P, uint32_t tile_z, const CUtensorMap *map0,
                                           const CUtensorMap *map1, uint32_t *tile_next, float *smem_raw,
                                           uint32_t *err, ROW &&row, bool withhold = false) {
@@ -757,15 +860,16 @@ __device__ __forceinline__ void tma_tiles(const FieldView &P, uint32_t tile_z, c
     const TileGeom tg = tile_geom(G.nx, G.ny, G.nz, tile_z);
     constexpr uint32_t kWarps = THREADS / 32;
     __shared__ uint32_t s_tile;
-    __shared__ __align__(8) uint64_t s_full[NSLOT];
-    __shared__ uint32_t s_rel[NSLOT];
-    __shared__ uint32_t s_pending[NSLOT];
+    constexpr int NS = TSLOTS;
+    __shared__ __align__(8) uint64_t s_full[NS];
+    __shared__ uint32_t s_rel[NS];
+    __shared__ uint32_t s_pending[NS];
     __shared__ uint32_t s_dead;
     float *ring = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
     __syncthreads();  // the ring's previous users are done with its barriers
     if (tid == 0) {
-        for (int q = 0; q < NSLOT; ++q) {
+        for (int q = 0; q < NS; ++q) {
             tma::mbar_init(tma::smem_u32(&s_full[q]), 1);
             s_rel[q] = 0;
             s_pending[q] = 0;
@@ -790,7 +894,7 @@ __device__ __forceinline__ void tma_tiles(const FieldView &P, uint32_t tile_z, c
         const uint32_t txi = t % tg.tx, tyi = (t / tg.tx) % tg.ty, tzi = t / (tg.tx * tg.ty);
         const int x0 = (int)(txi * BX), y0 = (int)(tyi * BY), zb = (int)(tzi * tg.bz);
         const int ze = min(zb + (int)tg.bz, (int)G.nz);
-        auto slot_of = [&](int p) { return (p - zb + 1) % NSLOT; };
+        auto slot_of = [&](int p) { return (p - zb + 1) % NS; };
         auto issue = [&](int p, int q) {
             const uint32_t bar = tma::smem_u32(&s_full[q]);
             const uint32_t dst = tma::smem_u32(ring + q * TSLOT);
@@ -806,38 +910,45 @@ __device__ __forceinline__ void tma_tiles(const FieldView &P, uint32_t tile_z, c
             if (tid == 0) s_pending[q] = 0;
             return true;
         };
-        // planes zb-1 .. ze; the first NSLOT now, each later one when the
-        // plane NSLOT before it is released
+        // planes zb-1 .. ze; the first NS now, each later one when the plane
+        // NS before it is released
         if (tid == 0) {
             tma::fence_proxy_async();  // the previous tile's reads of the ring come first
-            for (int q = 0; q < NSLOT && zb - 1 + q <= ze; ++q)
+            for (int q = 0; q < NS && zb - 1 + q <= ze; ++q)
                 if (!(withhold && first_tile && blockIdx.x == 0 && q == 0)) issue(zb - 1 + q, q);
         }
         first_tile = false;
+        // this warp is done with plane p: the last warp to say so refills its
+        // slot with plane p + NS
+        auto release = [&](int p) {
+            if (lane == 0) {
+                const int q = slot_of(p);
+                __threadfence_block();
+                if (atomicAdd(&s_rel[q], 1u) == kWarps - 1u) {
+                    s_rel[q] = 0;
+                    __threadfence_block();
+                    if (p + NS <= ze) {
+                        tma::fence_proxy_async();
+                        issue(p + NS, q);
+                    }
+                }
+            }
+        };
         bool alive = wait_plane(zb - 1) && wait_plane(zb);
         const int y = y0 + (int)warp, r = (int)warp + 1;
-        for (int z = zb; alive && z < ze; ++z) {
-            if (!wait_plane(z + 1)) {
+        for (int z = zb; alive && z < ze; z += STEP) {
+            const bool two = STEP == 2 && z + 1 < ze;
+            if (!wait_plane(z + 1) || (two && !wait_plane(z + 2))) {
                 alive = false;
                 break;
             }
             const float *pm = ring + slot_of(z - 1) * TSLOT, *p0 = ring + slot_of(z) * TSLOT;
             const float *pp = ring + slot_of(z + 1) * TSLOT;
-            if (y < (int)G.ny) row(pm, p0, pp, r, x0, (uint32_t)z * G.nxy + (uint32_t)y * G.nx);
-            // this warp is done with plane z-1
+            const float *pq = two ? ring + slot_of(z + 2) * TSLOT : pp;
+            if (y < (int)G.ny) row(pm, p0, pp, pq, r, x0, (uint32_t)z * G.nxy + (uint32_t)y * G.nx, two);
             __syncwarp();
-            if (lane == 0) {
-                const int q = slot_of(z - 1);
-                __threadfence_block();
-                if (atomicAdd(&s_rel[q], 1u) == kWarps - 1u) {
-                    s_rel[q] = 0;
-                    __threadfence_block();
-                    if (z - 1 + NSLOT <= ze) {
-                        tma::fence_proxy_async();
-                        issue(z - 1 + NSLOT, q);
-                    }
-                }
-            }
+            release(z - 1);
+            if (two) release(z);
         }
         if (!alive) {
             atomicOr(err, kErrTimeout);
@@ -847,23 +958,25 @@ __device__ __forceinline__ void tma_tiles(const FieldView &P, uint32_t tile_z, c
     if (s_dead && tid == 0) {
         // copies still in flight land before the block leaves (bounded)
         uint32_t none = 0;
-        for (int q = 0; q < NSLOT; ++q)
+        for (int q = 0; q < NS; ++q)
             if (s_pending[q]) tma::mbar_wait_bounded(tma::smem_u32(&s_full[q]), (ph >> q) & 1u, &none, limit);
     }
 }
 
 // The code pass (sweep 0) on the TMA ring: f and the second field (the start
-// field when DETECT, else fhat) a plane.
+// field when DETECT, else fhat) a plane, two planes a step (tile_rows2).
 template <bool DETECT>
 __device__ __forceinline__ void first_tiled_tma(const FieldView &P, const CUtensorMap *map_f, const CUtensorMap *map_s,
                                                 uint32_t *tile_next, float *smem_raw, uint32_t *err,
                                                 uint32_t &distorted, bool withhold = false) {
     bool bad = false;
-    tma_tiles<2>(
+    tma_tiles<2, 2>(
         P, P.tile_z, map_f, map_s, tile_next, smem_raw, err,
-        [&](const float *pm, const float *p0, const float *pp, int r, int x0, uint32_t rowbase) {
+        [&](const float *pm, const float *p0, const float *pp, const float *pq, int r, int x0, uint32_t rowbase,
+            bool two) {
             own_row_tma<DETECT>(P, p0, r, x0, rowbase, bad);
-            tile_row<DETECT>(P, pm, p0, pp, tile::TFIELD, r, x0, rowbase, distorted);
+            if (two) own_row_tma<DETECT>(P, pp, r, x0, rowbase + P.G.nxy, bad);
+            tile_rows2<DETECT>(P, pm, p0, pp, pq, tile::TFIELD, r, x0, rowbase, two, distorted);
         },
         withhold);
     if (bad) atomicOr(err, kErrInput);
@@ -885,8 +998,9 @@ __device__ __forceinline__ void detect_tiled_tma(const FieldView &P, uint32_t ti
     // the prefetched row: index of the tile row's first vertex (x0, y, z),
     // this lane's raw bitmap word and codes
     uint32_t pf_row = 0xffffffffu, pf_ubw = 0, pf_cfw = 0;
-    tma_tiles<1>(P, tile_z, map_g, nullptr, tile_next, smem_raw, err,
-                 [&](const float *pm, const float *p0, const float *pp, int r, int x0, uint32_t rowbase) {
+    tma_tiles<1, 1>(P, tile_z, map_g, nullptr, tile_next, smem_raw, err,
+                    [&](const float *pm, const float *p0, const float *pp, const float *, int r, int x0,
+                        uint32_t rowbase, bool) {
                      const uint32_t lane = lane_id();
                      const int xl = x0 + 4 * (int)lane;
                      const bool in = xl < (int)G.nx;

@@ -56,7 +56,12 @@ constexpr int TBOX = ROWS * PW;                                  // 1360 floats
 constexpr int TFIELD = 1376;                                     // 5504 bytes
 constexpr int TSLOT = 2 * TFIELD;
 constexpr uint32_t kTboxBytes = (uint32_t)TBOX * sizeof(float);  // 5440
-constexpr size_t kTmaRingBytes = (size_t)NSLOT * TSLOT * sizeof(float) + 128;  // + alignment slack
+// slots of the TMA ring: the code pass takes two planes a step (rows z and
+// z+1 use planes z-1 .. z+2) with one more in flight (a sixth slot measured
+// slower: the larger ring leaves less of the SM's memory to L1, which the
+// gathering phases of the loop need)
+constexpr int TSLOTS = 5;
+constexpr size_t kTmaRingBytes = (size_t)TSLOTS * TSLOT * sizeof(float) + 128;  // + alignment slack
 static_assert(TFIELD >= TBOX && (TFIELD * 4) % 128 == 0, "TMA boxes must start on 128-byte boundaries");
 
 struct TileGeom {
