@@ -104,9 +104,9 @@ typedef struct {
                                  time in ns from the start of the correction kernel to the
                                  end of sweep k's detection and of its edit phase (-1: none) */
     int32_t tile_z;           /* z-planes per tile of the code pass (3D); at most 1024; 0: the
-                                 deepest of 32, 16, 8 that gives every block of the persistent
+                                 deepest of 24, 16, 8 that gives every block of the persistent
                                  grid two tiles (msz_correct; the batch and relaxed entry points
-                                 use 32).  Affects speed only (see the autotuner), never results */
+                                 use 24).  Affects speed only (see the autotuner), never results */
     int32_t local_cap;        /* msz_correct_relaxed: local sweeps per tile run; 0: 65536 */
 } msz_options;
 

@@ -339,11 +339,12 @@ static msz_status correct_blocks(const DeviceInfo &d, int &blocks) {
     return MSZ_OK;
 }
 
-// Default planes per tile of the code pass: the deepest of 32, 16, 8 that
-// still gives every block of the persistent grid two tiles or more (deeper
-// tiles re-read fewer halo planes; more tiles balance the blocks' work).
+// Default planes per tile of the code pass: the deepest of kTileZ (24), 16,
+// 8 that still gives every block of the persistent grid two tiles or more
+// (deeper tiles re-read fewer halo planes; more tiles balance the blocks'
+// work).
 static uint32_t default_tile_z(const GridDev &G, int blocks) {
-    for (uint32_t tz = kTileZ; tz > 8; tz /= 2)
+    for (const uint32_t tz : {kTileZ, 16u})
         if ((uint64_t)tile::tile_geom(G.nx, G.ny, G.nz, tz).count >= 2ull * (uint64_t)blocks) return tz;
     return 8;
 }

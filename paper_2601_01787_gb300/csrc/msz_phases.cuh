@@ -18,7 +18,9 @@
 
 namespace msz {
 
-constexpr uint32_t kTileZ = 32;  // default planes per tile of the code pass
+// default planes per tile of the code pass (512^3 Perlin field, two planes a
+// step: 8, 16, 24, 32, 48, 64 -> 1.548, 1.551, 1.541, 1.574, 1.550, 1.658 ms)
+constexpr uint32_t kTileZ = 24;
 #ifndef MSZ_WALK_AHEAD
 #define MSZ_WALK_AHEAD 4
 #endif
