@@ -322,7 +322,8 @@ __device__ void first_generic(const FieldView &P, uint32_t *err) {
     if (bad) atomicOr(err, kErrInput);
 }
 
-// One warp row of the code pass (warp-collective): row r (1 .. BY) of the
+// One warp row of the code pass on the cp.async ring (warp-collective; the
+// TMA ring takes two rows at once, tile_rows2): row r (1 .. BY) of the
 // planes pm / p0 / pp staged at pitch PW (column c <-> x = x0 - 4 + c), the
 // second field soff floats after each plane; rowbase = the linear index of
 // (0, y, z).  Certifies the row's 128 vertices, marks the uncertified ones in
