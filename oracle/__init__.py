@@ -39,35 +39,39 @@ def build(force: bool = False) -> str:
     return _OUT
 
 
+def _configure(lib):
+    """Declare the argument and result types of the oracle's C functions."""
+    P, I64, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    lib.orc_neighbour.argtypes = [I, I64, I64, I64, I64, I, ctypes.POINTER(I64)]
+    lib.orc_neighbour.restype = I
+    lib.orc_code_at.argtypes = [P, I, I64, I64, I64, I64]
+    lib.orc_code_at.restype = ctypes.c_uint8
+    lib.orc_codes.argtypes = [P, I, I64, I64, I64, P]
+    lib.orc_floor.argtypes = [ctypes.c_float, ctypes.c_float]
+    lib.orc_floor.restype = ctypes.c_float
+    lib.orc_ceil.argtypes = [ctypes.c_float, ctypes.c_float]
+    lib.orc_ceil.restype = ctypes.c_float
+    lib.orc_validate.argtypes = [P, P, I64, ctypes.c_float]
+    lib.orc_validate.restype = I
+    lib.orc_edit.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.c_float, I]
+    lib.orc_edit.restype = I
+    lib.orc_correct.argtypes = [P, P, ctypes.c_float, I, I64, I64, I64, I, I, I64, P, P,
+                                P, P, I64, ctypes.POINTER(I64), P, P, I64]
+    lib.orc_correct.restype = I
+    lib.orc_correct_relaxed.argtypes = [P, P, ctypes.c_float, I, I64, I64, I64, I64, I64, I64, I, I64,
+                                        I64, P, P]
+    lib.orc_correct_relaxed.restype = I
+    lib.orc_labels.argtypes = [P, I, I64, I64, I64, P, P]
+    lib.orc_labels.restype = I
+    lib.orc_compare.argtypes = [P, P, P, P, P, P, I64, P]
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            P, I64, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
-            lib.orc_neighbour.argtypes = [I, I64, I64, I64, I64, I, ctypes.POINTER(I64)]
-            lib.orc_neighbour.restype = I
-            lib.orc_code_at.argtypes = [P, I, I64, I64, I64, I64]
-            lib.orc_code_at.restype = ctypes.c_uint8
-            lib.orc_codes.argtypes = [P, I, I64, I64, I64, P]
-            lib.orc_floor.argtypes = [ctypes.c_float, ctypes.c_float]
-            lib.orc_floor.restype = ctypes.c_float
-            lib.orc_ceil.argtypes = [ctypes.c_float, ctypes.c_float]
-            lib.orc_ceil.restype = ctypes.c_float
-            lib.orc_validate.argtypes = [P, P, I64, ctypes.c_float]
-            lib.orc_validate.restype = I
-            lib.orc_edit.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.c_float, I]
-            lib.orc_edit.restype = I
-            lib.orc_correct.argtypes = [P, P, ctypes.c_float, I, I64, I64, I64, I, I, I64, P, P,
-                                        P, P, I64, ctypes.POINTER(I64), P, P, I64]
-            lib.orc_correct_relaxed.argtypes = [P, P, ctypes.c_float, I, I64, I64, I64, I64, I64, I64, I, I64,
-                                                I64, P, P]
-            lib.orc_correct_relaxed.restype = I
-            lib.orc_correct.restype = I
-            lib.orc_labels.argtypes = [P, I, I64, I64, I64, P, P]
-            lib.orc_labels.restype = I
-            lib.orc_compare.argtypes = [P, P, P, P, P, P, I64, P]
-            _lib = lib
+            _lib = _configure(ctypes.CDLL(build()))
     return _lib
 
 

@@ -155,9 +155,8 @@ def test_random_tiny_grids_converge_with_invariants():
         fhat = (f.astype(np.float64) + noise).astype(np.float32)
         assert oracle.validate(f, fhat, xi) == oracle.OK
         r = oracle.correct(f, fhat, xi)
-        assert r.status in (oracle.OK, oracle.STUCK)
-        if r.status == oracle.OK:
-            assert np.array_equal(bf.brute_codes(r.g), bf.brute_codes(f))
+        assert r.status == oracle.OK  # floors of values 1/8 apart never collapse
+        assert np.array_equal(bf.brute_codes(r.g), bf.brute_codes(f))
         d = oracle.correct(f, fhat, xi, worklist=False)
         assert d.status == r.status and np.array_equal(d.g.view(np.uint32), r.g.view(np.uint32))
 
