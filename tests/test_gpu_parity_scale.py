@@ -1,0 +1,149 @@
+"""Bit-exact parity with the CPU oracle at the sizes the kernels run at.
+
+The correction kernel is one persistent cooperative grid of (resident blocks
+per SM) x 152 blocks that take code-pass tiles of 128 x 8 x tile_z vertices
+from an atomic counter.  At these sizes every block takes several tiles, so
+these cases reach what the small cases of test_gpu_parity.py cannot: reuse of
+the staging ring across tiles, the tile-counter hand-off, the default tile
+depth and the TMA whole-grid detection at full size.  Each case compares,
+element by element with the oracle's whole correction (Sec. III-B loop,
+Eq. 1, synchronous sweeps):
+
+- the corrected field g, bit for bit;
+- the sorted edit list (index and delta, bit for bit);
+- the per-sweep log (distorted vertices, distinct targets, changed values;
+  the worklist sizes too where the GPU keeps worklists only);
+- the counts (sweeps, edits, edited vertices, first and last distortions).
+
+The oracle runs in spawn-started worker processes (tests/oracle_pool.py),
+several fields at once, while the GPU corrections run here.
+"""
+import numpy as np
+import pytest
+import torch
+
+from tests import oracle_pool
+
+pytestmark = pytest.mark.gpu
+
+PERLIN_256 = ("perlin", dict(shape=(256, 256, 256), seed=21, eb_rel=1e-4))
+PEAKS_256 = ("peaks", dict(shape=(256, 256, 256), seed=22, eb_rel=1e-4))
+PERLIN_512 = ("perlin", dict(shape=(512, 512, 512), seed=2, eb_rel=1e-4))  # the bench workload
+BATCH = 64
+
+
+@pytest.fixture(scope="module")
+def api():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2601_01787_gb300 import api as a
+    a.load()
+    return a
+
+
+@pytest.fixture(scope="module")
+def refs():
+    """Every oracle job of this module, submitted at once."""
+    pool = oracle_pool.Pool()
+    jobs = {"perlin256": pool.submit(PERLIN_256), "peaks256": pool.submit(PEAKS_256),
+            "perlin512": pool.submit(PERLIN_512)}
+    for k in range(BATCH):
+        jobs[("batch", k)] = pool.submit(("batch", k))
+    yield jobs
+    pool.close()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def bits(t):
+    a = t.detach().cpu().numpy() if isinstance(t, torch.Tensor) else t
+    return np.ascontiguousarray(a).view(np.uint32).reshape(-1)
+
+
+def check(res, ref, worklist_column=False):
+    assert res.status == ref.status
+    got, want = bits(res.out), bits(ref.g)
+    bad = np.flatnonzero(got != want)
+    assert bad.size == 0, f"{bad.size} values differ, first at {bad[:8].tolist()}"
+    assert res.edit_count == ref.edit_count
+    assert np.array_equal(res.edit_idx.cpu().numpy().view(np.uint32), ref.edit_idx)
+    assert np.array_equal(bits(res.edit_delta), bits(ref.edit_delta))
+    st = res.stats
+    assert (st["sweeps"], st["edits"], st["edited"], st["first_distorted"], st["left"]) == \
+        (ref.sweeps, ref.edits, ref.edited, ref.first_distorted, ref.left)
+    assert np.array_equal(res.sweep_log[:, 1:], ref.sweep_log[:, 1:])
+    if worklist_column:
+        assert np.array_equal(res.sweep_log[:, 0], ref.sweep_log[:, 0])
+        assert st["examined"] == ref.examined
+
+
+def _correct(api, spec, **kw):
+    fl = oracle_pool.make_field(spec)
+    return fl, api.correct(dev(fl.f), dev(fl.fhat), fl.xi, log_capacity=100000, **kw)
+
+
+# 256^3 Perlin: at the default depth (16 planes) the code pass has
+# 2 x 32 x 16 = 1,024 tiles for the 456 blocks; at 8 planes 2,048.
+@pytest.mark.parametrize("kw", [dict(), dict(tile_z=8), dict(tile_z=24), dict(dense_min_items=1)],
+                         ids=["default", "tile_z8", "tile_z24", "always_dense"])
+def test_perlin256_bit_exact(api, refs, kw):
+    fl, res = _correct(api, PERLIN_256, **kw)
+    check(res, refs["perlin256"].result())
+
+
+def test_perlin256_worklist_only_bit_exact(api, refs):
+    fl, res = _correct(api, PERLIN_256, dense_min_items=-1)
+    check(res, refs["perlin256"].result(), worklist_column=True)
+    assert res.stats["dense_sweeps"] == 1
+
+
+# 256^3 peak field: tens of sweeps; with dense_min_items=1 every sweep after
+# the first is the TMA whole-grid detection over the whole grid.
+@pytest.mark.parametrize("kw", [dict(), dict(dense_min_items=1), dict(dense_min_items=256 ** 3 // 16),
+                                dict(dense_min_items=-1)],
+                         ids=["default", "always_dense", "mixed", "worklist_only"])
+def test_peaks256_bit_exact(api, refs, kw):
+    fl, res = _correct(api, PEAKS_256, **kw)
+    ref = refs["peaks256"].result()
+    assert ref.sweeps > 10
+    check(res, ref, worklist_column=kw.get("dense_min_items") == -1)
+    if kw.get("dense_min_items") == 1:
+        assert res.stats["dense_sweeps"] == res.stats["sweeps"] + 1
+
+
+def test_perlin512_bench_launch_bit_exact(api, refs):
+    """The 512^3 prequantized Perlin field in the launch configuration the
+    benchmark times: default options, an edit capacity of N/4 and a reused
+    workspace."""
+    fl = oracle_pool.make_field(PERLIN_512)
+    f, fh = dev(fl.f), dev(fl.fhat)
+    cap = fl.n // 4
+    out = torch.empty_like(f)
+    eidx = torch.empty(cap, dtype=torch.int32, device=f.device)
+    edel = torch.empty(cap, dtype=torch.float32, device=f.device)
+    ws = api.workspace(api.workspace_size(f.shape), f.device)
+    for _ in range(2):  # the second call runs on the first call's workspace contents
+        res = api.correct(f, fh, fl.xi, out=out, edit_idx=eidx, edit_delta=edel, edit_capacity=cap, ws=ws,
+                          log_capacity=100000)
+        check(res, refs["perlin512"].result())
+
+
+def test_batch64_every_field_bit_exact(api, refs):
+    """The 64-field uneven batch (axes 64..384, eb_rel in {1e-3, 1e-4, 1e-5})
+    in one persistent launch with the autotuner's tile depths, as the
+    benchmark runs it: every field against the oracle's own correction."""
+    from paper_2601_01787_gb300 import autotune, synth
+    shapes = synth.batch_shapes(BATCH)
+    fields = [oracle_pool.make_field(("batch", k)) for k in range(BATCH)]
+    assert [fl.shape for fl in fields] == [s for s, _, _ in shapes]
+    fs = [dev(fl.f) for fl in fields]
+    fhs = [dev(fl.fhat) for fl in fields]
+    caps = [fl.n // 4 for fl in fields]
+    tz = autotune.tile_z_for([fl.shape for fl in fields], tune_missing=False)
+    res = api.correct_batch(fs, fhs, [fl.xi for fl in fields], edit_capacities=caps, tile_z=tz,
+                            log_capacity=4096)
+    assert res.status == api.OK
+    del fs, fhs
+    for k, r in enumerate(res.fields):
+        check(r, refs[("batch", k)].result())
