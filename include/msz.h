@@ -420,9 +420,10 @@ msz_status msz_correct_relaxed(const float *d_f, const float *d_fhat, float xi, 
  * about 8.0 MB compiled into the library, held by every GPU that loads it until
  * the process exits.  Grids of more than MSZ_STATIC_MAX_VERTICES vertices are
  * rejected with MSZ_ERR_WORKSPACE.  Arguments, results and synchronization are
- * those of msz_correct.  The first call on a device looks up the array's device
- * address (make that call before any stream capture).  Every call shares the
- * array: calls that overlap on the GPU race, so serialize them. */
+ * those of msz_correct.  Each call looks up the array's device address on the
+ * current device (the first call on a device loads the library's module there;
+ * make that call before any stream capture).  Every call shares the array:
+ * calls that overlap on the GPU race, so serialize them. */
 #define MSZ_STATIC_MAX_VERTICES 4194304LL
 msz_status msz_correct_static(const float *d_f, const float *d_fhat, float xi, msz_grid grid, float *d_out,
                               uint32_t *d_edit_idx, float *d_edit_delta, int64_t edit_capacity,

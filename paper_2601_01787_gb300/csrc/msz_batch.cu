@@ -414,10 +414,13 @@ std::mutex g_batch_mu;
 msz_status batch_blocks(const DeviceInfo &d, int &blocks) {
     static int cache[64];
     std::lock_guard<std::mutex> lk(g_batch_mu);
+    const size_t sm = tile::kRingBytes;
+    // the attribute belongs to the current context, so it is set on every
+    // call (a context re-created after cudaDeviceReset starts without it);
+    // the occupancy it allows is a property of the device and is cached
+    if (cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+        return MSZ_ERR_CUDA;
     if (!cache[d.device]) {
-        const size_t sm = tile::kRingBytes;
-        if (cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
-            return MSZ_ERR_CUDA;
         int per = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch, kThreads, sm) != cudaSuccess)
             return MSZ_ERR_CUDA;

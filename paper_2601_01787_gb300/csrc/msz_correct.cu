@@ -321,12 +321,15 @@ template <int NDIM, bool TMA>
 static msz_status correct_blocks(const DeviceInfo &d, int &blocks) {
     static int cache[64];
     std::lock_guard<std::mutex> lk(g_mu);
+    const size_t sm = correct_smem<NDIM, TMA>();
+    // the attribute belongs to the current context, so it is set on every
+    // call (a context re-created after cudaDeviceReset starts without it);
+    // the occupancy it allows is a property of the device and is cached
+    if (sm > 48 * 1024 &&
+        cudaFuncSetAttribute(k_correct<NDIM, TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+            cudaSuccess)
+        return MSZ_ERR_CUDA;
     if (!cache[d.device]) {
-        const size_t sm = correct_smem<NDIM, TMA>();
-        if (sm > 48 * 1024 &&
-            cudaFuncSetAttribute(k_correct<NDIM, TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
-                cudaSuccess)
-            return MSZ_ERR_CUDA;
         int per = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_correct<NDIM, TMA>, kThreads, sm) != cudaSuccess)
             return MSZ_ERR_CUDA;
@@ -805,15 +808,12 @@ static msz_status pipeline_submit(msz_pipeline *pl, const float *h_f, const floa
     return MSZ_OK;
 }
 
-// Waits for the oldest field: its status, edit count, stats and (encoded)
-// stream length; its host results are complete on return.
-static msz_status pipeline_collect(msz_pipeline *pl, int64_t *h_edit_count, size_t *h_stream_bytes,
+// The results of dequeued slot k: status, edit count, stats, (encoded) stream
+// length, and the downloads whose length is known only now, queued behind
+// the field's own download.
+static msz_status pipeline_results(msz_pipeline *pl, int k, int64_t *h_edit_count, size_t *h_stream_bytes,
                                    msz_stats *h_stats) {
-    if (pl->pending == 0) return MSZ_ERR_INVALID_ARG;
-    const int k = pl->tail;
     msz_pipeline::Slot &sl = pl->slot[k];
-    pl->tail ^= 1;
-    pl->pending -= 1;
     if (cudaEventSynchronize(sl.comp_done) != cudaSuccess) return MSZ_ERR_CUDA;
     int64_t count = 0;
     msz_status st = finish_correct(pl->h_ctrl[k], pl->h_rec[k], pl->cap, &count, h_stats);
@@ -845,7 +845,20 @@ static msz_status pipeline_collect(msz_pipeline *pl, int64_t *h_edit_count, size
                 return MSZ_ERR_CUDA;
         }
     }
-    if (cudaEventSynchronize(sl.out_done) != cudaSuccess) return MSZ_ERR_CUDA;
+    return st;
+}
+
+// Waits for the oldest field: its status, edit count, stats and (encoded)
+// stream length.  Its host buffers are complete, and no copy into them is
+// still in flight, on every return, errors included.
+static msz_status pipeline_collect(msz_pipeline *pl, int64_t *h_edit_count, size_t *h_stream_bytes,
+                                   msz_stats *h_stats) {
+    if (pl->pending == 0) return MSZ_ERR_INVALID_ARG;
+    const int k = pl->tail;
+    pl->tail ^= 1;
+    pl->pending -= 1;
+    msz_status st = pipeline_results(pl, k, h_edit_count, h_stream_bytes, h_stats);
+    if (cudaEventSynchronize(pl->slot[k].out_done) != cudaSuccess && st == MSZ_OK) st = MSZ_ERR_CUDA;
     return st;
 }
 }  // namespace msz

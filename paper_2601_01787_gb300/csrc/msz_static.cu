@@ -16,8 +16,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <mutex>
-
 #include "msz.h"
 #include "msz_workspace.h"
 
@@ -27,21 +25,15 @@ constexpr size_t kStaticBytes = msz::layout_for((uint64_t)MSZ_STATIC_MAX_VERTICE
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
-std::mutex g_static_mu;
-void *g_static_ptr[64];  // device address of the array, per device (host code cannot use its name)
-
-// Looks up the array's device address once per device, with that device current.
+// The array's device address, looked up on every call with the caller's
+// device current (host code cannot use the array's name as a device address).
+// The lookup is cheap once the module is loaded, and a cached address would go
+// stale if the context were torn down and re-created (cudaDeviceReset), which
+// reloads the module at a possibly different address.
 msz_status static_scratch(void **out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return MSZ_ERR_CUDA;
-    if (dev < 0 || dev >= 64) return MSZ_ERR_UNSUPPORTED;
-    std::lock_guard<std::mutex> lk(g_static_mu);
-    if (!g_static_ptr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return MSZ_ERR_CUDA;
-        g_static_ptr[dev] = p;
-    }
-    *out = g_static_ptr[dev];
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return MSZ_ERR_CUDA;
+    *out = p;
     return MSZ_OK;
 }
 
