@@ -24,7 +24,7 @@ _lib = None
 
 SELF = 15
 OK, ERR_INVALID_ARG, ERR_INPUT_BOUND, ERR_CAPACITY, ERR_OOM, ERR_MAX_SWEEPS, STUCK = 0, 1, 2, 3, 4, 6, 8
-RULE_HALVE, RULE_SNAP = 0, 1
+RULE_HALVE, RULE_SNAP, RULE_BELOW = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
@@ -55,6 +55,8 @@ def _configure(lib):
     lib.orc_validate.restype = I
     lib.orc_edit.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.c_float, I]
     lib.orc_edit.restype = I
+    lib.orc_edit_below.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.c_float, ctypes.c_float]
+    lib.orc_edit_below.restype = I
     lib.orc_correct.argtypes = [P, P, ctypes.c_float, I, I64, I64, I64, I, I, I64, P, P,
                                 P, P, I64, ctypes.POINTER(I64), P, P, I64]
     lib.orc_correct.restype = I
@@ -135,6 +137,13 @@ def edit(g: float, L: float, rule: int = RULE_HALVE):
     """One application of Eq. 1: returns (new g, changed)."""
     c = ctypes.c_float(np.float32(g))
     ch = _load().orc_edit(ctypes.byref(c), np.float32(L), rule)
+    return np.float32(c.value), bool(ch)
+
+
+def edit_below(g: float, L: float, cand: float):
+    """One BELOW-REFERENCE edit towards the candidate value: (new g, changed)."""
+    c = ctypes.c_float(np.float32(g))
+    ch = _load().orc_edit_below(ctypes.byref(c), np.float32(L), np.float32(cand))
     return np.float32(c.value), bool(ch)
 
 

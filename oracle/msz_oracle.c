@@ -15,9 +15,11 @@
  *               the grid; distinct values made concrete by an index tie-break;
  *               extrema; steepest neighbours n_min(i), n_max(i) (Sec. IV-A).
  *   Eq. 1       the edit g <- max(g - delta, f - xi), with the HALVE choice of
- *               delta (the paper leaves delta open) or SNAP (delta large
+ *               delta (the paper leaves delta open), SNAP (delta large
  *               enough to reach the floor, as Fig. "nonextrema"(c) drops 0.1
- *               to 0).
+ *               to 0) or BELOW-REFERENCE (Sec. IV-A: the offending vertex
+ *               drops "to 0.3 or slightly below", just under the vertex it
+ *               must fall below).
  *   Sec. III-B  C-loop extremum rules (FPmax spelled out, the other three
  *   Sec. IV-A   follow the same non-increasing logic) and the local-ordering
  *               rules for the descending and ascending directions.
@@ -66,7 +68,7 @@ enum {
     ORC_STUCK = 8
 };
 
-enum { ORC_RULE_HALVE = 0, ORC_RULE_SNAP = 1 };
+enum { ORC_RULE_HALVE = 0, ORC_RULE_SNAP = 1, ORC_RULE_BELOW = 2 };
 
 /* ---------------------------------------------------------------------------
  * Sec. III-A: the grid, its triangulation and the neighbourhood N(i).
@@ -230,6 +232,62 @@ static int targets_of(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_t i,
     return k;
 }
 
+/* The vertex each target of i must end up below (BELOW-REFERENCE only), in
+ * the order targets_of writes the targets.  Ascending mismatch: the target
+ * (i itself for FPmax, else g's largest neighbour) must fall below the vertex
+ * that f makes i's steepest ascent (i itself for FNmax): in Fig. nonextrema
+ * (d)-(f) the spurious 0.4 falls below the 0.3 of n_max(i).  Descending
+ * mismatch: the target (i itself for FNmin, else f's smallest neighbour) must
+ * fall below the vertex that g makes i's steepest descent (i itself for FPmin):
+ * in Fig. nonextrema (a)-(c) the original minimum 0.1 falls below the spurious
+ * 0.08. */
+static int references_of(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_t i,
+                         uint8_t cf, uint8_t cg, int64_t r[2])
+{
+    int k = 0;
+    int asc_f = cf & 15, asc_g = cg & 15, desc_f = cf >> 4, desc_g = cg >> 4;
+    int64_t j;
+    if (asc_g != asc_f) {
+        if (asc_f == ORC_SELF) r[k++] = i;
+        else if (orc_neighbour(ndim, nx, ny, nz, i, asc_f, &j)) r[k++] = j;
+    }
+    if (desc_g != desc_f) {
+        if (desc_g == ORC_SELF) r[k++] = i;
+        else if (orc_neighbour(ndim, nx, ny, nz, i, desc_g, &j)) r[k++] = j;
+    }
+    return k;
+}
+
+/* BELOW-REFERENCE (Sec. IV-A: decrease the offender "to 0.3 or slightly
+ * below"): the largest value that puts target t below reference r, whose
+ * current value is vr, in the order of Sec. III-A -- vr itself when r has the
+ * larger index (the tie is then broken in r's favour), else the next float
+ * below vr. */
+static float below_value(int64_t t, int64_t r, float vr)
+{
+    return r > t ? vr : nextafterf(vr, -INFINITY);
+}
+
+/* IEEE totalOrder key of a float: unsigned comparison of keys orders the
+ * floats, with -0 below +0. */
+static uint32_t total_key(float v)
+{
+    uint32_t b;
+    memcpy(&b, &v, 4);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+/* One BELOW-REFERENCE edit: g moves to the candidate c (the smallest, in
+ * totalOrder, of the values its requests ask for in this sweep), kept at or
+ * above the floor L.  Returns 1 when g decreased, 0 when g was at its floor. */
+int orc_edit_below(float *g, float L, float c)
+{
+    float h = c < L ? L : c;
+    if (!(h < *g)) return 0;
+    *g = h;
+    return 1;
+}
+
 /* ---------------------------------------------------------------------------
  * The correction loop (Sec. III-B iterative strategy, redesigned C-loop of
  * Sec. IV-A, synchronous sweeps).  Sweep k:
@@ -265,7 +323,8 @@ int orc_correct(const float *f, const float *fhat, float xi,
                 int64_t *stats, int64_t *sweep_log, int64_t log_capacity)
 {
     if (!f || !fhat || !g || nx < 1 || ny < 1 || nz < 1 || (ndim != 2 && ndim != 3) ||
-        (ndim == 2 && nz != 1) || max_sweeps < 0 || (rule != ORC_RULE_HALVE && rule != ORC_RULE_SNAP))
+        (ndim == 2 && nz != 1) || max_sweeps < 0 ||
+        (rule != ORC_RULE_HALVE && rule != ORC_RULE_SNAP && rule != ORC_RULE_BELOW))
         return ORC_ERR_INVALID_ARG;
     int64_t n = nx * ny * nz;
     int st = orc_validate(f, fhat, n, xi);
@@ -283,8 +342,10 @@ int orc_correct(const float *f, const float *fhat, float xi,
     int64_t *wl = malloc(sizeof(int64_t) * (size_t)n);
     int64_t *wl_next = malloc(sizeof(int64_t) * (size_t)n);
     float *L = malloc(sizeof(float) * (size_t)n);
-    if (!cf || !is_target || !in_next || !tlist || !wl || !wl_next || !L) {
-        free(cf); free(is_target); free(in_next); free(tlist); free(wl); free(wl_next); free(L);
+    /* BELOW-REFERENCE: per target, the smallest value its requests ask for */
+    float *cand = rule == ORC_RULE_BELOW ? malloc(sizeof(float) * (size_t)n) : NULL;
+    if (!cf || !is_target || !in_next || !tlist || !wl || !wl_next || !L || (rule == ORC_RULE_BELOW && !cand)) {
+        free(cf); free(is_target); free(in_next); free(tlist); free(wl); free(wl_next); free(L); free(cand);
         return ORC_ERR_OOM;
     }
 
@@ -310,10 +371,19 @@ int orc_correct(const float *f, const float *fhat, float xi,
             uint8_t cg = orc_code_at(g, ndim, nx, ny, nz, i);
             if (cg == cf[i]) continue;
             ++distorted;
-            int64_t t[2];
+            int64_t t[2], r[2];
             int m = targets_of(ndim, nx, ny, nz, i, cf[i], cg, t);
-            for (int q = 0; q < m; ++q)
-                if (!is_target[t[q]]) { is_target[t[q]] = 1; tlist[nt++] = t[q]; }
+            if (rule == ORC_RULE_BELOW) references_of(ndim, nx, ny, nz, i, cf[i], cg, r);
+            for (int q = 0; q < m; ++q) {
+                float c = rule == ORC_RULE_BELOW ? below_value(t[q], r[q], g[r[q]]) : 0.0f;
+                if (!is_target[t[q]]) {
+                    is_target[t[q]] = 1;
+                    tlist[nt++] = t[q];
+                    if (cand) cand[t[q]] = c;
+                } else if (cand && total_key(c) < total_key(cand[t[q]])) {
+                    cand[t[q]] = c;  /* conflicting requests: the minimum (Sec. IV-B) */
+                }
+            }
             if (use_worklist && !in_next[i]) { in_next[i] = 1; wl_next[nn++] = i; }
         }
         if (k == 0) first_distorted = distorted;
@@ -343,7 +413,8 @@ int orc_correct(const float *f, const float *fhat, float xi,
         for (int64_t q = 0; q < nt; ++q) {
             int64_t t = tlist[q];
             is_target[t] = 0;
-            if (!orc_edit(&g[t], L[t], rule)) continue;
+            if (rule == ORC_RULE_BELOW ? !orc_edit_below(&g[t], L[t], cand[t]) : !orc_edit(&g[t], L[t], rule))
+                continue;
             ++changed;
             if (use_worklist) {
                 if (!in_next[t]) { in_next[t] = 1; wl_next[nn++] = t; }
@@ -394,7 +465,7 @@ int orc_correct(const float *f, const float *fhat, float xi,
         stats[0] = sweeps; stats[1] = edits; stats[2] = ne; stats[3] = first_distorted;
         stats[4] = left; stats[5] = examined; stats[6] = status; stats[7] = 0;
     }
-    free(cf); free(is_target); free(in_next); free(tlist); free(wl); free(wl_next); free(L);
+    free(cf); free(is_target); free(in_next); free(tlist); free(wl); free(wl_next); free(L); free(cand);
     if (status == ORC_OK && ne > edit_capacity) return ORC_ERR_CAPACITY;
     return status;
 }
@@ -423,15 +494,6 @@ int orc_correct(const float *f, const float *fhat, float xi,
  * [3] distorted vertices in iteration 0, [4] distorted vertices left, [5] tile
  * runs, [6] status, [7] 0.
  * ------------------------------------------------------------------------- */
-/* IEEE totalOrder key of a float: unsigned comparison of keys orders the
- * floats, with -0 below +0. */
-static uint32_t total_key(float v)
-{
-    uint32_t b;
-    memcpy(&b, &v, 4);
-    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-}
-
 int orc_correct_relaxed(const float *f, const float *fhat, float xi, int ndim, int64_t nx, int64_t ny,
                         int64_t nz, int64_t tx, int64_t ty, int64_t tz, int rule, int64_t local_cap,
                         int64_t max_iters, float *g, int64_t *stats)

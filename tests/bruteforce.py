@@ -133,3 +133,91 @@ def brute_labels(codes: np.ndarray):
             lab[i] = p
         res.append(lab.reshape(codes.shape))
     return res[0], res[1]
+
+
+def exact_floor(f, xi):
+    """Smallest float32 >= f - xi, with f - xi taken as an exact rational."""
+    from fractions import Fraction
+    want = Fraction(float(np.float32(f))) - Fraction(float(np.float32(xi)))
+    c = np.float32(float(want))  # nearest double, then nearest float: close, fixed up below
+    while Fraction(float(c)) < want:
+        c = np.nextafter(c, np.float32(np.inf), dtype=np.float32)
+    while True:
+        d = np.nextafter(c, np.float32(-np.inf), dtype=np.float32)
+        if Fraction(float(d)) >= want:
+            c = d
+        else:
+            return np.float32(c)
+
+
+def _vertex(i, slot, shape_xyz):
+    if slot == 15:
+        return i
+    c = coords(i, shape_xyz)
+    d = slot_offsets(len(shape_xyz))[slot]
+    return lin(tuple(a + b for a, b in zip(c, d)), shape_xyz)
+
+
+def _above(v, j, i):
+    return (float(v[j]), j) > (float(v[i]), i)
+
+
+def brute_sweep(f, g, xi, rule):
+    """One synchronous sweep written out from the reading of Sec. III-B / IV-A
+    (no oracle code): returns (g', distorted, distinct targets, changed).
+    Targets: an ascending mismatch lowers g's steepest ascent of i (i itself
+    when g makes i a maximum); a descending mismatch lowers f's steepest
+    descent of i (i itself when f makes i a minimum).  Edits: HALVE (0),
+    SNAP (1), or BELOW-REFERENCE (2): the target drops to the largest value
+    below its reference (f's steepest ascent of i, resp. g's steepest descent
+    of i) in the (value, index) order, the smallest request winning; all
+    computed from g, at or above the floor."""
+    shape_xyz = xyz_shape(f.shape)
+    cf = brute_codes(f).reshape(-1)
+    cg = brute_codes(g).reshape(-1)
+    gf = g.reshape(-1).astype(np.float32)
+    ff = f.reshape(-1)
+    req = {}
+    distorted = 0
+    for i in range(gf.size):
+        if cf[i] == cg[i]:
+            continue
+        distorted += 1
+        af, ag, df, dg = cf[i] & 15, cg[i] & 15, cf[i] >> 4, cg[i] >> 4
+        pairs = []
+        if af != ag:
+            pairs.append((_vertex(i, int(ag), shape_xyz), _vertex(i, int(af), shape_xyz)))
+        if df != dg:
+            pairs.append((_vertex(i, int(df), shape_xyz), _vertex(i, int(dg), shape_xyz)))
+        for t, r in pairs:
+            if r > t:
+                c = gf[r]
+            else:
+                c = np.nextafter(gf[r], np.float32(-np.inf), dtype=np.float32)
+            key = (float(c), 0 if np.signbit(c) else 1)  # totalOrder on the candidates
+            if t not in req or key < req[t][0]:
+                req[t] = (key, np.float32(c))
+    out = gf.copy()
+    changed = 0
+    for t, (_, c) in req.items():
+        L = exact_floor(ff[t], xi)
+        gt = gf[t]
+        if rule == 2:
+            h = L if c < L else c
+            if not h < gt:
+                continue
+        else:
+            if not gt > L:
+                continue
+            if rule == 1:
+                h = L
+            else:
+                s = np.float32(gt - L)
+                h = np.float32(gt - np.float32(np.float32(0.5) * s))
+                if h < L:
+                    h = L
+                if not h < gt:
+                    h = L
+        out[t] = h
+        changed += 1
+    return out.reshape(g.shape), distorted, len(req), changed

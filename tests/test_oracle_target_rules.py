@@ -195,3 +195,62 @@ def test_random_tiny_grids_never_stuck_without_collapsed_floors():
             assert r.status == oracle.OK
             assert np.array_equal(bf.brute_codes(r.g), bf.brute_codes(f))
     assert stuck == 0
+
+
+# ------------------------------------------------------- BELOW-REFERENCE
+def below(v, t, r):
+    """The reading of 'slightly below' (Sec. IV-A): the largest value that puts
+    t below r in the (value, index) order -- r's value when r has the larger
+    index, else the float just below it."""
+    v = np.float32(v)
+    return v if r > t else np.nextafter(v, np.float32(-np.inf), dtype=np.float32)
+
+
+# fixture -> (lowered vertex, its reference vertex)
+BELOW_CASES = {
+    "fpmax_fig_fpmax.json": (1, 2),          # the false maximum falls below f's n_max (0.35 in f)
+    "fnmax_c_loop.json": (13, 12),           # the spurious neighbour falls below the maximum i
+    "fpmin_c_loop.json": (13, 12),           # f's n_min falls below i, which g makes a minimum
+    "fnmin_c_loop.json": (12, 17),           # the minimum i falls below g's smaller neighbour
+    "descending_fig_nonextrema_abc.json": (3, 5),   # the original minimum 0.1 falls below 0.08
+    "ascending_fig_nonextrema_def.json": (5, 8),    # the spurious 0.4 falls to 0.3
+}
+
+
+@pytest.mark.parametrize("name", list(BELOW_CASES))
+def test_below_reference_moves_just_under_the_reference(name):
+    d, f, fhat, xi = load(name)
+    t, r = BELOW_CASES[name]
+    res = oracle.correct(f, fhat, xi, rule=oracle.RULE_BELOW, log_capacity=8)
+    assert res.status == oracle.OK and res.sweeps == 1
+    assert list(res.edit_idx) == [t]
+    g = res.g.reshape(-1)
+    assert g[t].view(np.uint32) == below(fhat.reshape(-1)[r], t, r).view(np.uint32)
+    # t is below r, and the next float up would not be
+    assert (float(g[t]), t) < (float(g[r]), r)
+    up = np.nextafter(g[t], np.float32(np.inf), dtype=np.float32)
+    assert (float(up), t) > (float(g[r]), r)
+    assert np.array_equal(bf.brute_codes(res.g), bf.brute_codes(f))
+
+
+def test_below_reference_worked_example_values():
+    """Fig. nonextrema (d)-(f): 'decreased to 0.3 or slightly below' and the
+    ascending path 0.15 -> 0.2 -> 0.3."""
+    d, f, fhat, xi = load("ascending_fig_nonextrema_def.json")
+    pf = d["paper_facts"]
+    res = oracle.correct(f, fhat, xi, rule=oracle.RULE_BELOW)
+    g = res.g.reshape(-1)
+    assert g[pf["D"]] == np.float32(pf["C_value"])
+    codes = oracle.codes(res.g).reshape(-1)
+    path = [pf["P"]]
+    while (codes[path[-1]] & 15) != 15:
+        path.append(oracle.neighbour(f.shape, path[-1], int(codes[path[-1]] & 15)))
+    assert [np.float32(g[p]) for p in path] == [np.float32(v) for v in pf["path"]]
+
+
+def test_edit_below_clamps_at_the_floor_and_never_raises():
+    assert oracle.edit_below(0.5, 0.2, 0.3) == (np.float32(0.3), True)
+    assert oracle.edit_below(0.5, 0.35, 0.3) == (np.float32(0.35), True)   # clamped at the floor
+    assert oracle.edit_below(0.35, 0.35, 0.3) == (np.float32(0.35), False)  # already at the floor
+    g, ch = oracle.edit_below(0.0, -1.0, -0.0)
+    assert not ch and g.view(np.uint32) == np.float32(0.0).view(np.uint32)  # -0 is not below +0 in value
