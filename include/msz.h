@@ -76,8 +76,20 @@ typedef struct {
 
 /* Eq. 1 leaves the edit amount delta open.  HALVE moves g halfway to its floor
  * L (s = g - L; h = g - 0.5*s; h = max(h, L); h = L when h is not below g),
- * SNAP moves it to the floor in one edit (Fig. nonextrema (c): 0.1 -> 0). */
-typedef enum { MSZ_RULE_HALVE = 0, MSZ_RULE_SNAP = 1 } msz_rule;
+ * SNAP moves it to the floor in one edit (Fig. nonextrema (c): 0.1 -> 0).
+ * BELOW_REFERENCE (Sec. IV-A: the spurious maximum is decreased "to 0.3 or
+ * slightly below") moves the target to the largest value that puts it below
+ * the vertex it must fall under, in the (value, index) order: r's value when
+ * the reference r has the larger index, else the float just below it; kept at
+ * or above L.  The reference of an ascending mismatch at i is f's steepest
+ * ascent of i (i itself when f makes i a maximum); of a descending mismatch,
+ * g's steepest descent of i (i itself when g makes i a minimum).  All values
+ * come from g of the sweep (Jacobi); a target several vertices ask for takes
+ * the smallest candidate in IEEE totalOrder (Sec. IV-B: the minimum of the
+ * candidates).  BELOW_REFERENCE is available in msz_correct only (the batch,
+ * relaxed and pipelined entry points return MSZ_ERR_INVALID_ARG or
+ * MSZ_ERR_WORKSPACE), with the workspace of msz_workspace_size_rule. */
+typedef enum { MSZ_RULE_HALVE = 0, MSZ_RULE_SNAP = 1, MSZ_RULE_BELOW_REFERENCE = 2 } msz_rule;
 
 typedef struct {
     int32_t rule;             /* msz_rule; default HALVE */
@@ -131,6 +143,12 @@ typedef struct {
  * per vertex plus 1.2 MB); 0 for an invalid grid. */
 size_t msz_workspace_size(msz_grid grid);
 
+/* Bytes of device workspace msz_correct needs for this grid under edit rule
+ * `rule`: msz_workspace_size for HALVE and SNAP, plus 4 bytes per vertex (each
+ * target's smallest candidate) for BELOW_REFERENCE; 0 for an invalid grid or
+ * rule. */
+size_t msz_workspace_size_rule(msz_grid grid, int32_t rule);
+
 /* Sec. IV-A / Sec. III-A: steepest-neighbour codes of one field.
  * codes[i] low nibble = slot of n_max(i) = argmax over N(i) when it is above i,
  * else MSZ_SELF (i is a maximum); high nibble = slot of n_min(i) when below i,
@@ -155,8 +173,9 @@ msz_status msz_directions(const float *d_v, msz_grid grid, uint8_t *d_codes, msz
  *   delta = float32(g_i - fhat_i); *h_edit_count = the number of such i (may
  *   exceed edit_capacity: then MSZ_ERR_CAPACITY on an otherwise OK run; d_out
  *   is complete either way).
- * Workspace: d_workspace of at least msz_workspace_size(grid) bytes, 256-byte
- *   aligned, not used by any concurrent call.
+ * Workspace: d_workspace of at least msz_workspace_size_rule(grid, rule) bytes
+ *   (msz_workspace_size(grid) for HALVE and SNAP), 256-byte aligned, not used
+ *   by any concurrent call.
  * Synchronizes `stream` before returning (status, counts and stats are read back). */
 msz_status msz_correct(const float *d_f, const float *d_fhat, float xi, msz_grid grid, float *d_out,
                        uint32_t *d_edit_idx, float *d_edit_delta, int64_t edit_capacity,

@@ -18,7 +18,7 @@ from . import _build
 
 OK, ERR_INVALID_ARG, ERR_INPUT_BOUND, ERR_CAPACITY, ERR_WORKSPACE, ERR_CUDA = 0, 1, 2, 3, 4, 5
 ERR_MAX_SWEEPS, ERR_TIMEOUT, STUCK, ERR_UNSUPPORTED = 6, 7, 8, 9
-RULES = {"halve": 0, "snap": 1}
+RULES = {"halve": 0, "snap": 1, "below": 2}
 SELF = 15
 MAX_SWEEPS_LIMIT = 65536
 SMALL_WORKSPACE = 65536
@@ -85,6 +85,8 @@ def load(build_if_missing: bool = True):
         st = ctypes.c_int
         lib.msz_workspace_size.argtypes = [Grid]
         lib.msz_workspace_size.restype = SZ
+        lib.msz_workspace_size_rule.argtypes = [Grid, ctypes.c_int32]
+        lib.msz_workspace_size_rule.restype = SZ
         lib.msz_host_workspace_size.argtypes = [Grid, I64]
         lib.msz_host_workspace_size.restype = SZ
         lib.msz_directions.argtypes = [P, Grid, P, P]
@@ -254,7 +256,7 @@ def correct(f: torch.Tensor, fhat: torch.Tensor, xi: float, *, rule="halve", max
         edit_idx = torch.empty(max(cap, 1), dtype=torch.int32, device=f.device)
     if edit_delta is None or edit_delta.numel() < cap:
         edit_delta = torch.empty(max(cap, 1), dtype=torch.float32, device=f.device)
-    need = int(lib.msz_workspace_size(g))
+    need = int(lib.msz_workspace_size_rule(g, RULES[rule] if isinstance(rule, str) else int(rule)))
     if ws is None:
         ws = workspace(need, f.device)
     opt, log = _options(rule, max_sweeps, dense_min_items, g_init, log_capacity, tile_z, test_fault)

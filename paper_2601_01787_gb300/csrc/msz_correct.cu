@@ -435,6 +435,14 @@ extern "C" size_t msz_workspace_size(msz_grid grid) {
     return layout_for(G.n).total;
 }
 
+extern "C" size_t msz_workspace_size_rule(msz_grid grid, int32_t rule) {
+    GridDev G;
+    if (make_grid(grid, G) != MSZ_OK) return 0;
+    if (rule == MSZ_RULE_HALVE || rule == MSZ_RULE_SNAP) return layout_for(G.n).total;
+    if (rule == MSZ_RULE_BELOW_REFERENCE) return layout_for(G.n).total + cand_bytes(G.n);
+    return 0;
+}
+
 extern "C" msz_status msz_directions(const float *d_v, msz_grid grid, uint8_t *d_codes, msz_stream_t stream) {
     if (!d_v || !d_codes) return MSZ_ERR_INVALID_ARG;
     GridDev G;
@@ -467,14 +475,16 @@ static msz_status prepare_correct(const float *d_f, const float *d_fhat, float x
     if (st != MSZ_OK) return st;
     o = msz_options{};
     if (opt) o = *opt;
-    if (o.rule != MSZ_RULE_HALVE && o.rule != MSZ_RULE_SNAP) return MSZ_ERR_INVALID_ARG;
+    if (o.rule != MSZ_RULE_HALVE && o.rule != MSZ_RULE_SNAP && o.rule != MSZ_RULE_BELOW_REFERENCE)
+        return MSZ_ERR_INVALID_ARG;
     if (o.test_fault < 0 || o.test_fault > 2) return MSZ_ERR_INVALID_ARG;
     if (o.max_sweeps > MSZ_MAX_SWEEPS_LIMIT || o.dense_min_items < -1 || o.log_capacity < 0 || o.tile_z < 0 ||
         o.tile_z > 1024 ||
         (o.log_capacity > 0 && !o.h_sweep_log))
         return MSZ_ERR_INVALID_ARG;
     const Layout L = layout_for(G.n);
-    if (!d_workspace || workspace_bytes < L.total) return MSZ_ERR_WORKSPACE;
+    const bool below = o.rule == MSZ_RULE_BELOW_REFERENCE;
+    if (!d_workspace || workspace_bytes < L.total + (below ? cand_bytes(G.n) : 0)) return MSZ_ERR_WORKSPACE;
     if ((uintptr_t)d_workspace % kAlign) return MSZ_ERR_INVALID_ARG;
 
     char *ws = (char *)d_workspace;
@@ -491,6 +501,7 @@ static msz_status prepare_correct(const float *d_f, const float *d_fhat, float x
     F.dm[1] = (uint32_t *)(ws + L.d1);
     F.eb = (uint32_t *)(ws + L.eb);
     F.ub = (uint32_t *)(ws + L.ub);
+    F.cand = below ? (uint32_t *)(ws + L.total) : nullptr;  // after the shared layout
     F.xi = xi;
     F.two_xi = 2.0f * xi;  // exact (power-of-two scaling), +inf on overflow
     F.rule = o.rule;
@@ -511,6 +522,8 @@ static msz_status prepare_correct(const float *d_f, const float *d_fhat, float x
 
 static msz_status enqueue_correct(Problem &P, const DeviceInfo &dev, cudaStream_t s) {
     if (cudaMemsetAsync(P.ctrl, 0, layout_for(P.F.G.n).zero_bytes, s) != cudaSuccess) return MSZ_ERR_CUDA;
+    // BELOW_REFERENCE: no candidate yet anywhere (all-ones keys)
+    if (P.F.cand && cudaMemsetAsync(P.F.cand, 0xff, (size_t)P.F.G.n * 4u, s) != cudaSuccess) return MSZ_ERR_CUDA;
     return P.F.G.ndim == 3 ? run_correct<3>(P, dev, s) : run_correct<2>(P, dev, s);
 }
 

@@ -306,6 +306,38 @@ __device__ __forceinline__ int targets_of(const GridDev &G, uint32_t i, uint8_t 
     return (int)ta + (int)td;
 }
 
+// The vertices the targets of targets_of must fall below (BELOW_REFERENCE),
+// in the same order: for an ascending mismatch, f's steepest ascent of i (i
+// itself when f makes i a maximum); for a descending one, g's steepest
+// descent of i (i itself when g makes i a minimum).
+__device__ __forceinline__ void references_of(const GridDev &G, uint32_t i, uint8_t cf, uint8_t cg, uint32_t &r0,
+                                              uint32_t &r1) {
+    const uint32_t af = cf & 15u, ag = cg & 15u, dg = cg >> 4;
+    const uint32_t a = (af == kSelf) ? i : (uint32_t)((int64_t)i + G.off[af & 15u]);
+    const uint32_t d = (dg == kSelf) ? i : (uint32_t)((int64_t)i + G.off[dg & 15u]);
+    r0 = ag != af ? a : d;
+    r1 = d;
+}
+
+// IEEE totalOrder key of a float (unsigned comparison orders the floats, -0
+// below +0) and its inverse.
+__device__ __forceinline__ uint32_t total_key(float v) {
+    const uint32_t b = __float_as_uint(v);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float from_total_key(uint32_t k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// The next float below a finite v (towards -inf): one unit in the last place
+// down in magnitude for v > 0, up for v < 0, and the negative subnormal of
+// least magnitude for either zero.
+__device__ __forceinline__ float float_below(float v) {
+    const uint32_t b = __float_as_uint(v);
+    if ((b & 0x7fffffffu) == 0u) return __uint_as_float(0x80000001u);
+    return __uint_as_float((b & 0x80000000u) ? b + 1u : b - 1u);
+}
+
 // Set bit v of a bitmap; true when this call set it (first claimer).
 __device__ __forceinline__ bool claim_bit(uint32_t *bm, uint32_t v) {
     const uint32_t bit = 1u << (v & 31u);

@@ -37,6 +37,8 @@ struct FieldView {
     uint32_t *dm[2];   // worklist of a sweep, by sweep parity
     uint32_t *eb;      // edited vertices
     uint32_t *ub;      // uncertified vertices: the only ones that can ever be distorted
+    uint32_t *cand;    // BELOW_REFERENCE only (else null): per vertex, the totalOrder key of
+                       // the smallest value requested for it in this sweep (all ones: none)
     float xi;
     float two_xi;      // 2 xi (exact): the certification margin
     int rule;
@@ -51,11 +53,22 @@ struct Emitter {
     uint32_t distorted;
 };
 
+// BELOW_REFERENCE: the value target t asks for to fall below reference r
+// (value vr of this sweep) in the (value, index) order -- vr when r has the
+// larger index, else the float just below vr -- recorded as the minimum, in
+// IEEE totalOrder, over every request of the sweep.
+__device__ __forceinline__ void request_below(const FieldView &P, uint32_t t, uint32_t r, float vr) {
+    const float c = r > t ? vr : float_below(vr);
+    atomicMin(&P.cand[t], total_key(c));
+}
+
 // Warp-collective: vertex v (valid lanes) with codes cf in f and cg in g; a
 // distorted vertex marks its targets and, unless the caller marks whole words
-// itself (self_marked), itself for the next worklist.
+// itself (self_marked), itself for the next worklist.  sweep0: the pass that
+// runs sweep 0's detection while it writes g, where g of the sweep is still
+// the start field (BELOW_REFERENCE reads its reference values there).
 __device__ __forceinline__ bool report(const FieldView &P, Emitter &E, bool valid, uint32_t v, uint32_t cf,
-                                       uint32_t cg, bool self_marked = false) {
+                                       uint32_t cg, bool self_marked = false, bool sweep0 = false) {
     const bool dist = valid && cf != cg;
     if (!__any_sync(kFull, dist)) return false;
     if (dist) {
@@ -63,6 +76,13 @@ __device__ __forceinline__ bool report(const FieldView &P, Emitter &E, bool vali
         const int nt = targets_of(P.G, v, (uint8_t)cf, (uint8_t)cg, t0, t1);
         red_or(&P.tb[t0 >> 5], 1u << (t0 & 31u));
         if (nt > 1) red_or(&P.tb[t1 >> 5], 1u << (t1 & 31u));
+        if (P.cand) {
+            uint32_t r0, r1;
+            references_of(P.G, v, (uint8_t)cf, (uint8_t)cg, r0, r1);
+            const float *gk = sweep0 ? (P.ginit ? P.ginit : P.fhat) : P.g;
+            request_below(P, t0, r0, gk[r0]);
+            if (nt > 1) request_below(P, t1, r1, gk[r1]);
+        }
         if (!self_marked) red_or(&E.dnext[v >> 5], 1u << (v & 31u));
         E.distorted += 1;
     }
@@ -378,7 +398,7 @@ __device__ __forceinline__ void tile_row(const FieldView &P, const float *pm, co
             P.codes_f[rowbase + (uint32_t)x0 + col] = (uint8_t)cf;
             if (DETECT) cg = code1(pm + soff, p0 + soff, pp + soff, r, 4 + (int)col);
         }
-        if (DETECT) report(P, E, has, rowbase + (uint32_t)x0 + col, cf, cg);
+        if (DETECT) report(P, E, has, rowbase + (uint32_t)x0 + col, cf, cg, false, true);
     }
     distorted += E.distorted;
 }
@@ -477,7 +497,7 @@ __device__ __forceinline__ void tile_rows2(const FieldView &P, const float *pm, 
             P.codes_f[base + col] = (uint8_t)cf;
             if (DETECT) cg = tile::code1(qm + soff, q0 + soff, qp + soff, r, 4 + (int)col);
         }
-        if (DETECT) report(P, E, has, base + col, cf, cg);
+        if (DETECT) report(P, E, has, base + col, cf, cg, false, true);
     }
     distorted += E.distorted;
 }
@@ -1104,7 +1124,16 @@ __device__ __forceinline__ bool edit_target(const FieldView &P, uint32_t t) {
     const float gt = P.g[t];
     const float L = floor_bound(__ldg(&P.f[t]), P.xi);
     float h;
-    if (!edit_value(gt, L, P.rule, h)) return false;
+    if (P.cand) {
+        // BELOW_REFERENCE: the smallest requested value, at or above the
+        // floor; the record is reset for the next sweep
+        const float c = from_total_key(P.cand[t]);
+        P.cand[t] = 0xffffffffu;
+        h = c < L ? L : c;
+        if (!(h < gt)) return false;
+    } else if (!edit_value(gt, L, P.rule, h)) {
+        return false;
+    }
     P.g[t] = h;
     return true;
 }

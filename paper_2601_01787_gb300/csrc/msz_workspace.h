@@ -73,6 +73,10 @@ constexpr Layout layout_for(uint64_t n) {
     return L;
 }
 
+// BELOW_REFERENCE's candidate records (4 bytes a vertex), placed after the
+// layout above.
+constexpr size_t cand_bytes(uint64_t n) { return align_up(n * 4); }
+
 // Validates a grid; fills G (offsets, sizes).  Returns MSZ_OK or INVALID_ARG.
 inline msz_status make_grid(const msz_grid &g, GridDev &G) {
     if (g.ndim != 2 && g.ndim != 3) return MSZ_ERR_INVALID_ARG;

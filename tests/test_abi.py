@@ -44,6 +44,11 @@ def test_status_strings_and_sizes_without_gpu():
     assert lib.msz_workspace_size(api.Grid(4, 0, 1, 1, 1)) == 0       # bad ndim
     assert lib.msz_workspace_size(api.Grid(2, 0, 3, 3, 2)) == 0       # 2D with nz != 1
     assert lib.msz_workspace_size(api.Grid(3, 0, 2048, 2048, 1024)) == 0  # > 2^31 - 1 vertices
+    g = api.grid_of((4, 5, 6))
+    base = lib.msz_workspace_size(g)
+    assert lib.msz_workspace_size_rule(g, 0) == lib.msz_workspace_size_rule(g, 1) == base
+    assert lib.msz_workspace_size_rule(g, 2) >= base + 4 * 4 * 5 * 6  # one candidate record a vertex
+    assert lib.msz_workspace_size_rule(g, 3) == 0                      # no such rule
 
 
 def test_invalid_arguments_rejected_on_host():

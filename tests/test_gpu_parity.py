@@ -321,3 +321,26 @@ def test_correct_host_matches_oracle(api, memory, shape):
     assert res.status == ref.status
     assert np.array_equal(bits(res.out), bits(ref.g))
     assert np.array_equal(res.edit_idx, ref.edit_idx) and np.array_equal(bits(res.edit_delta), bits(ref.edit_delta))
+
+
+@pytest.mark.parametrize("dense_min", [-1, 0, 1], ids=["worklist_only", "default", "always_dense"])
+@pytest.mark.parametrize("name", list(CASES))
+def test_below_reference_rule_bit_exact(api, name, dense_min):
+    """BELOW_REFERENCE (Sec. IV-A 'to 0.3 or slightly below'): the whole loop,
+    per-sweep counts included, against the oracle's BELOW rule."""
+    fl = CASES[name]()
+    ref = oracle.correct(fl.f, fl.fhat, fl.xi, rule=oracle.RULE_BELOW, log_capacity=100000)
+    assert ref.status == oracle.OK
+    res = api.correct(dev(fl.f), dev(fl.fhat), fl.xi, rule="below", dense_min_items=dense_min,
+                      log_capacity=100000)
+    _check_against(res, ref, fl, worklist_column=dense_min == -1)
+
+
+def test_below_reference_needs_its_workspace(api):
+    fl = synth.perlin3d_prequant((20, 21, 22), seed=41, eb_rel=1e-4)
+    lib = api.load()
+    need = lib.msz_workspace_size_rule(api.grid_of(fl.shape), 2)
+    assert need > api.workspace_size(fl.shape)
+    ws = torch.empty(api.workspace_size(fl.shape), dtype=torch.uint8, device="cuda")
+    res = api.correct(dev(fl.f), dev(fl.fhat), fl.xi, rule="below", ws=ws)
+    assert res.status == api.ERR_WORKSPACE
