@@ -395,9 +395,16 @@ msz_status msz_learned_target(const float *d_f, const float *d_fhat, const float
 /* Weight and bias gradients of one layer (FP32, accumulated into d_dw
  * [27][cout_real][cin_real] and d_db[cout_real]): dw[o][co][ci] += sum_v
  * dz[v][co] x[v + d_o][ci].  d_x: the layer's input (cin channels), d_dz: the
- * gradient of its pre-activation output (cout channels). */
+ * gradient of its pre-activation output (cout channels).  (cin, cout) is
+ * (16, 32), (32, 32) or (32, 16).  The partial sums of a fixed set of thread
+ * blocks go to d_workspace (msz_learned_wgrad_workspace_size(cin, cout) bytes,
+ * 16-byte aligned; MSZ_ERR_WORKSPACE if smaller) and are added in a fixed
+ * order, with no atomics: the same inputs give the same gradient bit for bit
+ * on every run. */
+size_t msz_learned_wgrad_workspace_size(int32_t cin, int32_t cout);
 msz_status msz_learned_wgrad(const uint16_t *d_x, int32_t cin, const uint16_t *d_dz, int32_t cout, msz_grid grid,
-                             int32_t cin_real, int32_t cout_real, float *d_dw, float *d_db, msz_stream_t stream);
+                             int32_t cin_real, int32_t cout_real, float *d_dw, float *d_db, void *d_workspace,
+                             size_t workspace_bytes, msz_stream_t stream);
 
 /* One Adam step on n FP32 parameters (bias-corrected; step >= 1). */
 msz_status msz_learned_adam(float *d_p, const float *d_g, float *d_m, float *d_v, int64_t n, float lr, float beta1,

@@ -531,12 +531,24 @@ __global__ void k_target(const float *f, const float *fhat, const float *g, floa
 // sum_v dz[v][cout] on CUDA cores (FP32).  A block takes rows of 128 voxels
 // (x) at one (y, z), stages dz and the 9 (y, z) neighbour lines of x in shared
 // memory, and each thread accumulates 27 offsets x 4 input channels of one
-// output channel in registers; partial sums go to global memory once per
-// block.  CIN in {16, 32} (x channels), COUT in {16, 32} (dz channels),
-// cin_real / cout_real the channels that carry weights.
+// output channel in registers.  Each thread then writes its partial sums to
+// its own slot of the workspace (no atomics), and k_wgrad_reduce adds the
+// slots in a fixed order: the gradient is the same bit for bit on every run.
+// CIN in {16, 32} (x channels), COUT in {16, 32} (dz channels), cin_real /
+// cout_real the channels that carry weights.
+constexpr int kWgradBlocks = 304;  // fixed, so the summation order is too
+
+template <int CIN, int COUT>
+struct WgradShape {
+    static constexpr int PAIRS = COUT * (CIN / 4);  // (cout, cin group) pairs
+    static constexpr int NREP = 256 / PAIRS;        // threads per pair (each a share of the voxels)
+    static constexpr int SLOT = 27 * COUT * CIN + COUT;  // floats of one partial: weights, then biases
+    static constexpr size_t BYTES = (size_t)kWgradBlocks * NREP * SLOT * sizeof(float);
+};
+
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(256) k_wgrad(const uint16_t *x, const uint16_t *dz, uint32_t nx, uint32_t ny,
-                                               uint32_t nz, int cin_real, int cout_real, float *dw, float *db) {
+                                               uint32_t nz, float *part) {
     constexpr int CG = CIN / 4;              // groups of 4 input channels
     constexpr int PAIRS = COUT * CG;         // (cout, cin group) pairs
     extern __shared__ __align__(16) unsigned char wsmem[];
@@ -588,15 +600,34 @@ __global__ void __launch_bounds__(256) k_wgrad(const uint16_t *x, const uint16_t
             }
         }
     }
-    if (co < cout_real) {
+    using S = WgradShape<CIN, COUT>;
+    float *slot = part + ((size_t)blockIdx.x * S::NREP + rep) * S::SLOT;
 #pragma unroll
-        for (int o = 0; o < 27; ++o)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int ci = cg * 4 + c;
-                if (ci < cin_real && acc[o][c] != 0.0f) atomicAdd(&dw[((size_t)o * cout_real + co) * cin_real + ci], acc[o][c]);
-            }
-        if (cg == 0 && bacc != 0.0f) atomicAdd(&db[co], bacc);
+    for (int o = 0; o < 27; ++o)
+        *reinterpret_cast<float4 *>(&slot[((size_t)o * COUT + co) * CIN + cg * 4]) =
+            make_float4(acc[o][0], acc[o][1], acc[o][2], acc[o][3]);
+    if (cg == 0) slot[27 * COUT * CIN + co] = bacc;
+}
+
+// dw[o][co][ci] (real channel counts) += the partials of every block and
+// share, added in slot order; db likewise.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(256) k_wgrad_reduce(const float *part, int cin_real, int cout_real, float *dw,
+                                                      float *db) {
+    using S = WgradShape<CIN, COUT>;
+    const int nw = 27 * cout_real * cin_real, total = nw + cout_real;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < total; j += gridDim.x * blockDim.x) {
+        int src;
+        if (j < nw) {
+            const int o = j / (cout_real * cin_real), co = (j / cin_real) % cout_real, ci = j % cin_real;
+            src = (o * COUT + co) * CIN + ci;
+        } else {
+            src = 27 * COUT * CIN + (j - nw);
+        }
+        float sum = 0.0f;
+        for (int p = 0; p < kWgradBlocks * S::NREP; ++p) sum += part[(size_t)p * S::SLOT + src];
+        if (j < nw) dw[j] += sum;
+        else db[j - nw] += sum;
     }
 }
 
@@ -677,17 +708,14 @@ msz_status launch_conv(const uint16_t *x, const ConvParams &P0, int sms, cudaStr
 
 template <int CIN, int COUT>
 msz_status launch_wgrad(const uint16_t *x, const uint16_t *dz, const GridDev &G, int cin_real, int cout_real,
-                        float *dw, float *db, int blocks, cudaStream_t s) {
+                        float *dw, float *db, void *ws, size_t ws_bytes, cudaStream_t s) {
+    if (!ws || ws_bytes < WgradShape<CIN, COUT>::BYTES || ((uintptr_t)ws & 15u)) return MSZ_ERR_WORKSPACE;
     const int smem = 9 * 130 * CIN * 2 + 128 * COUT * 2;
-    static bool attr_set[64];
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (!attr_set[dev & 63]) {
-        if (cudaFuncSetAttribute(k_wgrad<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-            return MSZ_ERR_CUDA;
-        attr_set[dev & 63] = true;
-    }
-    k_wgrad<CIN, COUT><<<blocks, 256, smem, s>>>(x, dz, G.nx, G.ny, G.nz, cin_real, cout_real, dw, db);
+    // the attribute belongs to the current context: set it on every call
+    if (cudaFuncSetAttribute(k_wgrad<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return MSZ_ERR_CUDA;
+    k_wgrad<CIN, COUT><<<kWgradBlocks, 256, smem, s>>>(x, dz, G.nx, G.ny, G.nz, (float *)ws);
+    k_wgrad_reduce<CIN, COUT><<<64, 256, 0, s>>>((const float *)ws, cin_real, cout_real, dw, db);
     return cudaGetLastError() == cudaSuccess ? MSZ_OK : MSZ_ERR_CUDA;
 }
 
@@ -817,9 +845,16 @@ extern "C" msz_status msz_learned_target(const float *d_f, const float *d_fhat, 
     return cudaGetLastError() == cudaSuccess ? MSZ_OK : MSZ_ERR_CUDA;
 }
 
+extern "C" size_t msz_learned_wgrad_workspace_size(int32_t cin, int32_t cout) {
+    if (cin == 16 && cout == 32) return WgradShape<16, 32>::BYTES;
+    if (cin == 32 && cout == 32) return WgradShape<32, 32>::BYTES;
+    if (cin == 32 && cout == 16) return WgradShape<32, 16>::BYTES;
+    return 0;
+}
+
 extern "C" msz_status msz_learned_wgrad(const uint16_t *d_x, int32_t cin, const uint16_t *d_dz, int32_t cout,
                                         msz_grid grid, int32_t cin_real, int32_t cout_real, float *d_dw, float *d_db,
-                                        msz_stream_t stream) {
+                                        void *d_workspace, size_t workspace_bytes, msz_stream_t stream) {
     GridDev G;
     msz_status st = make_grid(grid, G);
     if (st != MSZ_OK) return st;
@@ -829,11 +864,12 @@ extern "C" msz_status msz_learned_wgrad(const uint16_t *d_x, int32_t cin, const 
     if (((uintptr_t)d_x & 15u) || ((uintptr_t)d_dz & 15u)) return MSZ_ERR_INVALID_ARG;
     DeviceInfo dev;
     if ((st = current_device(dev)) != MSZ_OK) return st;
-    const int blocks = dev.sms * 2;
     cudaStream_t s = (cudaStream_t)stream;
-    if (cin == 16) return launch_wgrad<16, 32>(d_x, d_dz, G, cin_real, cout_real, d_dw, d_db, blocks, s);
-    if (cout == 32) return launch_wgrad<32, 32>(d_x, d_dz, G, cin_real, cout_real, d_dw, d_db, blocks, s);
-    return launch_wgrad<32, 16>(d_x, d_dz, G, cin_real, cout_real, d_dw, d_db, blocks, s);
+    void *w = d_workspace;
+    const size_t wb = workspace_bytes;
+    if (cin == 16) return launch_wgrad<16, 32>(d_x, d_dz, G, cin_real, cout_real, d_dw, d_db, w, wb, s);
+    if (cout == 32) return launch_wgrad<32, 32>(d_x, d_dz, G, cin_real, cout_real, d_dw, d_db, w, wb, s);
+    return launch_wgrad<32, 16>(d_x, d_dz, G, cin_real, cout_real, d_dw, d_db, w, wb, s);
 }
 
 extern "C" msz_status msz_learned_adam(float *d_p, const float *d_g, float *d_m, float *d_v, int64_t n, float lr,

@@ -52,7 +52,9 @@ def lib():
         L.msz_learned_conv.argtypes = [P, I32, I32, I32, api.Grid, P, P, P, P, P, P, P, F, I32, P, P, P]
         L.msz_learned_head_grad.argtypes = [P, P, I64, F, P, P, P]
         L.msz_learned_target.argtypes = [P, P, P, F, I64, P, P]
-        L.msz_learned_wgrad.argtypes = [P, I32, P, I32, api.Grid, I32, I32, P, P, P]
+        L.msz_learned_wgrad.argtypes = [P, I32, P, I32, api.Grid, I32, I32, P, P, P, ctypes.c_size_t, P]
+        L.msz_learned_wgrad_workspace_size.argtypes = [I32, I32]
+        L.msz_learned_wgrad_workspace_size.restype = ctypes.c_size_t
         L.msz_learned_adam.argtypes = [P, P, P, P, I64, F, F, F, F, I64, P]
         for name in ("features", "weight_image", "conv", "head_grad", "target", "wgrad", "adam"):
             getattr(L, "msz_learned_" + name).restype = st
@@ -129,11 +131,21 @@ def target(f: torch.Tensor, fhat: torch.Tensor, g: torch.Tensor, xi: float, out=
     return out
 
 
+_wgrad_ws: dict = {}
+
+
 def wgrad(x: torch.Tensor, cin: int, dz: torch.Tensor, cout: int, shape, dw: torch.Tensor, db: torch.Tensor,
           stream=None) -> None:
-    """dw += sum_v dz[v] x[v + d_o]^T, db += sum_v dz[v] (msz_learned_wgrad)."""
+    """dw += sum_v dz[v] x[v + d_o]^T, db += sum_v dz[v] (msz_learned_wgrad;
+    deterministic: partial sums in a cached workspace, added in a fixed order)."""
+    need = int(lib().msz_learned_wgrad_workspace_size(cin, cout))
+    key = x.device.index
+    ws = _wgrad_ws.get(key)
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(need, dtype=torch.uint8, device=x.device)
+        _wgrad_ws[key] = ws
     _check(lib().msz_learned_wgrad(_p(x), cin, _p(dz), cout, _grid(shape), int(dw.shape[2]), int(dw.shape[1]),
-                                   _p(dw), _p(db), _s(stream)), "msz_learned_wgrad")
+                                   _p(dw), _p(db), _p(ws), ws.numel(), _s(stream)), "msz_learned_wgrad")
 
 
 def adam(p, g, m, v, lr: float, step: int, beta1=0.9, beta2=0.999, eps=1e-8, stream=None) -> None:

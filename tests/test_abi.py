@@ -105,8 +105,10 @@ def test_learned_arguments_rejected_on_host():
     assert call(mode=learned.MODE_HEAD, cout=16) == api.ERR_INVALID_ARG  # neither r nor g0 requested
     assert call(mode=learned.MODE_RAW, ob=None) == api.ERR_INVALID_ARG   # no FP32 output
     w = lib.msz_learned_wgrad
-    assert w(a, 16, a, 16, g3, 16, 16, a, a, None) == api.ERR_INVALID_ARG   # 16 -> 16 is not a layer
-    assert w(a, 32, a, 32, g3, 33, 32, a, a, None) == api.ERR_INVALID_ARG   # more real than padded channels
+    assert w(a, 16, a, 16, g3, 16, 16, a, a, a, 1 << 30, None) == api.ERR_INVALID_ARG  # 16 -> 16 is not a layer
+    assert w(a, 32, a, 32, g3, 33, 32, a, a, a, 1 << 30, None) == api.ERR_INVALID_ARG  # more real than padded
+    assert lib.msz_learned_wgrad_workspace_size(16, 16) == 0
+    assert lib.msz_learned_wgrad_workspace_size(32, 32) >= 27 * 32 * 32 * 4  # a partial per block at least
     assert lib.msz_learned_weight_image(a, 0, 32, 32, 32, 0, a, None) == api.ERR_INVALID_ARG
     assert lib.msz_learned_weight_image(a, 32, 32, 32, 48, 0, a, None) == api.ERR_INVALID_ARG
     assert lib.msz_learned_features(a, a, F(1e-3), g2, a, a, a, None) == api.ERR_INVALID_ARG

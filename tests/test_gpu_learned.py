@@ -314,13 +314,31 @@ def test_features_bitwise(L):
 
 
 # ----------------------------------------------------- whole backward pass
-def test_network_gradients_match_oracle(L):
+def close_bf16(got, ref, bound, factor=2e-4, what=""):
+    """got is the BF16 rounding (nearest even, 2^-8 relative at most) of an
+    FP32 result within factor * bound of the exact value ref."""
+    e = factor * bound
+    err = np.abs(got - ref)
+    lim = e + 2.0 ** -8 * (np.abs(ref) + e) + 1e-30
+    bad = err > lim
+    assert not bad.any(), f"{what}: {bad.sum()} entries off, worst {err[bad].max()} vs {lim[bad].min()}"
+
+
+def test_network_forward_backward_elementwise(L):
+    """The whole forward and backward pass of the network, step by step, each
+    step element by element against the float64 oracle given the GPU's own
+    inputs to that step (so a BF16 rounding flip upstream does not carry into
+    the comparison), at the FP32-accumulation bound of the per-kernel tests;
+    then the gradients net.backward accumulated equal the step-by-step ones
+    bit for bit (every kernel is deterministic)."""
     shape = (4, 6, 130)
+    n = int(np.prod(shape))
     fl = synth.peaks3d(shape, seed=71, eb_rel=1e-3)
     f, fh = torch.from_numpy(fl.f).cuda(), torch.from_numpy(fl.fhat).cuda()
     net = L.ProposalNet(seed=3)
     x0 = L.features(f, fh, float(fl.xi))
-    tgt = torch.from_numpy(np.random.default_rng(72).integers(0, 16, shape).astype(np.float32)).cuda()
+    k = np.random.default_rng(72).integers(0, 16, shape)
+    tgt = torch.from_numpy(k.astype(np.float32)).cuda()
     net.build_images(mirror=True)
     net.grad.zero_()
     a, z = net.forward(x0, shape)
@@ -329,21 +347,76 @@ def test_network_gradients_match_oracle(L):
     torch.cuda.synchronize()
     net.check()
     params = net.params_numpy()
-    feat = host(x0).reshape(*shape, 16)
-    acts_o = OL.forward(feat, params)
-    # layer by layer the GPU activations equal the oracle's up to BF16 rounding flips
-    for l in (1, 2, 3):
-        ga = host(a[l]).reshape(*shape, 32)
-        assert np.abs(ga - acts_o[f"x{l}"]).max() <= 0.02 * np.abs(acts_o[f"x{l}"]).max() + 1e-6
-    grads_o, loss_o = OL.backward(acts_o, tgt.cpu().numpy().astype(np.int64), params, scale)
-    assert float(loss.item()) == pytest.approx(loss_o, rel=1e-3)
+    A = [host(t).reshape(*shape, -1) for t in a]
+    # forward: each layer from the GPU's own input
+    for l in range(3):
+        cin_r, cout_r, _, _ = L.LAYERS[l]
+        w, b = params[l]
+        wb = OL.bf16(w)
+        xin = A[l][..., :cin_r]
+        pre = OL.conv3d(xin, wb) + b
+        bound = OL.conv3d(np.abs(xin), np.abs(wb)) + np.abs(b)
+        close_bf16(A[l + 1][..., :cout_r], np.maximum(pre, 0.0), bound, what=f"x{l + 1}")
+    w3, b3 = params[3]
+    zref = OL.conv3d(A[3], OL.bf16(w3)) + b3
+    close(host(z).reshape(*shape, 16), zref, OL.conv3d(np.abs(A[3]), np.abs(OL.bf16(w3))) + np.abs(b3), what="z")
+    zg = host(z).reshape(*shape, 16)
+    assert float(loss.item()) == pytest.approx(float(OL.cross_entropy(zg, k).sum()), rel=1e-5)
+    # backward, one step at a time on the GPU, each checked on its own inputs
+    err = err_word()
+    dz = torch.empty(n, 16, dtype=torch.bfloat16, device="cuda")
+    L.head_grad(z, tgt.view(-1), scale, dz, torch.zeros(1, dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    ref = scale * (OL.softmax(zg) - np.eye(16)[k])
+    D = host(dz).reshape(*shape, 16)
+    assert np.all(np.abs(D - ref) <= 2.0 ** -8 * np.abs(ref) + 1e-6 * scale)
+    steps = {}
+
+    def wgrad_step(l, x_t, cin_pad, dz_t, cout_pad):
+        cin_r, cout_r, _, _ = L.LAYERS[l]
+        dw = torch.zeros(27, cout_r, cin_r, dtype=torch.float32, device="cuda")
+        db = torch.zeros(cout_pad, dtype=torch.float32, device="cuda")
+        L.wgrad(x_t, cin_pad, dz_t, cout_pad, shape, dw, db)
+        torch.cuda.synchronize()
+        xh = host(x_t).reshape(*shape, cin_pad)[..., :cin_r]
+        dzh = host(dz_t).reshape(*shape, cout_pad)[..., :cout_r]
+        close(host(dw), OL.conv3d_wgrad(xh, dzh), OL.conv3d_wgrad(np.abs(xh), np.abs(dzh)), factor=1e-4,
+              what=f"dw{l}")
+        close(host(db)[:cout_r], dzh.sum(axis=(0, 1, 2)), np.abs(dzh).sum(axis=(0, 1, 2)), factor=1e-4,
+              what=f"db{l}")
+        steps[l] = (dw, db[:cout_r])
+
+    wgrad_step(3, a[3], 32, dz, 16)
+    cur, cin_cur = dz, 16
+    for l in (3, 2, 1):
+        cin_r, cout_r, _, _ = L.LAYERS[l]
+        nxt = torch.empty(n, 32, dtype=torch.bfloat16, device="cuda")
+        L.conv(cur, cin_cur, 32, L.MODE_DGRAD, shape, net._mimg[l], err, out_bf16=nxt, mask=a[l])
+        torch.cuda.synchronize()
+        assert int(err.item()) == 0
+        dyh = host(cur).reshape(*shape, cin_cur)[..., :cout_r]
+        wb = OL.bf16(params[l][0])
+        ref = np.where(A[l][..., :cin_r] > 0, OL.conv3d_transpose(dyh, wb), 0.0)
+        bound = OL.conv3d_transpose(np.abs(dyh), np.abs(wb))
+        close_bf16(host(nxt).reshape(*shape, 32)[..., :cin_r], ref, bound, what=f"dgrad through layer {l}")
+        wgrad_step(l - 1, a[l - 1], L.LAYERS[l - 1][2], nxt, 32)
+        cur, cin_cur = nxt, 32
     for l in range(4):
-        gw = host(net.dw[l])
-        rw = grads_o[l][0]
-        assert np.linalg.norm(gw - rw) <= 0.03 * np.linalg.norm(rw), l
-        cout_r = LAYER_COUT[l]
-        gb = host(net.db[l])[:cout_r]
-        assert np.linalg.norm(gb - grads_o[l][1]) <= 0.03 * np.linalg.norm(grads_o[l][1]) + 1e-12, l
+        assert torch.equal(net.dw[l], steps[l][0]), l
+        assert torch.equal(net.db[l][:L.LAYERS[l][1]], steps[l][1]), l
+
+
+def test_training_is_deterministic(L):
+    """Two trainings from the same seed and data give the same weights bit for
+    bit (the weight gradients add their partial sums in a fixed order)."""
+    data = L.training_set(count=3, shape=(24, 24, 130), eb_rel=1e-4, seed0=9300)
+    nets = []
+    for _ in range(2):
+        net = L.ProposalNet(seed=8)
+        L.train(net, data, epochs=2, lr=3e-3)
+        nets.append(net)
+    torch.cuda.synchronize()
+    assert torch.equal(nets[0].flat, nets[1].flat)
 
 
 LAYER_COUT = (32, 32, 32, 16)
