@@ -18,6 +18,8 @@ Eq. 1, synchronous sweeps):
 The oracle runs in spawn-started worker processes (tests/oracle_pool.py),
 several fields at once, while the GPU corrections run here.
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -147,3 +149,22 @@ def test_batch64_every_field_bit_exact(api, refs):
     del fs, fhs
     for k, r in enumerate(res.fields):
         check(r, refs[("batch", k)].result())
+
+
+@pytest.mark.skipif(os.environ.get("MSZ_PARITY_1024") != "1",
+                    reason="about 20 minutes of one host core for the oracle: MSZ_PARITY_1024=1 runs it")
+def test_peaks_1024x1024x512_bit_exact(api):
+    """The 1024 x 1024 x 512 Gaussian-peak field (20,000 peaks, eb_rel 1e-4,
+    seed 3) in the launch configuration of the full-size test: the GPU's
+    corrected field, edit list and sweep log against the oracle's."""
+    spec = ("peaks", dict(shape=(512, 1024, 1024), seed=3, eb_rel=1e-4))
+    pool = oracle_pool.Pool(workers=1)
+    try:
+        job = pool.submit(spec)
+        fl = oracle_pool.make_field(spec)
+        f, fh = dev(fl.f), dev(fl.fhat)
+        cap = fl.n // 2
+        res = api.correct(f, fh, fl.xi, edit_capacity=cap, log_capacity=100000)
+        check(res, job.result())
+    finally:
+        pool.close()
