@@ -113,13 +113,23 @@ typedef struct {
                                  |worklist_k|, distorted_k, distinct targets_k, changed_k */
     int64_t log_capacity;
     int64_t *h_timeline;      /* NULL, or 2*log_capacity int64 (needs h_sweep_log): device
-                                 time in ns from the start of the correction kernel to the
-                                 end of sweep k's detection and of its edit phase (-1: none) */
+                                 time in ns from the start of the correction (sweep 0's pass)
+                                 to the end of sweep k's detection and of its edit phase
+                                 (-1: none) */
     int32_t tile_z;           /* z-planes per tile of the code pass (3D); at most 1024; 0: the
                                  deepest of 24, 16, 8 that gives every block of the persistent
                                  grid two tiles (msz_correct; the batch and relaxed entry points
                                  use 24).  Affects speed only (see the autotuner), never results */
     int32_t local_cap;        /* msz_correct_relaxed: local sweeps per tile run; 0: 65536 */
+    void *phase_events[3];    /* msz_correct and msz_correct_static only (other entry points
+                                 ignore them): each NULL or a cudaEvent_t of the current
+                                 device, recorded on the stream [0] before sweep 0's pass
+                                 over a 3D grid (its own kernel), [1] between that pass and
+                                 the kernel of the later sweeps and the edit list, [2] after
+                                 that kernel, so that cudaEventElapsedTime times each kernel
+                                 alone.  On 2D grids (one kernel) [0] and [1] are both
+                                 recorded before it.  A record that fails returns
+                                 MSZ_ERR_CUDA */
 } msz_options;
 
 typedef struct {

@@ -39,7 +39,8 @@ class Options(ctypes.Structure):
     _fields_ = [("rule", ctypes.c_int32), ("test_fault", ctypes.c_int32), ("max_sweeps", ctypes.c_int64),
                 ("dense_min_items", ctypes.c_int64), ("d_g_init", ctypes.c_void_p),
                 ("h_sweep_log", ctypes.c_void_p), ("log_capacity", ctypes.c_int64),
-                ("h_timeline", ctypes.c_void_p), ("tile_z", ctypes.c_int32), ("local_cap", ctypes.c_int32)]
+                ("h_timeline", ctypes.c_void_p), ("tile_z", ctypes.c_int32), ("local_cap", ctypes.c_int32),
+                ("phase_events", ctypes.c_void_p * 3)]
 
 
 class Stats(ctypes.Structure):
@@ -228,6 +229,16 @@ class CorrectResult:
         return self.status == OK
 
 
+def _event_handle(ev):
+    """The cudaEvent_t of a torch.cuda.Event (None: None); torch creates the
+    event at its first record, so an event never recorded is recorded once."""
+    if ev is None:
+        return None
+    if not ev.cuda_event:
+        ev.record()
+    return ev.cuda_event
+
+
 def _options(rule, max_sweeps, dense_min_items, g_init, log_capacity, tile_z=0, test_fault=0, local_cap=0):
     log = np.zeros(max(4 * log_capacity, 4), dtype=np.int64)
     tl = np.full(max(2 * log_capacity, 2), -1, dtype=np.int64)
@@ -243,8 +254,10 @@ def correct(f: torch.Tensor, fhat: torch.Tensor, xi: float, *, rule="halve", max
             dense_min_items: int = 0, g_init: torch.Tensor | None = None, edit_capacity: int | None = None,
             log_capacity: int = 0, out: torch.Tensor | None = None, edit_idx: torch.Tensor | None = None,
             edit_delta: torch.Tensor | None = None, ws: torch.Tensor | None = None, stream=None,
-            check: bool = False, tile_z: int = 0, test_fault: int = 0) -> CorrectResult:
-    """Run the correction loop on device tensors (msz_correct)."""
+            check: bool = False, tile_z: int = 0, test_fault: int = 0, events=None) -> CorrectResult:
+    """Run the correction loop on device tensors (msz_correct).  events:
+    three torch.cuda.Event (entries may be None) recorded before sweep 0's
+    pass, between it and the loop kernel, and after the loop kernel."""
     assert f.dtype == torch.float32 and fhat.dtype == torch.float32 and f.shape == fhat.shape
     lib = load()
     g = grid_of(f.shape)
@@ -260,6 +273,9 @@ def correct(f: torch.Tensor, fhat: torch.Tensor, xi: float, *, rule="halve", max
     if ws is None:
         ws = workspace(need, f.device)
     opt, log = _options(rule, max_sweeps, dense_min_items, g_init, log_capacity, tile_z, test_fault)
+    if events is not None:
+        for i, ev in enumerate(events):
+            opt.phase_events[i] = _event_handle(ev)
     stats = Stats()
     count = ctypes.c_int64()
     st = lib.msz_correct(_dptr(f), _dptr(fhat), ctypes.c_float(np.float32(xi)), g, _dptr(out),

@@ -47,12 +47,22 @@ constexpr uint32_t kDenseFactor = 6;        // worklist estimate: 6 x distorted 
 // planes per tile of the whole-grid TMA detection (measured on the 512^3
 // peak field: 4, 8, 16 and 32 planes within 1.5 % of one another; 16 best)
 constexpr uint32_t kDetectTileZ = MSZ_DETECT_TILE_Z;
+// a sweep keeps chunk flags when its worklist is bounded by this many
+// vertices (measured on the 512^3 peak field, kernel time with bounds of
+// 2^10, 2^13, 2^16, 2^19, 2^22: 16.0, 15.4, 15.2, 15.2, 15.3 ms; 16.2 ms
+// without flags)
+#ifndef MSZ_SPARSE_WORKLIST
+#define MSZ_SPARSE_WORKLIST (1ull << 19)
+#endif
+constexpr unsigned long long kSparseWorklist = MSZ_SPARSE_WORKLIST;
 
 struct Problem {
     CUtensorMap map_f;  // TMA maps of f, of the start field and of g (the TMA passes only)
     CUtensorMap map_s;
     CUtensorMap map_g;
     FieldView F;
+    uint32_t *stb;     // chunk flags of F.tb, F.dm[0], F.dm[1] (kept in sparse sweeps)
+    uint32_t *sdm[2];
     Ctrl *ctrl;
     SweepRec *log;
     uint32_t *bsum;
@@ -66,6 +76,31 @@ struct Problem {
     uint32_t detect_tile_z;  // planes per tile of the whole-grid TMA detection
 };
 
+// ------------------------------------------------ sweep 0's pass over a 3D grid
+// The codes of f with their certification, g = start, the bound check and
+// sweep 0's detection, in a kernel of its own: its staging ring is the
+// largest shared-memory user of the correction, and as a separate launch it
+// leaves the loop kernel's L1 (which its gathering phases need) alone.  The
+// kernel boundary orders its writes before the loop kernel.
+template <bool TMA>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_codes(__grid_constant__ const Problem P) {
+    extern __shared__ __align__(16) float smem[];
+    const FieldView &F = P.F;
+    Ctrl *C = P.ctrl;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        C->t_start = global_ns();
+        P.log[0].worklist = F.G.n;
+        C->examined = F.G.n;
+        C->dense_sweeps = 1;
+    }
+    uint32_t distorted = 0;
+    if (TMA)
+        first_tiled_tma<true>(F, &P.map_f, &P.map_s, &P.log[0].tile_next, smem, &C->error, distorted,
+                              P.test_fault == 2);
+    else first_tiled<true>(F, &P.log[0].tile_next, smem, &C->error, distorted);
+    warp_add(distorted, &P.log[0].distorted);
+}
+
 // ------------------------------------------------------ the persistent kernel
 template <int NDIM, bool TMA>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constant__ const Problem P) {
@@ -77,30 +112,25 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
     const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t stride = gridDim.x * blockDim.x;
     const bool leader = gtid == 0;
-    if (leader) C->t_start = global_ns();
 
     // ---- sweep 0: codes of f with their certification, g = start, bound
     // check, and the detection of sweep 0 (only uncertified vertices can be
-    // distorted).  3D tiles detect their own uncertified vertices from the
-    // staged start field; 2D grids detect in a second phase.
-    if (leader) {
-        P.log[0].worklist = G.n;
-        C->examined = G.n;
-        C->dense_sweeps = 1;
-    }
+    // distorted).  On 3D grids k_codes ran it (tiles detect their own
+    // uncertified vertices from the staged start field); 2D grids take it
+    // here, the detection in a second phase.
     bool ok;
     if (NDIM == 3) {
-        uint32_t distorted = 0;
-        if (TMA)
-            first_tiled_tma<true>(F, &P.map_f, &P.map_s, &P.log[0].tile_next, smem, &C->error, distorted,
-                                  P.test_fault == 2);
-        else first_tiled<true>(F, &P.log[0].tile_next, smem, &C->error, distorted);
-        warp_add(distorted, &P.log[0].distorted);
-        ok = P.test_fault == 1
-                 ? grid_barrier(&C->bar_count, &C->bar_gen, &C->error, kTestBarrierNs, blockIdx.x == 0)
-                 : grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
+        ok = ld_relaxed(&C->error) == 0;  // every block reads k_codes' verdict
+        if (ok && P.test_fault == 1)
+            ok = grid_barrier(&C->bar_count, &C->bar_gen, &C->error, kTestBarrierNs, blockIdx.x == 0);
         if (leader) C->t_codes = global_ns();
     } else {
+        if (leader) {
+            C->t_start = global_ns();
+            P.log[0].worklist = G.n;
+            C->examined = G.n;
+            C->dense_sweeps = 1;
+        }
         first_generic<NDIM>(F, &C->error);
         ok = P.test_fault == 1
                  ? grid_barrier(&C->bar_count, &C->bar_gen, &C->error, kTestBarrierNs, blockIdx.x == 0)
@@ -117,6 +147,13 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
         ok = ok && grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
     }
     if (leader) P.log[0].t_detect = global_ns();
+    // Chunk flags are kept only in sparse sweeps (a dense sweep would store
+    // them millions of times over for no walk that skips anything).
+    // sum_k: the phases of sweep k keep them -- decided before sweep k's
+    // detection from a bound on its worklist (15 x changed + distorted of
+    // sweep k-1), so that every mark into sweep k's targets and into the next
+    // worklist sets its chunk's flag whenever a walk relies on it.
+    bool sum_k = false;  // sweep 0 keeps none
     uint32_t k = 0;
     while (ok) {
         const uint32_t m = ld_relaxed(&P.log[k].distorted);
@@ -127,7 +164,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
         if (k >= P.max_sweeps) {
             // count the distinct targets this sweep found, for the record
             uint32_t nt = 0;
-            walk_bits<true>(F.tb, nullptr, G, nt, [&](bool, uint32_t) {});
+            if (!sum_k) walk_bits<true>(F.tb, nullptr, G, nt, [&](bool, uint32_t) {});
+            else walk_flagged<true, false>(F.tb, P.stb, nullptr, G, nt, [&](bool, uint32_t) {});
             warp_add(nt, &P.log[k].targets);
             if (leader) { C->status = MSZ_ERR_MAX_SWEEPS; C->sweeps = k; C->left = m; }
             ok = grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
@@ -135,13 +173,22 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
         }
         const bool dense_next =
             P.dense_min >= 0 && (unsigned long long)m * kDenseFactor >= (unsigned long long)P.dense_min;
-        // ---- edit phase of sweep k (Eq. 1), one application per distinct target
+        // ---- edit phase of sweep k (Eq. 1), one application per distinct target.
+        // In a sparse sweep the targets and the next worklist carry chunk
+        // flags, so the walks visit only the chunks that may hold set bits.
         {
             uint32_t *dnext = F.dm[(k + 1) & 1];
             uint32_t targets = 0, changed_here = 0;
-            walk_bits<true>(F.tb, nullptr, G, targets, [&](bool has, uint32_t t) {
-                if (has && apply_target<NDIM>(F, t, dense_next, dnext)) ++changed_here;
-            });
+            if (!sum_k) {
+                walk_bits<true>(F.tb, nullptr, G, targets, [&](bool has, uint32_t t) {
+                    if (has && apply_target<NDIM>(F, t, dense_next, dnext)) ++changed_here;
+                });
+            } else {
+                uint32_t *dsum = P.sdm[(k + 1) & 1];
+                walk_flagged<true, false>(F.tb, P.stb, nullptr, G, targets, [&](bool has, uint32_t t) {
+                    if (has && apply_target<NDIM>(F, t, dense_next, dnext, dsum)) ++changed_here;
+                });
+            }
             if (TMA && dense_next) tma::fence_proxy_async_global();  // g is read by TMA next
             warp_add(targets, &P.log[k].targets);
             warp_add(changed_here, &P.log[k].changed);
@@ -155,10 +202,15 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
             break;
         }
         if (leader) C->edits += changed_k;
+        const bool sum_k1 = 15ull * changed_k + m <= kSparseWorklist;
         // ---- detection phase of sweep k + 1
+        // Detection of sweep k1 keeps flags of its targets and of the next
+        // worklist when sum_k1; the current worklist has them when sweep k
+        // kept them (sum_k).
         const uint32_t k1 = k + 1;
-        Emitter E{F.dm[(k1 + 1) & 1], 0};
+        Emitter E{F.dm[(k1 + 1) & 1], 0, sum_k1 ? P.sdm[(k1 + 1) & 1] : nullptr, sum_k1 ? P.stb : nullptr};
         uint32_t *dcur = F.dm[k1 & 1];
+        uint32_t *dcur_sum = sum_k ? P.sdm[k1 & 1] : nullptr;
         uint32_t seen = 0;
         if (dense_next) {
             // whole grid: every uncertified vertex
@@ -168,18 +220,27 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
                 C->dense_sweeps += 1;
             }
             for (uint32_t w = gtid; w < G.words; w += stride) dcur[w] = 0;
+            if (dcur_sum)
+                for (uint32_t w = gtid; w < (uint32_t)chunk_count(G.words); w += stride) dcur_sum[w] = 0;
             if (TMA) {
                 detect_tiled_tma(F, P.detect_tile_z, &P.map_g, &P.log[k1].tile_next, smem, &C->error, E.dnext,
-                                 E.distorted);
+                                 E.distorted, E.dsum, E.tsum);
             } else if (NDIM == 3) {
-                detect_tiled_cp(F, P.detect_tile_z, &P.log[k1].tile_next, smem, E.dnext, E.distorted);
+                detect_tiled_cp(F, P.detect_tile_z, &P.log[k1].tile_next, smem, E.dnext, E.distorted, E.dsum,
+                                E.tsum);
             } else {
                 walk_bits_pairs<false>(F.ub, nullptr, G, seen, [&](bool h1, uint32_t v1, bool h2, uint32_t v2) {
                     detect_vertex2<NDIM>(F, E, h1, v1, h2, v2);
                 });
             }
+        } else if (dcur_sum) {
+            // the worklist, restricted to uncertified vertices, flagged chunk by flagged chunk
+            walk_flagged<true, true>(dcur, dcur_sum, F.ub, G, seen, [&](bool h1, uint32_t v1, bool h2, uint32_t v2) {
+                detect_vertex2<NDIM>(F, E, h1, v1, h2, v2);
+            });
+            warp_add(seen, &P.log[k1].worklist);
         } else {
-            // the worklist, restricted to uncertified vertices
+            // a worklist without flags (sweep 1's, built by sweep 0, and a dense sweep's)
             walk_bits_pairs<true>(dcur, F.ub, G, seen, [&](bool h1, uint32_t v1, bool h2, uint32_t v2) {
                 detect_vertex2<NDIM>(F, E, h1, v1, h2, v2);
             });
@@ -192,6 +253,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
             if (!dense_next) C->examined += P.log[k1].worklist;
         }
         k = k1;
+        sum_k = sum_k1;
     }
     if (!ok) return;
 
@@ -314,25 +376,31 @@ msz_status current_device(DeviceInfo &info) {
     return MSZ_OK;
 }
 
+// Dynamic shared memory: the loop kernel stages one field for its whole-grid
+// detection (TMA, or the cp.async ring on other 3D grids); k_codes stages f
+// and the start field.
 template <int NDIM, bool TMA>
-static size_t correct_smem() { return NDIM == 3 ? (TMA ? tile::kTmaRingBytes : tile::kRingBytes) : 0; }
+static size_t correct_smem() {
+    return NDIM == 3 ? (TMA ? tile::tma_ring_bytes(tile::kDetectSlots, 1) : tile::kRingBytes) : 0;
+}
+template <bool TMA>
+static size_t codes_smem() {
+    return TMA ? tile::tma_ring_bytes(tile::kCodeSlots, 2) : tile::kRingBytes;
+}
 
-template <int NDIM, bool TMA>
-static msz_status correct_blocks(const DeviceInfo &d, int &blocks) {
-    static int cache[64];
+// Resident blocks of kernel fn with sm bytes of dynamic shared memory, times
+// the SM count (the persistent grid).  The attribute belongs to the current
+// context, so it is set on every call (a context re-created after
+// cudaDeviceReset starts without it); the occupancy it allows is a property of
+// the device and is cached in *cache.
+template <class K>
+static msz_status persistent_blocks(K fn, size_t sm, const DeviceInfo &d, int *cache, int &blocks) {
     std::lock_guard<std::mutex> lk(g_mu);
-    const size_t sm = correct_smem<NDIM, TMA>();
-    // the attribute belongs to the current context, so it is set on every
-    // call (a context re-created after cudaDeviceReset starts without it);
-    // the occupancy it allows is a property of the device and is cached
-    if (sm > 48 * 1024 &&
-        cudaFuncSetAttribute(k_correct<NDIM, TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
-            cudaSuccess)
+    if (sm > 48 * 1024 && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
         return MSZ_ERR_CUDA;
     if (!cache[d.device]) {
         int per = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_correct<NDIM, TMA>, kThreads, sm) != cudaSuccess)
-            return MSZ_ERR_CUDA;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kThreads, sm) != cudaSuccess) return MSZ_ERR_CUDA;
         if (per < 1) return MSZ_ERR_UNSUPPORTED;
         int b = per * d.sms;
         if (b > (int)kMaxBlocks) b = (int)kMaxBlocks;
@@ -340,6 +408,18 @@ static msz_status correct_blocks(const DeviceInfo &d, int &blocks) {
     }
     blocks = cache[d.device];
     return MSZ_OK;
+}
+
+template <int NDIM, bool TMA>
+static msz_status correct_blocks(const DeviceInfo &d, int &blocks) {
+    static int cache[64];
+    return persistent_blocks(k_correct<NDIM, TMA>, correct_smem<NDIM, TMA>(), d, cache, blocks);
+}
+
+template <bool TMA>
+static msz_status codes_blocks(const DeviceInfo &d, int &blocks) {
+    static int cache[64];
+    return persistent_blocks(k_codes<TMA>, codes_smem<TMA>(), d, cache, blocks);
 }
 
 // Default planes per tile of the code pass: the deepest of kTileZ (24), 16,
@@ -390,17 +470,32 @@ static bool plane_map(const float *v, const GridDev &G, CUtensorMap &map) {
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NAN_REQUEST_ZERO_FMA) == CUDA_SUCCESS;
 }
 
+// Records the caller's timing event ev (if any) on the stream.
+static msz_status record(void *ev, cudaStream_t stream) {
+    return !ev || cudaEventRecord((cudaEvent_t)ev, stream) == cudaSuccess ? MSZ_OK : MSZ_ERR_CUDA;
+}
+
 template <int NDIM, bool TMA>
-static msz_status launch_correct(Problem &P, const DeviceInfo &dev, cudaStream_t stream) {
+static msz_status launch_correct(Problem &P, const DeviceInfo &dev, cudaStream_t stream, void *const *ev) {
     int blocks = 0;
     msz_status st = correct_blocks<NDIM, TMA>(dev, blocks);
     if (st != MSZ_OK) return st;
-    if (P.F.tile_z == 0) P.F.tile_z = default_tile_z(P.F.G, blocks);
+    if ((st = record(ev[0], stream)) != MSZ_OK) return st;
+    if (NDIM == 3) {
+        // sweep 0's pass first, as its own persistent launch (no grid-wide
+        // wait inside it: an ordinary launch)
+        int cblocks = 0;
+        if ((st = codes_blocks<TMA>(dev, cblocks)) != MSZ_OK) return st;
+        if (P.F.tile_z == 0) P.F.tile_z = default_tile_z(P.F.G, cblocks);
+        k_codes<TMA><<<cblocks, kThreads, codes_smem<TMA>(), stream>>>(P);
+        if (cudaGetLastError() != cudaSuccess) return MSZ_ERR_CUDA;
+    }
+    if ((st = record(ev[1], stream)) != MSZ_OK) return st;
     void *args[] = {(void *)&P};
     if (cudaLaunchCooperativeKernel((const void *)k_correct<NDIM, TMA>, dim3(blocks), dim3(kThreads), args,
                                     correct_smem<NDIM, TMA>(), stream) != cudaSuccess)
         return MSZ_ERR_CUDA;
-    return MSZ_OK;
+    return record(ev[2], stream);
 }
 
 // Default whole-grid detection rule (P.dense_min == 0).  A tiled whole-grid
@@ -413,16 +508,16 @@ static msz_status launch_correct(Problem &P, const DeviceInfo &dev, cudaStream_t
 // default is N: the whole-grid pass only when nearly every vertex is on the
 // worklist anyway.  2D grids keep worklists (their whole-grid walk gathers).
 template <int NDIM>
-static msz_status run_correct(Problem &P, const DeviceInfo &dev, cudaStream_t stream) {
+static msz_status run_correct(Problem &P, const DeviceInfo &dev, cudaStream_t stream, void *const *ev) {
     if constexpr (NDIM == 3) {
         if (tma_eligible(P.F) && plane_map(P.F.f, P.F.G, P.map_f) &&
             plane_map(P.F.ginit ? P.F.ginit : P.F.fhat, P.F.G, P.map_s) && plane_map(P.F.g, P.F.G, P.map_g)) {
             if (P.dense_min == 0) P.dense_min = (long long)P.F.G.n;
-            return launch_correct<3, true>(P, dev, stream);
+            return launch_correct<3, true>(P, dev, stream, ev);
         }
     }
     if (P.dense_min == 0) P.dense_min = NDIM == 3 ? (long long)P.F.G.n : -1;
-    return launch_correct<NDIM, false>(P, dev, stream);
+    return launch_correct<NDIM, false>(P, dev, stream, ev);
 }
 
 }  // namespace msz
@@ -506,6 +601,9 @@ static msz_status prepare_correct(const float *d_f, const float *d_fhat, float x
     F.two_xi = 2.0f * xi;  // exact (power-of-two scaling), +inf on overflow
     F.rule = o.rule;
     F.tile_z = o.tile_z > 0 ? (uint32_t)o.tile_z : 0u;  // 0: chosen from the grid and the launch
+    P.stb = (uint32_t *)(ws + L.stb);
+    P.sdm[0] = (uint32_t *)(ws + L.sd0);
+    P.sdm[1] = (uint32_t *)(ws + L.sd1);
     P.ctrl = (Ctrl *)(ws + L.ctrl);
     P.log = (SweepRec *)(ws + L.log);
     P.bsum = (uint32_t *)(ws + L.bsum);
@@ -520,11 +618,14 @@ static msz_status prepare_correct(const float *d_f, const float *d_fhat, float x
     return MSZ_OK;
 }
 
-static msz_status enqueue_correct(Problem &P, const DeviceInfo &dev, cudaStream_t s) {
+// ev: the caller's three timing events (entries may be null), or null.
+static msz_status enqueue_correct(Problem &P, const DeviceInfo &dev, cudaStream_t s, void *const *ev = nullptr) {
+    static void *const kNoEvents[3] = {nullptr, nullptr, nullptr};
+    if (!ev) ev = kNoEvents;
     if (cudaMemsetAsync(P.ctrl, 0, layout_for(P.F.G.n).zero_bytes, s) != cudaSuccess) return MSZ_ERR_CUDA;
     // BELOW_REFERENCE: no candidate yet anywhere (all-ones keys)
     if (P.F.cand && cudaMemsetAsync(P.F.cand, 0xff, (size_t)P.F.G.n * 4u, s) != cudaSuccess) return MSZ_ERR_CUDA;
-    return P.F.G.ndim == 3 ? run_correct<3>(P, dev, s) : run_correct<2>(P, dev, s);
+    return P.F.G.ndim == 3 ? run_correct<3>(P, dev, s, ev) : run_correct<2>(P, dev, s, ev);
 }
 
 // Status, edit count and stats from the control block and the record of
@@ -567,7 +668,7 @@ extern "C" msz_status msz_correct(const float *d_f, const float *d_fhat, float x
     DeviceInfo dev;
     if ((st = current_device(dev)) != MSZ_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    if ((st = enqueue_correct(P, dev, s)) != MSZ_OK) return st;
+    if ((st = enqueue_correct(P, dev, s, o.phase_events)) != MSZ_OK) return st;
     // the control block and sweep 0's record in one read-back (the log
     // follows the control block in the workspace)
     static_assert(offsetof(Layout, ctrl) == 0, "layout order");

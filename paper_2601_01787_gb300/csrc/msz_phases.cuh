@@ -48,10 +48,19 @@ struct FieldView {
 // Where a detection phase records: the targets (P.tb) and the worklist of the
 // next sweep (dnext); distorted vertices are counted per thread and added to
 // the sweep's record when the phase ends.
+// A phase that keeps chunk flags (one word per chunk of 32 bitmap words,
+// 1024 vertices, nonzero when the chunk may hold a set bit) sets them through
+// dsum (the next worklist's) and tsum (the targets').
 struct Emitter {
     uint32_t *dnext;
     uint32_t distorted;
+    uint32_t *dsum = nullptr;  // chunk flags of dnext, or null
+    uint32_t *tsum = nullptr;  // chunk flags of P.tb, or null
 };
+
+// Sets the flag of the chunk (32 words, 1024 vertices) holding vertex v of a
+// bitmap: a plain store of 1 (every writer stores the same value).
+__device__ __forceinline__ void mark_chunk(uint32_t *sum, uint32_t v) { st_relaxed(&sum[v >> 10], 1u); }
 
 // BELOW_REFERENCE: the value target t asks for to fall below reference r
 // (value vr of this sweep) in the (value, index) order -- vr when r has the
@@ -76,6 +85,10 @@ __device__ __forceinline__ bool report(const FieldView &P, Emitter &E, bool vali
         const int nt = targets_of(P.G, v, (uint8_t)cf, (uint8_t)cg, t0, t1);
         red_or(&P.tb[t0 >> 5], 1u << (t0 & 31u));
         if (nt > 1) red_or(&P.tb[t1 >> 5], 1u << (t1 & 31u));
+        if (E.tsum) {
+            mark_chunk(E.tsum, t0);
+            if (nt > 1) mark_chunk(E.tsum, t1);
+        }
         if (P.cand) {
             uint32_t r0, r1;
             references_of(P.G, v, (uint8_t)cf, (uint8_t)cg, r0, r1);
@@ -83,7 +96,10 @@ __device__ __forceinline__ bool report(const FieldView &P, Emitter &E, bool vali
             request_below(P, t0, r0, gk[r0]);
             if (nt > 1) request_below(P, t1, r1, gk[r1]);
         }
-        if (!self_marked) red_or(&E.dnext[v >> 5], 1u << (v & 31u));
+        if (!self_marked) {
+            red_or(&E.dnext[v >> 5], 1u << (v & 31u));
+            if (E.dsum) mark_chunk(E.dsum, v);
+        }
         E.distorted += 1;
     }
     return dist;
@@ -244,6 +260,51 @@ __device__ __forceinline__ void walk_bits_pairs(uint32_t *bm, const uint32_t *fi
             if (bits && !word_ok(wi)) bits = 0u;
         }
         chunk_pairs(base, bits, fn);
+    }
+}
+
+// walk_bits / walk_bits_pairs over the chunks (32 words) whose flags are
+// set.  Chunk c belongs to warp c mod (warps of the grid), as in walk_bits,
+// so that a cluster of flagged chunks spreads over many warps.  A warp reads
+// the flags of 32 of its chunks at once (one per lane), then walks the
+// flagged ones, loading the words of the next flagged chunk before the
+// current one is handed out.  CLEAR zeroes the visited words and flags.
+// PAIRS: two vertices per lane per round (chunk_pairs), else one (chunk_each).
+template <bool CLEAR, bool PAIRS, class F>
+__device__ __forceinline__ void walk_flagged(uint32_t *bm, uint32_t *flags, const uint32_t *filter, const GridDev &G,
+                                             uint32_t &seen, F &&fn) {
+    const uint32_t lane = lane_id();
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t chunks = (G.words + 31u) / 32u;
+    for (uint32_t c0 = gw; c0 < chunks; c0 += 32u * nw) {
+        const uint32_t mine = c0 + lane * nw;  // this lane's chunk of the round
+        const bool set = mine < chunks && flags[mine] != 0u;
+        if (CLEAR && set) flags[mine] = 0u;
+        uint32_t marks = __ballot_sync(kFull, set);
+        if (!marks) continue;
+        uint32_t c = c0 + (uint32_t)(__ffs(marks) - 1) * nw;
+        marks &= marks - 1u;
+        uint32_t nxt = c * 32u + lane < G.words ? bm[c * 32u + lane] : 0u;
+        for (;;) {
+            const uint32_t base = c * 32u;
+            const uint32_t wi = base + lane;
+            uint32_t bits = nxt;
+            const bool more = marks != 0u;
+            if (more) {
+                c = c0 + (uint32_t)(__ffs(marks) - 1) * nw;
+                marks &= marks - 1u;
+                nxt = c * 32u + lane < G.words ? bm[c * 32u + lane] : 0u;
+            }
+            if (bits) {
+                if (CLEAR) bm[wi] = 0u;
+                seen += (uint32_t)__popc(bits);
+                if (filter) bits &= filter[wi];
+            }
+            if constexpr (PAIRS) chunk_pairs(base, bits, fn);
+            else chunk_each(base, bits, fn);
+            if (!more) break;
+        }
     }
 }
 
@@ -657,7 +718,8 @@ __device__ __forceinline__ void first_tile(const FieldView &P, int x0, int y0, i
 // mark their targets and themselves in dnext and add to `distorted`.
 // Block-collective; the caller synchronizes the block before the next tile.
 __device__ __forceinline__ void detect_tile_cp(const FieldView &P, int x0, int y0, int zb, int ze, float *smem,
-                                               uint32_t *dnext, uint32_t &distorted) {
+                                               uint32_t *dnext, uint32_t &distorted, uint32_t *dsum = nullptr,
+                                               uint32_t *tsum = nullptr) {
     using namespace tile;
     const GridDev &G = P.G;
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
@@ -725,7 +787,7 @@ __device__ __forceinline__ void detect_tile_cp(const FieldView &P, int x0, int y
             if ((valid >> e) & 1u) cb[e] = __ldg(&P.codes_f[i0 + e]);
     };
     fetch(zb);
-    Emitter E{dnext, 0};
+    Emitter E{dnext, 0, dsum, tsum};
     for (int z = zb; z < ze; ++z) {
         cp_async_wait<1>();
         __syncthreads();
@@ -773,7 +835,8 @@ __device__ __forceinline__ void detect_tile_cp(const FieldView &P, int x0, int y
 // Whole-grid detection of a later sweep over the tiles of one field (the
 // cp.async form; block-collective).
 __device__ __forceinline__ void detect_tiled_cp(const FieldView &P, uint32_t tile_z, uint32_t *tile_next, float *smem,
-                                                uint32_t *dnext, uint32_t &distorted) {
+                                                uint32_t *dnext, uint32_t &distorted, uint32_t *dsum = nullptr,
+                                               uint32_t *tsum = nullptr) {
     using namespace tile;
     const GridDev &G = P.G;
     const TileGeom tg = tile_geom(G.nx, G.ny, G.nz, tile_z);
@@ -787,7 +850,7 @@ __device__ __forceinline__ void detect_tiled_cp(const FieldView &P, uint32_t til
         const uint32_t txi = t % tg.tx, tyi = (t / tg.tx) % tg.ty, tzi = t / (tg.tx * tg.ty);
         const int zb = (int)(tzi * tg.bz);
         detect_tile_cp(P, (int)(txi * BX), (int)(tyi * BY), zb, min(zb + (int)tg.bz, (int)G.nz), smem, dnext,
-                       distorted);
+                       distorted, dsum, tsum);
     }
 }
 
@@ -824,7 +887,7 @@ __device__ __forceinline__ void first_tiled(const FieldView &P, uint32_t *tile_n
 // slot's mbarrier, and out-of-grid positions arrive as NaN from the maps'
 // fill mode.  Warps never wait for one another inside a tile: each waits only
 // for the planes it needs, and the last warp to finish with a plane refills
-// its slot with the plane TSLOTS further on, so fast warps run ahead of slow
+// its slot with the plane NS further on, so fast warps run ahead of slow
 // ones by up to the planes in flight.  Every wait is bounded; a wait that runs out
 // records kErrTimeout, stops the block's tiles and, before leaving, waits
 // (bounded) for the block's copies still in flight.
@@ -874,7 +937,7 @@ __device__ __forceinline__ void own_row_tma(const FieldView &P, const float *p0,
 // row z alone (two false) when the tile's last plane is z.  withhold (a test
 // hook): block 0 never issues its first plane, so its waits run out after
 // kTestWaitNs.
-template <int NBOX, int STEP, class ROW>
+template <int NBOX, int STEP, int NS, class ROW>
 __device__ __forceinline__ void tma_tiles(const FieldView &P, uint32_t tile_z, const CUtensorMap *map0,
                                           const CUtensorMap *map1, uint32_t *tile_next, float *smem_raw,
                                           uint32_t *err, ROW &&row, bool withhold = false) {
@@ -883,7 +946,7 @@ __device__ __forceinline__ void tma_tiles(const FieldView &P, uint32_t tile_z, c
     const TileGeom tg = tile_geom(G.nx, G.ny, G.nz, tile_z);
     constexpr uint32_t kWarps = THREADS / 32;
     __shared__ uint32_t s_tile;
-    constexpr int NS = TSLOTS;
+    constexpr int TSLOT = NBOX * TFIELD;  // floats of one slot
     __shared__ __align__(8) uint64_t s_full[NS];
     __shared__ uint32_t s_rel[NS];
     __shared__ uint32_t s_pending[NS];
@@ -993,7 +1056,7 @@ __device__ __forceinline__ void first_tiled_tma(const FieldView &P, const CUtens
                                                 uint32_t *tile_next, float *smem_raw, uint32_t *err,
                                                 uint32_t &distorted, bool withhold = false) {
     bool bad = false;
-    tma_tiles<2, 2>(
+    tma_tiles<2, 2, tile::kCodeSlots>(
         P, P.tile_z, map_f, map_s, tile_next, smem_raw, err,
         [&](const float *pm, const float *p0, const float *pp, const float *pq, int r, int x0, uint32_t rowbase,
             bool two) {
@@ -1015,13 +1078,14 @@ __device__ __forceinline__ void first_tiled_tma(const FieldView &P, const CUtens
 // overlaps the examination and the wait for the next staged plane.
 __device__ __forceinline__ void detect_tiled_tma(const FieldView &P, uint32_t tile_z, const CUtensorMap *map_g,
                                                  uint32_t *tile_next, float *smem_raw, uint32_t *err,
-                                                 uint32_t *dnext, uint32_t &distorted) {
+                                                 uint32_t *dnext, uint32_t &distorted, uint32_t *dsum = nullptr,
+                                               uint32_t *tsum = nullptr) {
     using namespace tile;
     const GridDev &G = P.G;
     // the prefetched row: index of the tile row's first vertex (x0, y, z),
     // this lane's raw bitmap word and codes
     uint32_t pf_row = 0xffffffffu, pf_ubw = 0, pf_cfw = 0;
-    tma_tiles<1, 1>(P, tile_z, map_g, nullptr, tile_next, smem_raw, err,
+    tma_tiles<1, 1, tile::kDetectSlots>(P, tile_z, map_g, nullptr, tile_next, smem_raw, err,
                     [&](const float *pm, const float *p0, const float *pp, const float *, int r, int x0,
                         uint32_t rowbase, bool) {
                      const uint32_t lane = lane_id();
@@ -1059,7 +1123,7 @@ __device__ __forceinline__ void detect_tiled_tma(const FieldView &P, uint32_t ti
                      const uint32_t w2 = __shfl_sync(kFull, w, 16), w3 = __shfl_sync(kFull, w, 24);
                      const uint32_t c0 = (uint32_t)__popc(w0), c1 = c0 + (uint32_t)__popc(w1);
                      const uint32_t c2 = c1 + (uint32_t)__popc(w2), total = c2 + (uint32_t)__popc(w3);
-                     Emitter E{dnext, 0};
+                     Emitter E{dnext, 0, dsum, tsum};
                      for (uint32_t j0 = 0; j0 < total; j0 += 32u) {
                          const uint32_t j = j0 + lane;
                          const bool has = j < total;
@@ -1080,10 +1144,15 @@ __device__ __forceinline__ void detect_tiled_tma(const FieldView &P, uint32_t ti
 
 // Sets the bits of up to 3 consecutive vertices j0, j0+1, j0+2 (bit k of m
 // for vertex j0+k) with one reduction per bitmap word touched.
-__device__ __forceinline__ void mark_run(uint32_t *bm, uint32_t j0, uint32_t m) {
+__device__ __forceinline__ void mark_run(uint32_t *bm, uint32_t j0, uint32_t m, uint32_t *sum = nullptr) {
     const uint32_t w = j0 >> 5, s = j0 & 31u;
     red_or(&bm[w], m << s);
-    if (s && (m >> (32u - s))) red_or(&bm[w + 1], m >> (32u - s));
+    const bool spill = s && (m >> (32u - s));
+    if (spill) red_or(&bm[w + 1], m >> (32u - s));
+    if (sum) {
+        mark_chunk(sum, j0);
+        if (spill && ((w + 1u) >> 5) != (w >> 5)) mark_chunk(sum, j0 + 32u);
+    }
 }
 
 // Marks vertex t and its neighbours in bitmap bm.  The closed neighbourhood
@@ -1092,15 +1161,15 @@ __device__ __forceinline__ void mark_run(uint32_t *bm, uint32_t j0, uint32_t m) 
 // (y-1, z-1) at x-1, x; (y+1, z), (y, z+1) and (y+1, z+1) at x, x+1.  One
 // reduction marks a run (two where it crosses a word).
 template <int NDIM>
-__device__ __forceinline__ void mark_closed(const GridDev &G, uint32_t t, uint32_t *bm) {
+__device__ __forceinline__ void mark_closed(const GridDev &G, uint32_t t, uint32_t *bm, uint32_t *sum = nullptr) {
     uint32_t x, y, z;
     coords_of(G, t, x, y, z);
     // bit 0: x-1, bit 1: x, bit 2: x+1 -- dropped outside the grid
     const uint32_t xm = x > 0 ? 1u : 0u, xp = x + 1 < G.nx ? 4u : 0u;
     auto row = [&](uint32_t rt, uint32_t m) {
         m &= xm | 2u | xp;
-        if (x == 0) mark_run(bm, rt, m >> 1);
-        else mark_run(bm, rt - 1u, m);
+        if (x == 0) mark_run(bm, rt, m >> 1, sum);
+        else mark_run(bm, rt - 1u, m, sum);
     };
     const uint32_t nx = G.nx, nxy = G.nxy;
     row(t, 7u);
@@ -1142,11 +1211,12 @@ __device__ __forceinline__ bool edit_target(const FieldView &P, uint32_t t) {
 // edited bitmap and, unless the next sweep scans densely, its closed
 // neighbourhood in the next worklist.  Returns whether g_t decreased.
 template <int NDIM>
-__device__ __forceinline__ bool apply_target(const FieldView &P, uint32_t t, bool dense_next, uint32_t *dnext) {
+__device__ __forceinline__ bool apply_target(const FieldView &P, uint32_t t, bool dense_next, uint32_t *dnext,
+                                             uint32_t *dsum = nullptr) {
     if (!edit_target(P, t)) return false;
     red_or(&P.eb[t >> 5], 1u << (t & 31u));
     if (dense_next) return true;
-    mark_closed<NDIM>(P.G, t, dnext);
+    mark_closed<NDIM>(P.G, t, dnext, dsum);
     return true;
 }
 

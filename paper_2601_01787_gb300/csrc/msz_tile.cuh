@@ -54,14 +54,17 @@ constexpr size_t kRingBytes = (size_t)NSLOT * SLOT * sizeof(float);
 // boundary.
 constexpr int TBOX = ROWS * PW;                                  // 1360 floats
 constexpr int TFIELD = 1376;                                     // 5504 bytes
-constexpr int TSLOT = 2 * TFIELD;
 constexpr uint32_t kTboxBytes = (uint32_t)TBOX * sizeof(float);  // 5440
-// slots of the TMA ring: the code pass takes two planes a step (rows z and
-// z+1 use planes z-1 .. z+2) with one more in flight (a sixth slot measured
-// slower: the larger ring leaves less of the SM's memory to L1, which the
-// gathering phases of the loop need)
-constexpr int TSLOTS = 5;
-constexpr size_t kTmaRingBytes = (size_t)TSLOTS * TSLOT * sizeof(float) + 128;  // + alignment slack
+// Slots of the TMA rings.  The code pass takes two planes a step (rows z and
+// z+1 use planes z-1 .. z+2) with two more in flight; it runs as a kernel of
+// its own, so its ring does not shrink the L1 of the loop kernel, whose
+// whole-grid detection stages one field a step with one plane in flight.
+constexpr int kCodeSlots = 6;
+constexpr int kDetectSlots = 5;
+// ring bytes for `slots` slots of `nbox` boxes (+ alignment slack)
+constexpr size_t tma_ring_bytes(int slots, int nbox) {
+    return (size_t)slots * nbox * TFIELD * sizeof(float) + 128;
+}
 static_assert(TFIELD >= TBOX && (TFIELD * 4) % 128 == 0, "TMA boxes must start on 128-byte boundaries");
 
 struct TileGeom {

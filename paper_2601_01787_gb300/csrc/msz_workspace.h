@@ -51,9 +51,13 @@ constexpr size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign;
 // Byte offsets of each region for a grid of n vertices (bitmaps: one bit per
 // vertex).
 struct Layout {
-    size_t ctrl, log, bsum, tb, d0, d1, eb, ub, codes, total;
+    size_t ctrl, log, bsum, tb, d0, d1, eb, ub, stb, sd0, sd1, codes, total;
     size_t zero_bytes;  // [0, zero_bytes) is cleared at the start of every call
 };
+
+// Chunk flags of a bitmap: one word per chunk of 32 bitmap words (1024
+// vertices), nonzero when the chunk may hold a set bit.
+__host__ __device__ constexpr uint64_t chunk_count(uint64_t words) { return (words + 31) / 32; }
 
 constexpr Layout layout_for(uint64_t n) {
     Layout L{};
@@ -67,6 +71,9 @@ constexpr Layout layout_for(uint64_t n) {
     L.d1 = o;     o = align_up(o + words * 4);
     L.eb = o;     o = align_up(o + words * 4);
     L.ub = o;     o = align_up(o + words * 4);
+    L.stb = o;    o = align_up(o + chunk_count(words) * 4);
+    L.sd0 = o;    o = align_up(o + chunk_count(words) * 4);
+    L.sd1 = o;    o = align_up(o + chunk_count(words) * 4);
     L.zero_bytes = o;
     L.codes = o;  o = align_up(o + n);
     L.total = o;

@@ -49,3 +49,13 @@ def test_alu_ops_and_peak():
         UNCERT + 353850 + 5684 + 75)  # sweep 1's worklist exceeds the uncertified count
     assert ops == want == 10540445172
     assert bench.alu_peak(2070.0) == 152 * 64 * 2070e6
+
+
+def test_codes_kernel_share_of_the_counts():
+    # sweep 0's pass (k_codes): f, fhat read and g written for every vertex,
+    # the code of f written where uncertified; the loop kernel gets the rest
+    assert bench.codes_bytes(N, UNCERT) == 12 * N + UNCERT
+    rest = bench.algorithmic_bytes(N, LOG, EDITED, UNCERT) - bench.codes_bytes(N, UNCERT)
+    assert rest == 5 * int(LOG[1:, 0].sum()) + 12 * int(LOG[:, 2].sum()) + N // 8 + 8 * EDITED
+    assert bench.codes_alu_ops(N, UNCERT) == bench.ALU_OPS_CERT * N + 2 * bench.ALU_OPS_CODE * UNCERT
+    assert bench.codes_alu_ops(N, UNCERT) < bench.algorithmic_alu_ops(N, LOG, UNCERT)

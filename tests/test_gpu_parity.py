@@ -344,3 +344,31 @@ def test_below_reference_needs_its_workspace(api):
     ws = torch.empty(api.workspace_size(fl.shape), dtype=torch.uint8, device="cuda")
     res = api.correct(dev(fl.f), dev(fl.fhat), fl.xi, rule="below", ws=ws)
     assert res.status == api.ERR_WORKSPACE
+
+
+# ------------------------------------------------------ per-kernel events
+@pytest.mark.parametrize("shape", [(24, 20, 136), (21, 30, 45), (67, 91)], ids=["tma", "cp_async", "2d"])
+def test_phase_events_bracket_each_kernel(api, shape):
+    """The three timing events of msz_options: recorded around sweep 0's
+    kernel and the loop kernel, without changing the result; an entry left
+    null is skipped."""
+    fl = (synth.perlin3d_prequant(shape, seed=61, eb_rel=1e-4) if len(shape) == 3
+          else synth.perlin2d(shape, seed=61))
+    f, fh = dev(fl.f), dev(fl.fhat)
+    ref = api.correct(f, fh, fl.xi)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    res = api.correct(f, fh, fl.xi, events=ev)
+    torch.cuda.synchronize()
+    assert res.status == ref.status == api.OK
+    assert np.array_equal(bits(res.out), bits(ref.out))
+    assert np.array_equal(res.edit_idx.cpu().numpy(), ref.edit_idx.cpu().numpy())
+    t_codes, t_loop = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    assert t_loop > 0.0
+    if len(shape) == 3:
+        assert t_codes > 0.0
+    else:
+        assert 0.0 <= t_codes < t_loop  # one kernel: [0] and [1] both before it
+    part = [None, torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+    res2 = api.correct(f, fh, fl.xi, events=part)
+    torch.cuda.synchronize()
+    assert res2.status == api.OK and part[1].elapsed_time(part[2]) > 0.0
