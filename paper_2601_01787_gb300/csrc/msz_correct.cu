@@ -41,6 +41,8 @@ constexpr int kThreads = tile::THREADS;  // 256 per block of the persistent kern
 #endif
 constexpr int kMinBlocks = MSZ_MIN_BLOCKS;  // resident blocks per SM the register budget aims at
 constexpr uint32_t kDenseFactor = 6;        // worklist estimate: 6 x distorted vertices
+constexpr int kListRounds = 4;              // edit-list rounds whose loads a warp issues together
+static_assert(kListRounds == 4, "the edit list's round group is written out for four rounds");
 #ifndef MSZ_DETECT_TILE_Z
 #define MSZ_DETECT_TILE_Z 16
 #endif
@@ -109,6 +111,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
     const GridDev &G = F.G;
     Ctrl *C = P.ctrl;
     __shared__ uint32_t sm[40];
+    __shared__ uint32_t s_rq[kThreads / 32][kRoundCap];  // each warp's round queue (sparse walks)
     const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t stride = gridDim.x * blockDim.x;
     const bool leader = gtid == 0;
@@ -165,7 +168,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
             // count the distinct targets this sweep found, for the record
             uint32_t nt = 0;
             if (!sum_k) walk_bits<true>(F.tb, nullptr, G, nt, [&](bool, uint32_t) {});
-            else walk_flagged<true, false>(F.tb, P.stb, nullptr, G, nt, [&](bool, uint32_t) {});
+            else walk_flagged<true, false>(F.tb, P.stb, nullptr, G, nt, s_rq[threadIdx.x >> 5], [&](bool, uint32_t) {});
             warp_add(nt, &P.log[k].targets);
             if (leader) { C->status = MSZ_ERR_MAX_SWEEPS; C->sweeps = k; C->left = m; }
             ok = grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
@@ -185,7 +188,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
                 });
             } else {
                 uint32_t *dsum = P.sdm[(k + 1) & 1];
-                walk_flagged<true, false>(F.tb, P.stb, nullptr, G, targets, [&](bool has, uint32_t t) {
+                walk_flagged<true, false>(F.tb, P.stb, nullptr, G, targets, s_rq[threadIdx.x >> 5], [&](bool has, uint32_t t) {
                     if (has && apply_target<NDIM>(F, t, dense_next, dnext, dsum)) ++changed_here;
                 });
             }
@@ -235,15 +238,16 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
             }
         } else if (dcur_sum) {
             // the worklist, restricted to uncertified vertices, flagged chunk by flagged chunk
-            walk_flagged<true, true>(dcur, dcur_sum, F.ub, G, seen, [&](bool h1, uint32_t v1, bool h2, uint32_t v2) {
+            walk_flagged<true, true>(dcur, dcur_sum, F.ub, G, seen, s_rq[threadIdx.x >> 5], [&](bool h1, uint32_t v1, bool h2, uint32_t v2) {
                 detect_vertex2<NDIM>(F, E, h1, v1, h2, v2);
             });
             warp_add(seen, &P.log[k1].worklist);
         } else {
             // a worklist without flags (sweep 1's, built by sweep 0, and a dense sweep's)
-            walk_bits_pairs<true>(dcur, F.ub, G, seen, [&](bool h1, uint32_t v1, bool h2, uint32_t v2) {
-                detect_vertex2<NDIM>(F, E, h1, v1, h2, v2);
-            });
+            walk_bits_pairs<true>(
+                dcur, F.ub, G, seen,
+                [&](bool h1, uint32_t v1, bool h2, uint32_t v2) { detect_vertex2<NDIM>(F, E, h1, v1, h2, v2); },
+                AllWords(), s_rq[threadIdx.x >> 5]);
             warp_add(seen, &P.log[k1].worklist);
         }
         warp_add(E.distorted, &P.log[k1].distorted);
@@ -293,48 +297,59 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
     if (leader) C->edit_count = all;
     unsigned long long prefix = (unsigned long long)bpre + warp_pre;
     // Rounds of 32 words; a round's edits go to the lanes in index order
-    // (ChunkBits), so its stores coalesce.  Software-pipelined: the words of
-    // round r+2 are loaded and the first 32 edits of round r+1 gathered (g
-    // and fhat) before round r is stored.
+    // (ChunkBits), so its stores coalesce.  kListRounds rounds at a time: their
+    // words are loaded together, then the first 32 edits of each gathered (g
+    // and fhat) before any is stored, and the next group's words are loaded
+    // before this group's stores -- a warp's chain of dependent loads is one
+    // link per group instead of one per round.
+    constexpr int R = kListRounds;
     auto word_at = [&](uint32_t w) -> uint32_t { return w < w1 ? F.eb[w] : 0u; };
-    uint32_t wsoon = word_at(w0 + 32u + lane);
-    ChunkBits nxt(w0, word_at(w0 + lane));
-    bool hn;
-    uint32_t vn;
-    float gn = 0.f, fn = 0.f;
-    nxt.pick(lane, hn, vn);
-    if (hn) {
-        gn = F.g[vn];
-        fn = __ldg(&F.fhat[vn]);
-    }
-    for (uint32_t r = w0; r < w1; r += 32u) {
-        const ChunkBits cur = nxt;
-        const bool hc = hn;
-        const uint32_t vc = vn;
-        const float gc = gn, fc = fn;
-        const uint32_t wr = wsoon;
-        wsoon = word_at(r + 64u + lane);
-        nxt = ChunkBits(r + 32u, wr);
-        nxt.pick(lane, hn, vn);
-        if (hn) {
-            gn = F.g[vn];
-            fn = __ldg(&F.fhat[vn]);
+    uint32_t wd[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) wd[q] = word_at(w0 + 32u * q + lane);
+    for (uint32_t r = w0; r < w1; r += 32u * R) {
+        ChunkBits cb[R] = {ChunkBits(r, wd[0]), ChunkBits(r + 32u, wd[1]), ChunkBits(r + 64u, wd[2]),
+                           ChunkBits(r + 96u, wd[3])};
+        bool h[R];
+        uint32_t v[R];
+        float gv[R], fv[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            cb[q].pick(lane, h[q], v[q]);
+            gv[q] = h[q] ? F.g[v[q]] : 0.f;
+            fv[q] = h[q] ? __ldg(&F.fhat[v[q]]) : 0.f;
         }
-        if (hc && prefix + lane < P.edit_cap) {
-            P.edit_idx[prefix + lane] = vc;
-            P.edit_delta[prefix + lane] = __fsub_rn(gc, fc);
-        }
-        for (uint32_t j0 = 32u; j0 < cur.total; j0 += 32u) {
-            bool h;
-            uint32_t v;
-            cur.pick(j0 + lane, h, v);
-            const unsigned long long pos = prefix + j0 + lane;
-            if (h && pos < P.edit_cap) {
-                P.edit_idx[pos] = v;
-                P.edit_delta[pos] = __fsub_rn(F.g[v], __ldg(&F.fhat[v]));
+#pragma unroll
+        for (int q = 0; q < R; ++q) wd[q] = word_at(r + 32u * (R + q) + lane);
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            if (h[q] && prefix + lane < P.edit_cap) {
+                P.edit_idx[prefix + lane] = v[q];
+                P.edit_delta[prefix + lane] = __fsub_rn(gv[q], fv[q]);
             }
+            // a chunk with more than 32 edits (clustered edits): the rest
+            // four rounds at a time, gathers first
+            for (uint32_t j0 = 32u; j0 < cb[q].total; j0 += 32u * R) {
+                bool hj[R];
+                uint32_t vj[R];
+                float gj[R], fj[R];
+#pragma unroll
+                for (int u = 0; u < R; ++u) {
+                    cb[q].pick(j0 + 32u * u + lane, hj[u], vj[u]);
+                    gj[u] = hj[u] ? F.g[vj[u]] : 0.f;
+                    fj[u] = hj[u] ? __ldg(&F.fhat[vj[u]]) : 0.f;
+                }
+#pragma unroll
+                for (int u = 0; u < R; ++u) {
+                    const unsigned long long pos = prefix + j0 + 32u * u + lane;
+                    if (hj[u] && pos < P.edit_cap) {
+                        P.edit_idx[pos] = vj[u];
+                        P.edit_delta[pos] = __fsub_rn(gj[u], fj[u]);
+                    }
+                }
+            }
+            prefix += cb[q].total;
         }
-        prefix += cur.total;
     }
     if (!grid_barrier(&C->bar_count, &C->bar_gen, &C->error)) return;
     if (leader) C->t_end = global_ns();

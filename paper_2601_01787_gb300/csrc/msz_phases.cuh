@@ -171,6 +171,59 @@ __device__ __forceinline__ void chunk_pairs(uint32_t base, uint32_t bits, F &&fn
     }
 }
 
+// Vertices of several chunks gathered into full rounds (warp-collective):
+// the warp's buffer q (kRoundCap entries of shared memory) takes a chunk's
+// set bits in index order, and whenever it holds a full round -- 64 vertices
+// with PAIRS (two a lane), else 32 -- the round runs.  In a sparse sweep a
+// chunk holds a few set bits, so a round per chunk would leave most lanes
+// idle and put one dependent gather after another; a round over several
+// chunks keeps the warp full.  The order of the calls does not matter to
+// their callers (their effects are reductions and distinct targets).
+constexpr uint32_t kRoundCap = 96;  // a full round plus one chunk round (< 32) carried over
+
+template <bool PAIRS>
+struct RoundQueue {
+    static constexpr uint32_t R = PAIRS ? 64u : 32u;
+    uint32_t *q;
+    uint32_t n = 0;  // warp-uniform fill
+    // runs the first cnt (<= R) queued vertices and moves the rest up
+    template <class F>
+    __device__ __forceinline__ void run(uint32_t cnt, F &fn) {
+        const uint32_t lane = lane_id();
+        __syncwarp();
+        if constexpr (PAIRS) {
+            const bool h1 = lane < cnt, h2 = lane + 32u < cnt;
+            fn(h1, h1 ? q[lane] : 0u, h2, h2 ? q[lane + 32u] : 0u);
+        } else {
+            const bool h = lane < cnt;
+            fn(h, h ? q[lane] : 0u);
+        }
+        const uint32_t rest = n - cnt;  // < 32
+        const uint32_t mv = lane < rest ? q[cnt + lane] : 0u;
+        __syncwarp();
+        if (lane < rest) q[lane] = mv;
+        __syncwarp();
+        n = rest;
+    }
+    template <class F>
+    __device__ __forceinline__ void push_chunk(uint32_t base, uint32_t bits, F &fn) {
+        if (!__any_sync(kFull, bits != 0u)) return;
+        const ChunkBits cb(base, bits);
+        for (uint32_t j0 = 0; j0 < cb.total; j0 += 32u) {
+            bool h;
+            uint32_t v;
+            cb.pick(j0 + lane_id(), h, v);  // lanes 0 .. take-1
+            if (h) q[n + lane_id()] = v;
+            n += min(32u, cb.total - j0);
+            if (n >= R) run(R, fn);
+        }
+    }
+    template <class F>
+    __device__ __forceinline__ void flush(F &fn) {
+        while (n) run(min(n, R), fn);
+    }
+};
+
 // Warp-collective walk over the set bits of a bitmap: each warp takes 32
 // consecutive words (1024 vertices) at a time, grid-stride.  CLEAR zeroes the
 // visited words; `seen` counts their set bits; a non-null filter restricts the
@@ -215,18 +268,21 @@ __device__ __forceinline__ void walk_bits(uint32_t *bm, const uint32_t *filter, 
 // walk_bits for detection: two vertices per lane per round (chunk_pairs), so
 // that each lane has the neighbour loads of both in flight at once.
 // fn(has1, v1, has2, v2).  word_ok(w) false drops word w (after counting it
-// in `seen`).  The filter's words are loaded one chunk ahead.
+// in `seen`).  The filter's words are loaded one chunk ahead.  With rq (the
+// warp's kRoundCap entries of shared memory) the set bits go through a
+// RoundQueue, so rounds stay full where chunks hold few bits.
 struct AllWords {
     __device__ __forceinline__ bool operator()(uint32_t) const { return true; }
 };
 
 template <bool CLEAR, class F, class W = AllWords>
 __device__ __forceinline__ void walk_bits_pairs(uint32_t *bm, const uint32_t *filter, const GridDev &G,
-                                                uint32_t &seen, F &&fn, W word_ok = W()) {
+                                                uint32_t &seen, F &&fn, W word_ok = W(), uint32_t *rq = nullptr) {
     const uint32_t lane = lane_id();
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     const uint32_t chunks = (G.words + 31u) / 32u;
+    RoundQueue<true> Q{rq};
     uint32_t pre[kAhead];
 #pragma unroll
     for (int u = 0; u < kAhead; ++u) {
@@ -259,8 +315,10 @@ __device__ __forceinline__ void walk_bits_pairs(uint32_t *bm, const uint32_t *fi
             if (filter) bits &= fcur;
             if (bits && !word_ok(wi)) bits = 0u;
         }
-        chunk_pairs(base, bits, fn);
+        if (rq) Q.push_chunk(base, bits, fn);
+        else chunk_pairs(base, bits, fn);
     }
+    if (rq) Q.flush(fn);
 }
 
 // walk_bits / walk_bits_pairs over the chunks (32 words) whose flags are
@@ -268,15 +326,18 @@ __device__ __forceinline__ void walk_bits_pairs(uint32_t *bm, const uint32_t *fi
 // so that a cluster of flagged chunks spreads over many warps.  A warp reads
 // the flags of 32 of its chunks at once (one per lane), then walks the
 // flagged ones, loading the words of the next flagged chunk before the
-// current one is handed out.  CLEAR zeroes the visited words and flags.
-// PAIRS: two vertices per lane per round (chunk_pairs), else one (chunk_each).
+// current one is queued; the set bits go through a RoundQueue (rq: the
+// warp's kRoundCap entries of shared memory), so rounds are full.  CLEAR
+// zeroes the visited words and flags.  PAIRS: fn(h1, v1, h2, v2), two
+// vertices a lane; else fn(h, v).
 template <bool CLEAR, bool PAIRS, class F>
 __device__ __forceinline__ void walk_flagged(uint32_t *bm, uint32_t *flags, const uint32_t *filter, const GridDev &G,
-                                             uint32_t &seen, F &&fn) {
+                                             uint32_t &seen, uint32_t *rq, F &&fn) {
     const uint32_t lane = lane_id();
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     const uint32_t chunks = (G.words + 31u) / 32u;
+    RoundQueue<PAIRS> Q{rq};
     for (uint32_t c0 = gw; c0 < chunks; c0 += 32u * nw) {
         const uint32_t mine = c0 + lane * nw;  // this lane's chunk of the round
         const bool set = mine < chunks && flags[mine] != 0u;
@@ -301,11 +362,11 @@ __device__ __forceinline__ void walk_flagged(uint32_t *bm, uint32_t *flags, cons
                 seen += (uint32_t)__popc(bits);
                 if (filter) bits &= filter[wi];
             }
-            if constexpr (PAIRS) chunk_pairs(base, bits, fn);
-            else chunk_each(base, bits, fn);
+            Q.push_chunk(base, bits, fn);
             if (!more) break;
         }
     }
+    Q.flush(fn);
 }
 
 // Like walk_bits_pairs, with the bits of word w given by finish(w, raw),
