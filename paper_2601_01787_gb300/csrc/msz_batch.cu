@@ -159,6 +159,47 @@ __device__ __forceinline__ void detect_pair(const BatchProblem &P, const uint32_
     if (E2.distorted && lane == (uint32_t)(__ffs(p2) - 1)) atomicAdd(&s_cnt[f2][1], (uint32_t)__popc(p2));
 }
 
+// ---- sweep 0: codes of every field and the detection of sweep 0 over
+// their uncertified vertices, one shared tile queue, as an ordinary launch
+// of its own (its paired-row ring is the largest shared-memory user of the
+// batch; the kernel boundary orders its writes before k_batch)
+__global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch_codes(__grid_constant__ const BatchProblem P) {
+    extern __shared__ __align__(16) float smem[];
+    __shared__ uint32_t s_tile[MSZ_BATCH_MAX_FIELDS + 1];
+    __shared__ uint32_t s_cnt[MSZ_BATCH_MAX_FIELDS][4];
+    __shared__ uint32_t s_next;
+    const uint32_t nf = P.nfields;
+    Ctrl *C = P.ctrl;
+    for (uint32_t k = threadIdx.x; k <= nf; k += blockDim.x) s_tile[k] = k < nf ? P.fields[k].tile_base : P.ntiles;
+    for (uint32_t i = threadIdx.x; i < nf * 4; i += blockDim.x) s_cnt[i >> 2][i & 3] = 0;
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) C->t_start = global_ns();
+    bool bad = false;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_next = atomicAdd(&C->flag, 1u);
+        __syncthreads();
+        const uint32_t t = s_next;
+        if (t >= P.ntiles) break;
+        const uint32_t k = find_field(s_tile, nf, t);
+        const FieldView &F = P.fields[k].F;
+        const tile::TileGeom tg = tile::tile_geom(F.G.nx, F.G.ny, F.G.nz, F.tile_z);
+        const uint32_t lt = t - s_tile[k];
+        const uint32_t txi = lt % tg.tx, tyi = (lt / tg.tx) % tg.ty, tzi = lt / (tg.tx * tg.ty);
+        const int zb = (int)(tzi * tg.bz);
+        bool fb = false;
+        uint32_t dist = 0;
+        first_tile<true, true>(F, (int)(txi * tile::BX), (int)(tyi * tile::BY), zb,
+                               min(zb + (int)tg.bz, (int)F.G.nz), smem, fb, dist);
+        warp_add(dist, &s_cnt[k][1]);
+        if (fb) atomicOr(&P.res[k].error, kErrInput);
+        bad = bad || fb;
+    }
+    if (bad) atomicOr(&C->error, kErrInput);
+    flush_counts(s_cnt, nf, P.log);
+}
+
+// ---- the later sweeps and the edit lists (cooperative, persistent)
 __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant__ const BatchProblem P) {
     extern __shared__ __align__(16) float smem[];
     __shared__ uint32_t s_base[MSZ_BATCH_MAX_FIELDS + 1];
@@ -168,6 +209,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
     __shared__ uint32_t s_next;
     __shared__ unsigned long long s_sum;
     __shared__ uint32_t sm[40];
+    __shared__ uint32_t s_rq[kThreads / 32][kRoundCap];  // each warp's round queue
+    uint32_t *rq = s_rq[threadIdx.x >> 5];
     const uint32_t nf = P.nfields;
     Ctrl *C = P.ctrl;
     const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
@@ -178,37 +221,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
     for (uint32_t i = threadIdx.x; i < nf * 4; i += blockDim.x) s_cnt[i >> 2][i & 3] = 0;
     for (uint32_t i = threadIdx.x; i < (nf + 31) / 32; i += blockDim.x) s_alive[i] = 0xffffffffu;
     __syncthreads();
-    if (leader) C->t_start = global_ns();
     auto alive = [&](uint32_t k) { return (s_alive[k >> 5] >> (k & 31u)) & 1u; };
-
-    // ---- codes of every field and the detection of sweep 0 over their
-    // uncertified vertices, one shared tile queue
-    {
-        bool bad = false;
-        for (;;) {
-            __syncthreads();
-            if (threadIdx.x == 0) s_next = atomicAdd(&C->flag, 1u);
-            __syncthreads();
-            const uint32_t t = s_next;
-            if (t >= P.ntiles) break;
-            const uint32_t k = find_field(s_tile, nf, t);
-            const FieldView &F = P.fields[k].F;
-            const tile::TileGeom tg = tile::tile_geom(F.G.nx, F.G.ny, F.G.nz, F.tile_z);
-            const uint32_t lt = t - s_tile[k];
-            const uint32_t txi = lt % tg.tx, tyi = (lt / tg.tx) % tg.ty, tzi = lt / (tg.tx * tg.ty);
-            const int zb = (int)(tzi * tg.bz);
-            bool fb = false;
-            uint32_t dist = 0;
-            first_tile<true>(F, (int)(txi * tile::BX), (int)(tyi * tile::BY), zb,
-                             min(zb + (int)tg.bz, (int)F.G.nz), smem, fb, dist);
-            warp_add(dist, &s_cnt[k][1]);
-            if (fb) atomicOr(&P.res[k].error, kErrInput);
-            bad = bad || fb;
-        }
-        if (bad) atomicOr(&C->error, kErrInput);
-        flush_counts(s_cnt, nf, P.log);
-    }
-    bool ok = grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
+    bool ok = ld_relaxed(&C->error) == 0;  // every block reads k_batch_codes' verdict
     if (leader) C->t_codes = global_ns();
     uint32_t k = 0;
     while (ok) {
@@ -264,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
                     atomicAdd(&s_cnt[f][2], (uint32_t)__popc(peers));
                     if (nch) atomicAdd(&s_cnt[f][3], nch);
                 }
-            });
+            }, rq);
             (void)targets;
             flush_counts(s_cnt, nf, rec);
         }
@@ -332,7 +346,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
                 },
                 [&](bool h1, uint32_t v1, bool h2, uint32_t v2) {
                     detect_pair(P, s_base, nf, s_cnt, (k1 + 1) & 1, alive, h1, v1, h2, v2);
-                });
+                },
+                rq);
         }
         flush_counts(s_cnt, nf, rec1);
         ok = grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
@@ -411,19 +426,18 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
 
 std::mutex g_batch_mu;
 
-msz_status batch_blocks(const DeviceInfo &d, int &blocks) {
-    static int cache[64];
+// Resident blocks of kernel fn with sm bytes of dynamic shared memory, times
+// the SM count.  The attribute belongs to the current context, so it is set
+// on every call (a context re-created after cudaDeviceReset starts without
+// it); the occupancy it allows is a property of the device and is cached.
+template <class K>
+msz_status resident_blocks(K fn, size_t sm, const DeviceInfo &d, int *cache, int &blocks) {
     std::lock_guard<std::mutex> lk(g_batch_mu);
-    const size_t sm = tile::kRingBytes;
-    // the attribute belongs to the current context, so it is set on every
-    // call (a context re-created after cudaDeviceReset starts without it);
-    // the occupancy it allows is a property of the device and is cached
-    if (cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
         return MSZ_ERR_CUDA;
     if (!cache[d.device]) {
         int per = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch, kThreads, sm) != cudaSuccess)
-            return MSZ_ERR_CUDA;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kThreads, sm) != cudaSuccess) return MSZ_ERR_CUDA;
         if (per < 1) return MSZ_ERR_UNSUPPORTED;
         int b = per * d.sms;
         if (b > (int)kMaxBlocks) b = (int)kMaxBlocks;
@@ -431,6 +445,17 @@ msz_status batch_blocks(const DeviceInfo &d, int &blocks) {
     }
     blocks = cache[d.device];
     return MSZ_OK;
+}
+
+// the loop kernel (its dense detection stages g on the cp.async ring) and
+// the code pass (f and fhat on the paired-row ring)
+msz_status batch_blocks(const DeviceInfo &d, int &blocks) {
+    static int cache[64];
+    return resident_blocks(k_batch, tile::kRingBytes, d, cache, blocks);
+}
+msz_status batch_codes_blocks(const DeviceInfo &d, int &blocks) {
+    static int cache[64];
+    return resident_blocks(k_batch_codes, tile::kPairRingBytes, d, cache, blocks);
 }
 
 // Shared index space of the fields: per-field base (1024-aligned) and total.
@@ -478,6 +503,7 @@ struct BatchPlanImpl {
     int32_t n;
     uint32_t max_sweeps;
     int blocks;
+    int codes_blocks;
     int device;
     char *ws;
     BatchLayout L;
@@ -582,8 +608,9 @@ extern "C" msz_status msz_batch_plan_create(int32_t n, const msz_field *fields, 
     for (int32_t k = 0; k < n; ++k)
         for (uint64_t b = bases[k] / 1024; b < (bases[k] + (uint64_t)grids[k].n + 1023) / 1024; ++b)
             bfield[b] = (uint8_t)k;
-    int blocks = 0;
+    int blocks = 0, cblocks = 0;
     if ((st = batch_blocks(dev, blocks)) != MSZ_OK) return st;
+    if ((st = batch_codes_blocks(dev, cblocks)) != MSZ_OK) return st;
     // the descriptor table is uploaded once; launches only clear the control
     // block and bitmaps, so a captured launch can be replayed
     if (cudaMemcpyAsync(ws + L.fields, tab.data(), n * sizeof(FieldDev), cudaMemcpyHostToDevice, s) != cudaSuccess)
@@ -597,6 +624,7 @@ extern "C" msz_status msz_batch_plan_create(int32_t n, const msz_field *fields, 
     p->impl.n = n;
     p->impl.max_sweeps = max_sweeps;
     p->impl.blocks = blocks;
+    p->impl.codes_blocks = cblocks;
     p->impl.device = dev.device;
     p->impl.ws = ws;
     p->impl.L = L;
@@ -613,6 +641,8 @@ extern "C" msz_status msz_batch_launch(const msz_batch_plan *plan, msz_stream_t 
     if (cudaGetDevice(&cur) != cudaSuccess || cur != B.device) return MSZ_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     if (cudaMemsetAsync(B.ws, 0, B.L.zero_bytes, s) != cudaSuccess) return MSZ_ERR_CUDA;
+    k_batch_codes<<<B.codes_blocks, kThreads, tile::kPairRingBytes, s>>>(B.P);
+    if (cudaGetLastError() != cudaSuccess) return MSZ_ERR_CUDA;
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(B.blocks);
     cfg.blockDim = dim3(kThreads);

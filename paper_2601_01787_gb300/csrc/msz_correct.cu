@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_codes(__grid_constant_
     if (TMA)
         first_tiled_tma<true>(F, &P.map_f, &P.map_s, &P.log[0].tile_next, smem, &C->error, distorted,
                               P.test_fault == 2);
-    else first_tiled<true>(F, &P.log[0].tile_next, smem, &C->error, distorted);
+    else first_tiled<true, true>(F, &P.log[0].tile_next, smem, &C->error, distorted);
     warp_add(distorted, &P.log[0].distorted);
 }
 
@@ -183,9 +183,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_correct(__grid_constan
             uint32_t *dnext = F.dm[(k + 1) & 1];
             uint32_t targets = 0, changed_here = 0;
             if (!sum_k) {
-                walk_bits<true>(F.tb, nullptr, G, targets, [&](bool has, uint32_t t) {
-                    if (has && apply_target<NDIM>(F, t, dense_next, dnext)) ++changed_here;
-                });
+                walk_bits<true>(
+                    F.tb, nullptr, G, targets,
+                    [&](bool has, uint32_t t) {
+                        if (has && apply_target<NDIM>(F, t, dense_next, dnext)) ++changed_here;
+                    },
+                    s_rq[threadIdx.x >> 5]);
             } else {
                 uint32_t *dsum = P.sdm[(k + 1) & 1];
                 walk_flagged<true, false>(F.tb, P.stb, nullptr, G, targets, s_rq[threadIdx.x >> 5], [&](bool has, uint32_t t) {
@@ -400,7 +403,7 @@ static size_t correct_smem() {
 }
 template <bool TMA>
 static size_t codes_smem() {
-    return TMA ? tile::tma_ring_bytes(tile::kCodeSlots, 2) : tile::kRingBytes;
+    return TMA ? tile::tma_ring_bytes(tile::kCodeSlots, 2) : tile::kPairRingBytes;
 }
 
 // Resident blocks of kernel fn with sm bytes of dynamic shared memory, times

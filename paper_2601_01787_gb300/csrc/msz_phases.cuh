@@ -230,14 +230,16 @@ struct RoundQueue {
 // calls to the vertices also set there.  fn(valid, v) runs once per round
 // with one vertex per lane, the chunk's bits handed out in index order
 // (chunk_each), so that a round's loads are in flight together however the
-// bits fall on the words.
+// bits fall on the words; with rq (the warp's kRoundCap entries of shared
+// memory) the bits go through a RoundQueue instead, rounds spanning chunks.
 template <bool CLEAR, class F>
 __device__ __forceinline__ void walk_bits(uint32_t *bm, const uint32_t *filter, const GridDev &G, uint32_t &seen,
-                                          F &&fn) {
+                                          F &&fn, uint32_t *rq = nullptr) {
     const uint32_t lane = lane_id();
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     const uint32_t chunks = (G.words + 31u) / 32u;
+    RoundQueue<false> Q{rq};
     // the words of the next kAhead chunks are loaded ahead (a sparse walk is
     // otherwise one dependent load after another)
     uint32_t pre[kAhead];
@@ -261,8 +263,10 @@ __device__ __forceinline__ void walk_bits(uint32_t *bm, const uint32_t *filter, 
             seen += (uint32_t)__popc(bits);
             if (filter) bits &= filter[wi];
         }
-        chunk_each(base, bits, fn);
+        if (rq) Q.push_chunk(base, bits, fn);
+        else chunk_each(base, bits, fn);
     }
+    if (rq) Q.flush(fn);
 }
 
 // walk_bits for detection: two vertices per lane per round (chunk_pairs), so
@@ -371,13 +375,16 @@ __device__ __forceinline__ void walk_flagged(uint32_t *bm, uint32_t *flags, cons
 
 // Like walk_bits_pairs, with the bits of word w given by finish(w, raw),
 // where raw = fetch(w) is loaded kAhead chunks ahead (fetch only loads;
-// finish may read, clear and count whatever else it needs).
+// finish may read, clear and count whatever else it needs).  rq: as in
+// walk_bits_pairs.
 template <class FE, class FI, class F>
-__device__ __forceinline__ void walk_words_pairs(const GridDev &G, FE &&fetch, FI &&finish, F &&fn) {
+__device__ __forceinline__ void walk_words_pairs(const GridDev &G, FE &&fetch, FI &&finish, F &&fn,
+                                                 uint32_t *rq = nullptr) {
     const uint32_t lane = lane_id();
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     const uint32_t chunks = (G.words + 31u) / 32u;
+    RoundQueue<true> Q{rq};
     uint32_t pre[kAhead];
 #pragma unroll
     for (int u = 0; u < kAhead; ++u) {
@@ -395,8 +402,10 @@ __device__ __forceinline__ void walk_words_pairs(const GridDev &G, FE &&fetch, F
             pre[kAhead - 1] = wn < G.words ? fetch(wn) : 0u;
         }
         const uint32_t bits = wi < G.words ? finish(wi, raw) : 0u;
-        chunk_pairs(base, bits, fn);
+        if (rq) Q.push_chunk(base, bits, fn);
+        else chunk_pairs(base, bits, fn);
     }
+    if (rq) Q.flush(fn);
 }
 
 // Detection of two vertices per lane in the current g (warp-collective): all
@@ -668,9 +677,13 @@ __device__ __forceinline__ void own_row_cp(const FieldView &P, const float *p0, 
 // codes in the start field come from the staged planes; they mark targets and
 // the worklist P.dm[1], and add to `distorted`.
 // Block-collective; the caller synchronizes the block before the next tile.
-template <bool DETECT>
+// PAIR: rows of two planes a step (tile_rows2) on a ring of kPairSlots
+// planes (z-1 .. z+2 in use, z+3 and z+4 in flight; one block barrier per
+// two planes), else one plane a step (tile_row) on NSLOT planes.
+template <bool DETECT, bool PAIR = false>
 __device__ __forceinline__ void first_tile(const FieldView &P, int x0, int y0, int zb, int ze, float *smem,
                                            bool &bad, uint32_t &distorted) {
+    constexpr int NS = PAIR ? tile::kPairSlots : tile::NSLOT;
     using namespace tile;
     const GridDev &G = P.G;
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
@@ -702,7 +715,7 @@ __device__ __forceinline__ void first_tile(const FieldView &P, int x0, int y0, i
         const int e = (int)tid + j * THREADS;
         if (e >= ELEMS || (inm >> j & 1u)) continue;
         const int r = e / LOADW, c = e - r * LOADW;
-        for (int sl = 0; sl < NSLOT; ++sl) {
+        for (int sl = 0; sl < NS; ++sl) {
             smem[sl * SLOT + r * PW + c + 3] = qnan;
             if (DETECT) smem[sl * SLOT + PLANE + r * PW + c + 3] = qnan;
         }
@@ -722,7 +735,7 @@ __device__ __forceinline__ void first_tile(const FieldView &P, int x0, int y0, i
     // become NaN
     auto issue = [&](int p) {
         if (p >= 0 && p <= ze) {
-            const int slot = (p - zb + 1) % NSLOT;
+            const int slot = (p - zb + 1) % NS;
             const bool inside = p < (int)G.nz;
             const uint32_t pb = (uint32_t)p * G.nxy;
             const float *sec = DETECT && P.ginit ? P.ginit : P.fhat;
@@ -740,7 +753,7 @@ __device__ __forceinline__ void first_tile(const FieldView &P, int x0, int y0, i
                 if (secm >> j & 1u) cp_async4(sbase + 4u * (so + (uint32_t)PLANE), sec + gi);
             }
         } else if (p < 0) {
-            const int slot = (p - zb + 1) % NSLOT;
+            const int slot = (p - zb + 1) % NS;
 #pragma unroll
             for (int j = 0; j < PER_THREAD; ++j) {
                 if (!(inm >> j & 1u)) continue;
@@ -757,15 +770,31 @@ __device__ __forceinline__ void first_tile(const FieldView &P, int x0, int y0, i
     issue(zb + 1);
     issue(zb + 2);
     const int y = y0 + (int)warp, r = (int)warp + 1;
-    for (int z = zb; z < ze; ++z) {
-        cp_async_wait<1>();  // planes up to z+1 of this thread have landed (z+2 may be in flight)
-        __syncthreads();     // ... of every thread; the slot of z-2 is free
-        issue(z + 3);
-        if (y >= (int)G.ny) continue;
-        auto plane = [&](int p) { return smem + ((p - zb + 1) % NSLOT) * SLOT; };
-        const uint32_t rowbase = (uint32_t)z * G.nxy + (uint32_t)y * G.nx;
-        own_row_cp<DETECT>(P, plane(z), r, x0, rowbase, bad);
-        tile_row<DETECT>(P, plane(z - 1), plane(z), plane(z + 1), PLANE, r, x0, rowbase, distorted);
+    auto plane = [&](int p) { return smem + ((p - zb + 1) % NS) * SLOT; };
+    if constexpr (PAIR) {
+        for (int z = zb; z < ze; z += 2) {
+            cp_async_wait<0>();  // planes up to z+2 of this thread have landed
+            __syncthreads();     // ... of every thread; the slots of z-3 and z-2 are free
+            issue(z + 3);
+            issue(z + 4);
+            if (y >= (int)G.ny) continue;
+            const bool two = z + 1 < ze;
+            const uint32_t rowbase = (uint32_t)z * G.nxy + (uint32_t)y * G.nx;
+            own_row_cp<DETECT>(P, plane(z), r, x0, rowbase, bad);
+            if (two) own_row_cp<DETECT>(P, plane(z + 1), r, x0, rowbase + G.nxy, bad);
+            tile_rows2<DETECT>(P, plane(z - 1), plane(z), plane(z + 1), plane(z + 2), PLANE, r, x0, rowbase, two,
+                               distorted);
+        }
+    } else {
+        for (int z = zb; z < ze; ++z) {
+            cp_async_wait<1>();  // planes up to z+1 of this thread have landed (z+2 may be in flight)
+            __syncthreads();     // ... of every thread; the slot of z-2 is free
+            issue(z + 3);
+            if (y >= (int)G.ny) continue;
+            const uint32_t rowbase = (uint32_t)z * G.nxy + (uint32_t)y * G.nx;
+            own_row_cp<DETECT>(P, plane(z), r, x0, rowbase, bad);
+            tile_row<DETECT>(P, plane(z - 1), plane(z), plane(z + 1), PLANE, r, x0, rowbase, distorted);
+        }
     }
     cp_async_wait<0>();
 }
@@ -917,8 +946,9 @@ __device__ __forceinline__ void detect_tiled_cp(const FieldView &P, uint32_t til
 
 // Tiles of one field handed out by an atomic counter (block-collective).
 // DETECT: the pass also runs sweep 0's detection (distorted vertices counted
-// in `distorted`).
-template <bool DETECT>
+// in `distorted`).  PAIR: the paired-row form of first_tile (its ring is
+// kPairRingBytes of dynamic shared memory, else kRingBytes).
+template <bool DETECT, bool PAIR = false>
 __device__ __forceinline__ void first_tiled(const FieldView &P, uint32_t *tile_next, float *smem, uint32_t *err,
                                             uint32_t &distorted) {
     using namespace tile;
@@ -934,8 +964,8 @@ __device__ __forceinline__ void first_tiled(const FieldView &P, uint32_t *tile_n
         if (t >= tg.count) break;
         const uint32_t txi = t % tg.tx, tyi = (t / tg.tx) % tg.ty, tzi = t / (tg.tx * tg.ty);
         const int zb = (int)(tzi * tg.bz);
-        first_tile<DETECT>(P, (int)(txi * BX), (int)(tyi * BY), zb, min(zb + (int)tg.bz, (int)G.nz), smem, bad,
-                           distorted);
+        first_tile<DETECT, PAIR>(P, (int)(txi * BX), (int)(tyi * BY), zb, min(zb + (int)tg.bz, (int)G.nz), smem,
+                                 bad, distorted);
     }
     if (bad) atomicOr(err, kErrInput);
 }

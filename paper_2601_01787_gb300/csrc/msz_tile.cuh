@@ -47,6 +47,10 @@ __device__ __forceinline__ void cp_async_wait() {
 // pass).
 constexpr int SLOT = 2 * PLANE;
 constexpr size_t kRingBytes = (size_t)NSLOT * SLOT * sizeof(float);
+// The ring of the paired-row form (two planes a step): z-1 .. z+2 in use,
+// z+3 and z+4 in flight.
+constexpr int kPairSlots = 6;
+constexpr size_t kPairRingBytes = (size_t)kPairSlots * SLOT * sizeof(float);
 
 // The ring when TMA stages the planes: each slot holds two boxes of ROWS x PW
 // floats (x0-4 .. x0+131, y0-1 .. y0+8: the same indexing as above), f first,
