@@ -468,6 +468,11 @@ def run_ours(args, ws, rank, local):
         api._ws_cache.clear()
         torch.cuda.empty_cache()
         line["large"] = run_large(dev, stream)
+    if rank == 0 and args.configs:
+        f = fh = out = None
+        api._ws_cache.clear()
+        torch.cuda.empty_cache()
+        line["configs"] = run_configs(dev, stream)
     if rank == 0 and not args.no_relaxed:
         f = fh = out = None
         api._ws_cache.clear()
@@ -480,6 +485,8 @@ def run_ours(args, ws, rank, local):
         torch.cuda.empty_cache()
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(fl, args.cpu_slab)
+        if args.configs:
+            line["cpu_baseline"]["configs"] = cpu_baseline_configs()
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -552,6 +559,48 @@ def run_large(dev, stream, reps: int = 3) -> dict:
     return {"workload": "perlin3d_prequant_1024x1024x1024, seed 2, eb_rel 1e-4", "n_vertices": n, "unit": UNIT,
             "value": round(n / (best * 1e-3) / 1e9, 4), "ms": round(best, 4), "sweeps": r.stats["sweeps"],
             "edited": r.edit_count, "kernel_ms": round(r.stats["kernel_ns"] / 1e6, 4)}
+
+
+def run_configs(dev, stream, reps: int = 5) -> dict:
+    """The two configurations the default run does not time: the 2D 256^2
+    Perlin field with noise (eb_rel 1e-3) and the 1024 x 1024 x 512 Gaussian
+    peak field (20,000 peaks, eb_rel 1e-4), each corrected by msz_correct with
+    inputs resident on the device (best of `reps` after one warm-up)."""
+    import torch
+
+    from paper_2601_01787_gb300 import api, synth
+    out = {}
+    for name, make in (("perlin2d_256x256 (seed 1, eb_rel 1e-3, fhat = f + U[-xi, xi])",
+                        lambda: synth.perlin2d((256, 256), seed=1, eb_rel=1e-3)),
+                       ("peaks3d_1024x1024x512 (20,000 peaks, seed 3, eb_rel 1e-4, fhat = f + U[-xi, xi])",
+                        lambda: synth.peaks3d((512, 1024, 1024), seed=3, eb_rel=1e-4))):
+        fl = make()
+        f = torch.from_numpy(fl.f).to(dev)
+        fh = torch.from_numpy(fl.fhat).to(dev)
+        o = torch.empty_like(f)
+        cap = f.numel() // 2
+        eidx = torch.empty(cap, dtype=torch.int32, device=dev)
+        edel = torch.empty(cap, dtype=torch.float32, device=dev)
+        ws = api.workspace(api.workspace_size(f.shape), dev)
+        best, r = None, None
+        for _ in range(reps + 1):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r = api.correct(f, fh, fl.xi, out=o, edit_idx=eidx, edit_delta=edel, edit_capacity=cap, ws=ws,
+                            stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            assert r.status == api.OK, api.status_str(r.status)
+            t = a.elapsed_time(b)
+            best = t if best is None else min(best, t)
+        n = f.numel()
+        out[name] = {"n_vertices": n, "unit": UNIT, "value": round(n / (best * 1e-3) / 1e9, 4),
+                     "ms": round(best, 4), "sweeps": r.stats["sweeps"], "edited": r.edit_count,
+                     "kernel_ms": round(r.stats["kernel_ns"] / 1e6, 4)}
+        del f, fh, o, eidx, edel, ws, fl
+        api._ws_cache.clear()
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_batch(dev, stream, reps: int = 5, sm_mhz: float | None = None) -> dict:
@@ -898,6 +947,30 @@ def cpu_baseline(fl, slab: int) -> dict:
             "seconds": round(dt, 3), "sweeps": r.sweeps}
 
 
+def cpu_baseline_configs() -> dict:
+    """The CPU oracle (single thread) on the two configurations of
+    run_configs: the whole 2D field, and the first 8 z-planes of the peak
+    field (a bounded sample: the whole field takes about 14 minutes)."""
+    import oracle
+
+    from paper_2601_01787_gb300 import synth
+    out = {}
+    fl = synth.perlin2d((256, 256), seed=1, eb_rel=1e-3)
+    for name, f, fh in (("perlin2d_256x256, the whole field", fl.f, fl.fhat),):
+        t0 = time.perf_counter()
+        r = oracle.correct(np.ascontiguousarray(f), np.ascontiguousarray(fh), fl.xi)
+        dt = time.perf_counter() - t0
+        out[name] = {"value": round(f.size / dt / 1e9, 6), "unit": UNIT, "seconds": round(dt, 3), "sweeps": r.sweeps}
+    fl = synth.peaks3d((512, 1024, 1024), seed=3, eb_rel=1e-4)
+    f, fh = np.ascontiguousarray(fl.f[:8]), np.ascontiguousarray(fl.fhat[:8])
+    t0 = time.perf_counter()
+    r = oracle.correct(f, fh, fl.xi)
+    dt = time.perf_counter() - t0
+    out["peaks3d_1024x1024x512, first 8 z-planes"] = {"value": round(f.size / dt / 1e9, 6), "unit": UNIT,
+                                                      "seconds": round(dt, 3), "sweeps": r.sweeps}
+    return out
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -939,6 +1012,8 @@ def main(argv=None):
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal comparison")
     ap.add_argument("--large", action="store_true", help="also correct one 1024^3 field (about a minute more)")
     ap.add_argument("--no-relaxed", action="store_true", help="skip the relaxed-synchronization comparison")
+    ap.add_argument("--configs", action="store_true",
+                    help="also time the 2D 256^2 field and the 1024x1024x512 peak field (about a minute more)")
     ap.add_argument("--cpu-slab", type=int, default=128, help="z-planes of the CPU-baseline sample")
     ap.add_argument("--ref-slab", type=int, default=24, help="z-planes per reference-arm step")
     ap.add_argument("--shape", default=None, help="nz,ny,nx of a smaller field (profiling captures only)")
