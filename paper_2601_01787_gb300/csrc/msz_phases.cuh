@@ -558,16 +558,17 @@ __device__ __forceinline__ void row_word_of(uint32_t counts, uint32_t j, uint32_
     before = q == 0 ? 0u : q == 1 ? c0 : q == 2 ? c1 : c2;
 }
 
-// Certification of one warp row (planes pm / p0 / pp, row r): marks its
-// uncertified vertices in P.ub and returns them as RowBits.  rowbase = the
-// linear index of (0, y, z).
+// Certification of one warp row (planes pm / p0 / pp, row r) on the warp's
+// diagonal (tile::cert4_diag; cc and carried as there): marks its uncertified
+// vertices in P.ub and returns them as RowBits.  rowbase = the linear index of
+// (0, y, z).
 __device__ __forceinline__ RowBits certify_row(const FieldView &P, const float *pm, const float *p0, const float *pp,
-                                               int r, int x0, uint32_t rowbase) {
+                                               int r, int x0, uint32_t rowbase, tile::CubeCarry &cc, bool carried) {
     using namespace tile;
     const GridDev &G = P.G;
     const uint32_t lane = lane_id();
     const int xl = x0 + 4 * (int)lane;
-    const uint32_t cert = cert4(pm, p0, pp, r, lane, P.two_xi);
+    const uint32_t cert = cert4_diag(pm, p0, pp, r, lane, P.two_xi, cc, carried);
     const uint32_t i0 = rowbase + (uint32_t)xl;
     uint32_t nib = 0;
 #pragma unroll
@@ -589,31 +590,37 @@ __device__ __forceinline__ RowBits certify_row(const FieldView &P, const float *
     return b;
 }
 
-// The code pass on two warp rows at once (warp-collective): row r of plane
-// z (staged planes pm / p0 / pp) and, when `two`, of plane z+1 (p0 / pp /
-// pq); the second field soff floats after each plane.  Both rows are
-// certified first; their uncertified vertices then share rounds of 32 (one a
-// lane), so a round's exact codes -- of f, written to codes_f, and, when
-// DETECT, of the second field, compared with it -- serve up to 32 vertices
-// of either row instead of the dozen or so that one row of a smooth field
-// holds.
+// The code pass on two consecutive rows of a warp's diagonal (warp-
+// collective): row ra of plane z (staged planes pm / p0 / pp) when has_a, and
+// row rb of plane z+1 (p0 / pp / pq) when has_b; rowbase_a / rowbase_b = the
+// linear index of (0, y, z) of each; the second field soff floats after each
+// plane.  carried: cc holds the unit cubes of row ra-1 of plane z-1; on
+// return it says whether cc holds those of row rb of plane z+1.  Both rows
+// are certified first; their uncertified vertices then share rounds of 32
+// (one a lane), so a round's exact codes -- of f, written to codes_f, and,
+// when DETECT, of the second field, compared with it -- serve up to 32
+// vertices of either row instead of the dozen or so that one row of a smooth
+// field holds.
 template <bool DETECT>
 __device__ __forceinline__ void tile_rows2(const FieldView &P, const float *pm, const float *p0, const float *pp,
-                                           const float *pq, int soff, int r, int x0, uint32_t rowbase, bool two,
-                                           uint32_t &distorted) {
+                                           const float *pq, int soff, int ra, bool has_a, int rb, bool has_b, int x0,
+                                           uint32_t rowbase_a, uint32_t rowbase_b, tile::CubeCarry &cc,
+                                           bool &carried, uint32_t &distorted) {
     const uint32_t lane = lane_id();
-    const uint32_t nxy = P.G.nxy;
-    const RowBits A = certify_row(P, pm, p0, pp, r, x0, rowbase);
-    RowBits B;
-    B.w = B.counts = B.total = 0u;
-    if (two) B = certify_row(P, p0, pp, pq, r, x0, rowbase + nxy);
+    RowBits A, B;
+    A.w = A.counts = A.total = 0u;
+    B = A;
+    if (has_a) A = certify_row(P, pm, p0, pp, ra, x0, rowbase_a, cc, carried);
+    carried = has_a && rb == ra + 1;
+    if (has_b) B = certify_row(P, p0, pp, pq, rb, x0, rowbase_b, cc, carried);
+    carried = has_b;
     const uint32_t total = A.total + B.total;
     Emitter E{P.dm[1], 0};
     for (uint32_t j0 = 0; j0 < total; j0 += 32u) {
         const uint32_t j = j0 + lane;
         const bool has = j < total;
         const bool sec = j >= A.total;  // a vertex of the second row
-        const uint32_t base = (sec ? rowbase + nxy : rowbase) + (uint32_t)x0;
+        const uint32_t base = (sec ? rowbase_b : rowbase_a) + (uint32_t)x0;
         // the word of each row the lane's vertex would be in (every lane
         // shuffles both rows' words), then the one row's column
         uint32_t qa, ba, qb, bb;
@@ -624,6 +631,7 @@ __device__ __forceinline__ void tile_rows2(const FieldView &P, const float *pm, 
         if (has) {
             col = 32u * (sec ? qb : qa) + tile::nth_set(sec ? wb : wa, sec ? j - A.total - bb : j - ba);
             const float *qm = sec ? p0 : pm, *q0 = sec ? pp : p0, *qp = sec ? pq : pp;
+            const int r = sec ? rb : ra;
             cf = tile::code1(qm, q0, qp, r, 4 + (int)col);
             P.codes_f[base + col] = (uint8_t)cf;
             if (DETECT) cg = tile::code1(qm + soff, q0 + soff, qp + soff, r, 4 + (int)col);
@@ -769,23 +777,35 @@ __device__ __forceinline__ void first_tile(const FieldView &P, int x0, int y0, i
     issue(zb);
     issue(zb + 1);
     issue(zb + 2);
-    const int y = y0 + (int)warp, r = (int)warp + 1;
     auto plane = [&](int p) { return smem + ((p - zb + 1) % NS) * SLOT; };
     if constexpr (PAIR) {
+        // each warp walks a diagonal: row ra of plane z, then row rb = ra+1
+        // of plane z+1 (tile::diag_row)
+        tile::CubeCarry cc;
+        bool carried = false;
         for (int z = zb; z < ze; z += 2) {
             cp_async_wait<0>();  // planes up to z+2 of this thread have landed
             __syncthreads();     // ... of every thread; the slots of z-3 and z-2 are free
             issue(z + 3);
             issue(z + 4);
-            if (y >= (int)G.ny) continue;
             const bool two = z + 1 < ze;
-            const uint32_t rowbase = (uint32_t)z * G.nxy + (uint32_t)y * G.nx;
-            own_row_cp<DETECT>(P, plane(z), r, x0, rowbase, bad);
-            if (two) own_row_cp<DETECT>(P, plane(z + 1), r, x0, rowbase + G.nxy, bad);
-            tile_rows2<DETECT>(P, plane(z - 1), plane(z), plane(z + 1), plane(z + 2), PLANE, r, x0, rowbase, two,
-                               distorted);
+            const int ra = diag_row(warp, z - zb), rb = ra == BY ? 1 : ra + 1;
+            const int ya = y0 + ra - 1, yb = y0 + rb - 1;
+            const bool has_a = ya < (int)G.ny, has_b = two && yb < (int)G.ny;
+            if (ra == 1) carried = false;
+            if (!has_a && !has_b) {
+                carried = false;
+                continue;
+            }
+            const uint32_t rba = (uint32_t)z * G.nxy + (uint32_t)ya * G.nx;
+            const uint32_t rbb = (uint32_t)(z + 1) * G.nxy + (uint32_t)yb * G.nx;
+            if (has_a) own_row_cp<DETECT>(P, plane(z), ra, x0, rba, bad);
+            if (has_b) own_row_cp<DETECT>(P, plane(z + 1), rb, x0, rbb, bad);
+            tile_rows2<DETECT>(P, plane(z - 1), plane(z), plane(z + 1), plane(z + 2), PLANE, ra, has_a, rb, has_b,
+                               x0, rba, rbb, cc, carried, distorted);
         }
     } else {
+        const int y = y0 + (int)warp, r = (int)warp + 1;
         for (int z = zb; z < ze; ++z) {
             cp_async_wait<1>();  // planes up to z+1 of this thread have landed (z+2 may be in flight)
             __syncthreads();     // ... of every thread; the slot of z-2 is free
@@ -1027,8 +1047,10 @@ __device__ __forceinline__ void own_row_tma(const FieldView &P, const float *p0,
 // true; rowbase the linear index of (0, y, z)), pq staging plane z+2, or for
 // row z alone (two false) when the tile's last plane is z.  withhold (a test
 // hook): block 0 never issues its first plane, so its waits run out after
-// kTestWaitNs.
-template <int NBOX, int STEP, int NS, class ROW>
+// kTestWaitNs.  DIAG: the rows are the caller's to choose (each warp's
+// diagonal): row(pm, p0, pp, pq, x0, y0, z, zb, two) runs for every warp and
+// step, whether or not its rows lie in the grid.
+template <int NBOX, int STEP, int NS, bool DIAG = false, class ROW>
 __device__ __forceinline__ void tma_tiles(const FieldView &P, uint32_t tile_z, const CUtensorMap *map0,
                                           const CUtensorMap *map1, uint32_t *tile_next, float *smem_raw,
                                           uint32_t *err, ROW &&row, bool withhold = false) {
@@ -1122,7 +1144,8 @@ __device__ __forceinline__ void tma_tiles(const FieldView &P, uint32_t tile_z, c
             const float *pm = ring + slot_of(z - 1) * TSLOT, *p0 = ring + slot_of(z) * TSLOT;
             const float *pp = ring + slot_of(z + 1) * TSLOT;
             const float *pq = two ? ring + slot_of(z + 2) * TSLOT : pp;
-            if (y < (int)G.ny) row(pm, p0, pp, pq, r, x0, (uint32_t)z * G.nxy + (uint32_t)y * G.nx, two);
+            if constexpr (DIAG) row(pm, p0, pp, pq, x0, y0, z, zb, two);
+            else if (y < (int)G.ny) row(pm, p0, pp, pq, r, x0, (uint32_t)z * G.nxy + (uint32_t)y * G.nx, two);
             __syncwarp();
             release(z - 1);
             if (two) release(z);
@@ -1147,13 +1170,29 @@ __device__ __forceinline__ void first_tiled_tma(const FieldView &P, const CUtens
                                                 uint32_t *tile_next, float *smem_raw, uint32_t *err,
                                                 uint32_t &distorted, bool withhold = false) {
     bool bad = false;
-    tma_tiles<2, 2, tile::kCodeSlots>(
+    tile::CubeCarry cc;
+    bool carried = false;
+    tma_tiles<2, 2, tile::kCodeSlots, true>(
         P, P.tile_z, map_f, map_s, tile_next, smem_raw, err,
-        [&](const float *pm, const float *p0, const float *pp, const float *pq, int r, int x0, uint32_t rowbase,
+        [&](const float *pm, const float *p0, const float *pp, const float *pq, int x0, int y0, int z, int zb,
             bool two) {
-            own_row_tma<DETECT>(P, p0, r, x0, rowbase, bad);
-            if (two) own_row_tma<DETECT>(P, pp, r, x0, rowbase + P.G.nxy, bad);
-            tile_rows2<DETECT>(P, pm, p0, pp, pq, tile::TFIELD, r, x0, rowbase, two, distorted);
+            // each warp walks a diagonal: row ra of plane z, then row rb =
+            // ra+1 of plane z+1 (tile::diag_row)
+            const GridDev &G = P.G;
+            const int ra = tile::diag_row(threadIdx.x >> 5, z - zb), rb = ra == tile::BY ? 1 : ra + 1;
+            const int ya = y0 + ra - 1, yb = y0 + rb - 1;
+            const bool has_a = ya < (int)G.ny, has_b = two && yb < (int)G.ny;
+            if (z == zb || ra == 1) carried = false;
+            if (!has_a && !has_b) {
+                carried = false;
+                return;
+            }
+            const uint32_t rba = (uint32_t)z * G.nxy + (uint32_t)ya * G.nx;
+            const uint32_t rbb = (uint32_t)(z + 1) * G.nxy + (uint32_t)yb * G.nx;
+            if (has_a) own_row_tma<DETECT>(P, p0, ra, x0, rba, bad);
+            if (has_b) own_row_tma<DETECT>(P, pp, rb, x0, rbb, bad);
+            tile_rows2<DETECT>(P, pm, p0, pp, pq, tile::TFIELD, ra, has_a, rb, has_b, x0, rba, rbb, cc, carried,
+                               distorted);
         },
         withhold);
     if (bad) atomicOr(err, kErrInput);

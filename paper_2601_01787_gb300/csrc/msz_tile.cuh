@@ -226,6 +226,124 @@ __device__ __forceinline__ uint32_t cert4(const float *pm, const float *p0, cons
     return cert;
 }
 
+// ------------------------------------------- certification along the diagonal
+// The closed Freudenthal neighbourhood of a vertex i is the union of two unit
+// cubes: C(i) = i + {0,1}^3 (the vertex and its 7 positive offsets) and
+// C(i - (1,1,1)) = i - {0,1}^3 (the vertex and its 7 negative offsets).  The
+// forward cube of a vertex is therefore the backward cube of the vertex one
+// step further along the main diagonal.  A warp that certifies row y of plane
+// z and then row y+1 of plane z+1 forms each cube once and uses it twice,
+// and a cube is itself the union of two 2 x 2 columns (fixed x, y..y+1,
+// z..z+1), each shared by two neighbouring cubes of the row.  Merging these
+// partial results costs about 40 ALU-pipe cycles a vertex against about 70
+// for the 7 row segments of cert4.
+//
+// The vertex itself lies in both cubes, so a strict local maximum or minimum
+// sees its own value twice and is never certified (it only costs an exact
+// examination); no other vertex's margins change.
+
+// The two largest and two smallest values of a multiset (NaN: no value).
+struct T2 {
+    float h1, h2, l1, l2;
+};
+
+// The union of two multisets: the larger leader leads, the runner-up is the
+// largest of the smaller leader and both runners-up (the leaders compared
+// with NaN propagation, so an empty side adds nothing).
+__device__ __forceinline__ T2 t2_merge(const T2 &a, const T2 &b) {
+    T2 t;
+    t.h1 = fmaxf(a.h1, b.h1);
+    t.h2 = fmax3(fmin_nan(a.h1, b.h1), a.h2, b.h2);
+    t.l1 = fminf(a.l1, b.l1);
+    t.l2 = fmin3(fmax_nan(a.l1, b.l1), a.l2, b.l2);
+    return t;
+}
+
+// T2 of a 2 x 2 column: the pairs (a, b) and (c, d).  A pair with one NaN
+// counts its other value twice (a false tie at worst, which withholds a
+// certification but never grants one); a pair of two NaNs counts nothing.
+__device__ __forceinline__ T2 t2_quad(float a, float b, float c, float d) {
+    const float hi1 = fmaxf(a, b), lo1 = fminf(a, b), hi2 = fmaxf(c, d), lo2 = fminf(c, d);
+    T2 t;
+    t.h1 = fmaxf(hi1, hi2);
+    t.h2 = fmax3(fmin_nan(hi1, hi2), lo1, lo2);
+    t.l1 = fminf(lo1, lo2);
+    t.l2 = fmin3(fmax_nan(lo1, lo2), hi1, hi2);
+    return t;
+}
+
+// One staged row at the lane's columns x-1 .. x-1+NV-1 (x = x0 + 4 lane;
+// NV = 5 or 6): one 16-byte load, the outer columns passed by warp shuffles.
+template <int NV>
+__device__ __forceinline__ void row_vals(const float *row, uint32_t lane, float (&v)[NV]) {
+    static_assert(NV == 5 || NV == 6, "columns x-1 .. x+3 or x+4");
+    const float4 q = *reinterpret_cast<const float4 *>(row + 4 + 4 * lane);
+    float left = __shfl_up_sync(kFull, q.w, 1);
+    if (lane == 0) left = row[3];
+    v[0] = left; v[1] = q.x; v[2] = q.y; v[3] = q.z; v[4] = q.w;
+    if constexpr (NV == 6) {
+        float right = __shfl_down_sync(kFull, q.x, 1);
+        if (lane == 31) right = row[4 + BX];
+        v[5] = right;
+    }
+}
+
+// T2 of the unit cubes (c..c+1) x (y..y+1) x (z..z+1) at the lane's columns
+// c = x-1 .. x-1+NC-1, from staged rows r (y) and r+1 of planes pa (z) and
+// pb (z+1): each 2 x 2 column once, each cube the merge of two of them.
+template <int NC>
+__device__ __forceinline__ void unit_cubes(const float *pa, const float *pb, int r, uint32_t lane, T2 (&cb)[NC]) {
+    float v0[NC + 1], v1[NC + 1], v2[NC + 1], v3[NC + 1];
+    row_vals<NC + 1>(pa + r * PW, lane, v0);
+    row_vals<NC + 1>(pa + (r + 1) * PW, lane, v1);
+    row_vals<NC + 1>(pb + r * PW, lane, v2);
+    row_vals<NC + 1>(pb + (r + 1) * PW, lane, v3);
+    T2 prev = t2_quad(v0[0], v1[0], v2[0], v3[0]);
+#pragma unroll
+    for (int k = 1; k <= NC; ++k) {
+        const T2 cur = t2_quad(v0[k], v1[k], v2[k], v3[k]);
+        cb[k - 1] = t2_merge(prev, cur);
+        prev = cur;
+    }
+}
+
+// The backward cubes of the lane's 4 vertices in the next row on the
+// diagonal: the unit cubes at columns x-1 .. x+2 of the row certified last.
+struct CubeCarry {
+    T2 c[4];
+};
+
+// Certification bits (bit e) of the lane's 4 vertices in warp row r of the
+// plane staged at p0 (p1: plane z+1; pm: plane z-1, read only when !carried).
+// carried: cc holds the unit cubes at (x-1 .., y-1, z-1), i.e. this warp
+// certified row r-1 of plane z-1 last; otherwise they are formed here.  On
+// return cc holds this row's cubes for row r+1 of plane z+1.  A vertex is
+// certified when in f its winner beats the runner-up by more than 2 xi in
+// both directions (differences rounded down), as in cert4.
+__device__ __forceinline__ uint32_t cert4_diag(const float *pm, const float *p0, const float *p1, int r, uint32_t lane,
+                                               float two_xi, CubeCarry &cc, bool carried) {
+    if (!carried) unit_cubes<4>(pm, p0, r - 1, lane, cc.c);
+    T2 fw[5];
+    unit_cubes<5>(p0, p1, r, lane, fw);
+    uint32_t cert = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const T2 &a = fw[e + 1], &b = cc.c[e];
+        const float h1 = fmaxf(a.h1, b.h1), h2 = fmax3(fmin_nan(a.h1, b.h1), a.h2, b.h2);
+        const float l1 = fminf(a.l1, b.l1), l2 = fmin3(fmax_nan(a.l1, b.l1), a.l2, b.l2);
+        cert |= (uint32_t)(__fsub_rd(h1, h2) > two_xi && __fsub_rd(l2, l1) > two_xi) << e;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) cc.c[e] = fw[e];
+    return cert;
+}
+
+// Row of warp w on the diagonal at plane offset s = z - zb of a tile: row
+// (w + s) mod BY, as a staged row index (1 .. BY).  Over a plane the BY warps
+// cover every row once; from one plane to the next each warp moves one row
+// up, wrapping from the last row to the first.
+__device__ __forceinline__ int diag_row(uint32_t warp, int s) { return (int)((warp + (uint32_t)s) & (BY - 1)) + 1; }
+
 // Position of the k-th set bit (k counted from 0) of w; k < popc(w).
 __device__ __forceinline__ uint32_t nth_set(uint32_t w, uint32_t k) {
     uint32_t pos = 0;
