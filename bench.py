@@ -320,7 +320,7 @@ def run_ours(args, ws, rank, local):
     hidx = torch.empty(cap, dtype=torch.int32).pin_memory()
     hdel = torch.empty(cap, dtype=torch.float32).pin_memory()
     hws = api.workspace(api.host_workspace_size(fl.shape, cap), dev)
-    e2e_steps = max(5, args.steps // 10)
+    e2e_steps = max(10, args.steps // 2)
 
     def hstep():
         return api.correct_host(hf, hfh, fl.xi, out=hout, edit_idx=hidx, edit_delta=hdel, edit_capacity=cap,

@@ -791,6 +791,7 @@ struct msz_pipeline {
     struct Slot {
         cudaEvent_t in_done, comp_done, out_done;
         bool used;
+        bool stream_dev;  // the encoded stream went to the host buffer from the device (stream_out_async)
         float *h_out;
         uint32_t *h_idx;
         float *h_del;
@@ -802,9 +803,15 @@ struct msz_pipeline {
         uint32_t error, pad;
         unsigned long long total_words;
     };
-    msz::Ctrl *h_ctrl;  // pinned: the control block, sweep-0 record and encoder state of each slot
+    // pinned and mapped: the control block, sweep-0 record and encoder state
+    // of each slot, written by k_readback (the d_ pointers: their device
+    // addresses)
+    msz::Ctrl *h_ctrl;
     msz::SweepRec *h_rec;
     EncCtrl *h_enc;
+    msz::Ctrl *d_hctrl;
+    msz::SweepRec *d_hrec;
+    EncCtrl *d_henc;
     int head, tail, pending;
 };
 
@@ -844,10 +851,13 @@ static msz_status pipeline_create(msz_grid grid, int64_t edit_capacity, bool enc
     bool ok = cudaStreamCreateWithFlags(&pl->s_in, cudaStreamNonBlocking) == cudaSuccess &&
               cudaStreamCreateWithFlags(&pl->s_comp, cudaStreamNonBlocking) == cudaSuccess &&
               cudaStreamCreateWithFlags(&pl->s_out, cudaStreamNonBlocking) == cudaSuccess &&
-              cudaHostAlloc((void **)&pl->h_ctrl, 2 * sizeof(Ctrl), cudaHostAllocDefault) == cudaSuccess &&
-              cudaHostAlloc((void **)&pl->h_rec, 2 * sizeof(SweepRec), cudaHostAllocDefault) == cudaSuccess &&
-              cudaHostAlloc((void **)&pl->h_enc, 2 * sizeof(msz_pipeline::EncCtrl), cudaHostAllocDefault) ==
-                  cudaSuccess;
+              cudaHostAlloc((void **)&pl->h_ctrl, 2 * sizeof(Ctrl), cudaHostAllocMapped) == cudaSuccess &&
+              cudaHostAlloc((void **)&pl->h_rec, 2 * sizeof(SweepRec), cudaHostAllocMapped) == cudaSuccess &&
+              cudaHostAlloc((void **)&pl->h_enc, 2 * sizeof(msz_pipeline::EncCtrl), cudaHostAllocMapped) ==
+                  cudaSuccess &&
+              cudaHostGetDevicePointer((void **)&pl->d_hctrl, pl->h_ctrl, 0) == cudaSuccess &&
+              cudaHostGetDevicePointer((void **)&pl->d_hrec, pl->h_rec, 0) == cudaSuccess &&
+              cudaHostGetDevicePointer((void **)&pl->d_henc, pl->h_enc, 0) == cudaSuccess;
     for (int k = 0; ok && k < 2; ++k)
         ok = cudaEventCreateWithFlags(&pl->slot[k].in_done, cudaEventDisableTiming) == cudaSuccess &&
              cudaEventCreateWithFlags(&pl->slot[k].comp_done, cudaEventDisableTiming) == cudaSuccess &&
@@ -881,6 +891,35 @@ static SlotBufs slot_bufs(const msz_pipeline *pl, int k) {
     return b;
 }
 
+// The small results of a slot's correction -- the control block, sweep 0's
+// record and, when encoded, the encoder's state -- written by a kernel into
+// mapped pinned host memory.  A download on the correction's stream would
+// sit in a copy engine's queue waiting for the correction, and the next
+// field's upload, queued behind it, would wait too: the link would idle
+// while each field is corrected.
+__global__ void k_readback(const uint32_t *ctrl, uint32_t *h_ctrl, const uint32_t *rec, uint32_t *h_rec,
+                           const uint32_t *enc, uint32_t *h_enc) {
+    constexpr uint32_t nc = sizeof(Ctrl) / 4, nr = sizeof(SweepRec) / 4;
+    constexpr uint32_t ne = sizeof(msz_pipeline::EncCtrl) / 4;
+    static_assert(sizeof(Ctrl) % 4 == 0 && sizeof(SweepRec) % 4 == 0, "word copies");
+    for (uint32_t i = threadIdx.x; i < nc + nr + ne; i += blockDim.x) {
+        if (i < nc) h_ctrl[i] = ctrl[i];
+        else if (i < nc + nr) h_rec[i - nc] = rec[i - nc];
+        else if (enc) h_enc[i - nc - nr] = enc[i - nc - nr];
+    }
+}
+
+// The device address of host buffer p when the device can write it (pinned
+// or registered memory), else null.
+static void *device_view(void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();  // pageable memory on older runtimes: not an error here
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 // Queues one field into the head slot: inputs up, the correction (and, when
 // encoded, the edit list's stream), the result down.
 static msz_status pipeline_submit(msz_pipeline *pl, const float *h_f, const float *h_fhat, float xi, float *h_out,
@@ -910,18 +949,25 @@ static msz_status pipeline_submit(msz_pipeline *pl, const float *h_f, const floa
     if (cudaStreamWaitEvent(pl->s_comp, sl.in_done, 0) != cudaSuccess) return MSZ_ERR_CUDA;
     if (sl.used && cudaStreamWaitEvent(pl->s_comp, sl.out_done, 0) != cudaSuccess) return MSZ_ERR_CUDA;
     if ((st = enqueue_correct(sl.P, dev, pl->s_comp)) != MSZ_OK) return st;
+    sl.stream_dev = false;
     if (pl->encoded) {
         st = encode_async(b.fhat, b.g, pl->G.n, b.idx, &sl.P.ctrl->edit_count, (uint64_t)pl->cap, b.stream,
                           pl->stream_cap, b.enc_ws, dev, pl->s_comp);
         if (st != MSZ_OK) return st;
-        if (cudaMemcpyAsync(&pl->h_enc[k], b.enc_ws, sizeof(msz_pipeline::EncCtrl), cudaMemcpyDeviceToHost,
-                            pl->s_comp) != cudaSuccess)
-            return MSZ_ERR_CUDA;
+        // the stream into the caller's buffer from the device when it can
+        // (its length is known there), else by a copy at collect
+        if (uint8_t *hs = (uint8_t *)device_view(h_stream)) {
+            st = stream_out_async(b.stream, b.enc_ws, &sl.P.ctrl->edit_count, (uint64_t)pl->cap, hs, h_stream_cap,
+                                  pl->s_comp);
+            if (st != MSZ_OK) return st;
+            sl.stream_dev = true;
+        }
     }
-    if (cudaMemcpyAsync(&pl->h_ctrl[k], sl.P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, pl->s_comp) != cudaSuccess ||
-        cudaMemcpyAsync(&pl->h_rec[k], sl.P.log, sizeof(SweepRec), cudaMemcpyDeviceToHost, pl->s_comp) !=
-            cudaSuccess ||
-        cudaEventRecord(sl.comp_done, pl->s_comp) != cudaSuccess)
+    k_readback<<<1, 64, 0, pl->s_comp>>>((const uint32_t *)sl.P.ctrl, (uint32_t *)&pl->d_hctrl[k],
+                                         (const uint32_t *)sl.P.log, (uint32_t *)&pl->d_hrec[k],
+                                         pl->encoded ? (const uint32_t *)b.enc_ws : nullptr,
+                                         (uint32_t *)&pl->d_henc[k]);
+    if (cudaGetLastError() != cudaSuccess || cudaEventRecord(sl.comp_done, pl->s_comp) != cudaSuccess)
         return MSZ_ERR_CUDA;
     // the corrected field down (an encoded pipeline's stream comes down at
     // collect, when its length is known)
@@ -961,9 +1007,10 @@ static msz_status pipeline_results(msz_pipeline *pl, int k, int64_t *h_edit_coun
             if (e.error & 1u) return MSZ_ERR_INVALID_ARG;  // not expected: the loop lists edits in order
             if (e.error || len > sl.h_stream_cap) {
                 st = MSZ_ERR_CAPACITY;
-            } else if (cudaMemcpyAsync(sl.h_stream, b.stream, (size_t)len, cudaMemcpyDeviceToHost, pl->s_out) !=
-                           cudaSuccess ||
-                       cudaEventRecord(sl.out_done, pl->s_out) != cudaSuccess) {
+            } else if (!sl.stream_dev &&
+                       (cudaMemcpyAsync(sl.h_stream, b.stream, (size_t)len, cudaMemcpyDeviceToHost, pl->s_out) !=
+                            cudaSuccess ||
+                        cudaEventRecord(sl.out_done, pl->s_out) != cudaSuccess)) {
                 return MSZ_ERR_CUDA;
             }
         }

@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_apply(const uint8_t *in, uint64
     }
 }
 
-inline uint64_t blocks_of(int64_t count) { return ((uint64_t)count + B - 1) / B; }
+__host__ __device__ inline uint64_t blocks_of(int64_t count) { return ((uint64_t)count + B - 1) / B; }
 
 struct Work {
     Ctrl *ctrl;
@@ -352,6 +352,30 @@ msz_status encode_async(const float *d_fhat, const float *d_g, uint32_t n, const
     edits::k_scan<<<1, edits::kScanThreads, 0, s>>>(w.words, d_count, count_cap, w.start, w.ctrl);
     edits::k_pack<<<grid, edits::kWarps * 32, 0, s>>>(d_fhat, d_g, d_idx, d_count, count_cap, w.start, w.wd, w.wm,
                                                       d_stream, capacity, w.ctrl);
+    return cudaGetLastError() == cudaSuccess ? MSZ_OK : MSZ_ERR_CUDA;
+}
+
+namespace edits {
+// The stream into host memory the device addresses (stream_out_async): a
+// grid-stride copy, 16 bytes a thread where both ends are 16-byte aligned.
+__global__ void k_stream_out(const uint8_t *src, const Ctrl *ctrl, const unsigned long long *d_count,
+                             uint64_t count_cap, uint8_t *dst, uint64_t capacity) {
+    const uint64_t count = edit_count(d_count, count_cap);
+    const uint64_t len = layout_of(blocks_of((int64_t)count)).payload + 4ull * ctrl->total_words;
+    if (ctrl->error || len > capacity) return;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (uint64_t)gridDim.x * blockDim.x;
+    const bool vec = (((uintptr_t)src | (uintptr_t)dst) & 15u) == 0;
+    const uint64_t nv = vec ? len / 16 : 0;
+    for (uint64_t i = tid; i < nv; i += stride)
+        reinterpret_cast<uint4 *>(dst)[i] = reinterpret_cast<const uint4 *>(src)[i];
+    for (uint64_t i = 16 * nv + tid; i < len; i += stride) dst[i] = src[i];
+}
+}  // namespace edits
+
+msz_status stream_out_async(const uint8_t *d_stream, const void *d_ws, const unsigned long long *d_count,
+                            uint64_t count_cap, uint8_t *h_dst, size_t capacity, cudaStream_t s) {
+    const edits::Work w = edits::work_of(const_cast<void *>(d_ws), edits::blocks_of((int64_t)count_cap));
+    edits::k_stream_out<<<64, 256, 0, s>>>(d_stream, w.ctrl, d_count, count_cap, h_dst, (uint64_t)capacity);
     return cudaGetLastError() == cudaSuccess ? MSZ_OK : MSZ_ERR_CUDA;
 }
 

@@ -28,4 +28,14 @@ msz_status encode_async(const float *d_fhat, const float *d_g, uint32_t n, const
                         const unsigned long long *d_count, uint64_t count_cap, uint8_t *d_stream, size_t capacity,
                         void *d_ws, const DeviceInfo &dev, cudaStream_t s);
 
+// Copies the stream that encode_async wrote (d_stream, its state in d_ws)
+// into host memory that the device can address (h_dst: its device pointer,
+// capacity bytes), on stream s: the length is known on the device only, so
+// a kernel writes it there, and no copy engine is queued behind the
+// correction (an upload queued behind a download that waits for a kernel
+// would wait with it).  Nothing is written when the encode reported an error
+// or the stream exceeds the capacity (the host sees both in the state).
+msz_status stream_out_async(const uint8_t *d_stream, const void *d_ws, const unsigned long long *d_count,
+                            uint64_t count_cap, uint8_t *h_dst, size_t capacity, cudaStream_t s);
+
 }  // namespace msz

@@ -6,11 +6,13 @@
 // shared-memory slots filled by cp.async: planes z+2 and z+3 are in flight
 // while plane z is computed from the slots of z-1, z and z+1.  Staged
 // positions outside the grid hold NaN, which never wins a comparison.  Each
-// lane certifies 4 consecutive vertices of its warp's row from the two
-// largest and two smallest values of their closed neighbourhoods, read as 7
-// row segments (one 16-byte shared-memory load plus one halo value passed by
-// a warp shuffle each); the exact codes are then formed one vertex per lane,
-// only for the vertices left uncertified.
+// lane certifies 4 consecutive vertices of a row from the two largest and
+// two smallest values of their closed neighbourhoods: in the one-plane form
+// (cert4) read as 7 row segments (one 16-byte shared-memory load plus one
+// halo value passed by a warp shuffle each); in the two-plane forms of the
+// code pass (cert4_diag) as two unit cubes, each warp walking a diagonal of
+// the tile so that every cube serves two vertices.  The exact codes are then
+// formed one vertex per lane, only for the vertices left uncertified.
 #pragma once
 
 #include <cuda_runtime.h>

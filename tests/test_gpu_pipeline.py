@@ -96,8 +96,12 @@ def test_encoded_sequence_matches_the_oracle(api):
               synth.peaks3d(shape, seed=80 + k, eb_rel=1e-4) for k in range(4)]
     refs = [oracle.correct(fl.f, fl.fhat, fl.xi) for fl in fields]
     pl = api.Pipeline(shape, encoded=True)
-    bufs = [(_pinned(fl.f), _pinned(fl.fhat), torch.empty(pl.stream_bound(), dtype=torch.uint8).pin_memory())
-            for fl in fields]
+    # stream buffers: pinned (the device writes the stream into them) and
+    # pageable (copied at collect)
+    bufs = [(_pinned(fl.f), _pinned(fl.fhat),
+             torch.empty(pl.stream_bound(), dtype=torch.uint8).pin_memory() if k % 3 != 1 else
+             np.zeros(pl.stream_bound(), dtype=np.uint8))
+            for k, fl in enumerate(fields)]
     got = []
     for k, (fl, b) in enumerate(zip(fields, bufs)):
         if k >= 2:
@@ -107,9 +111,10 @@ def test_encoded_sequence_matches_the_oracle(api):
     for fl, ref, res in zip(fields, refs, got):
         assert res.status == api.OK and res.edit_count == ref.edit_count
         want = E.encode(*E.edits_of(fl.fhat, ref.g))
-        assert res.stream.numpy().tobytes() == want
+        stream = res.stream if torch.is_tensor(res.stream) else torch.from_numpy(np.array(res.stream))
+        assert stream.numpy().tobytes() == want
         field = torch.from_numpy(fl.fhat.copy()).cuda().reshape(-1)
-        assert api.decode_edits(res.stream.cuda(), field) == ref.edit_count
+        assert api.decode_edits(stream.cuda(), field) == ref.edit_count
         assert np.array_equal(field.cpu().numpy().view(np.uint32), ref.g.reshape(-1).view(np.uint32))
     # a field-mode call on an encoded pipeline is rejected
     import ctypes
@@ -123,8 +128,8 @@ def test_encoded_stream_capacity(api):
     ref = oracle.correct(fl.f, fl.fhat, fl.xi)
     assert ref.edit_count > 100
     pl = api.Pipeline(shape, encoded=True)
-    small = torch.empty(64, dtype=torch.uint8).pin_memory()
-    pl.submit(_pinned(fl.f), _pinned(fl.fhat), fl.xi, small)
-    r = pl.collect()
-    assert r.status == api.ERR_CAPACITY and r.edit_count == ref.edit_count
+    for small in (torch.empty(64, dtype=torch.uint8).pin_memory(), np.zeros(64, dtype=np.uint8)):
+        pl.submit(_pinned(fl.f), _pinned(fl.fhat), fl.xi, small)
+        r = pl.collect()
+        assert r.status == api.ERR_CAPACITY and r.edit_count == ref.edit_count
     pl.close()
