@@ -31,6 +31,11 @@ pytestmark = pytest.mark.gpu
 PERLIN_256 = ("perlin", dict(shape=(256, 256, 256), seed=21, eb_rel=1e-4))
 PEAKS_256 = ("peaks", dict(shape=(256, 256, 256), seed=22, eb_rel=1e-4))
 PERLIN_512 = ("perlin", dict(shape=(512, 512, 512), seed=2, eb_rel=1e-4))  # the bench workload
+# Ragged grids the TMA maps cannot describe (x extent not a multiple of 4):
+# the cp.async staging of the code pass and of the whole-grid detection,
+# partial tile rows (253 = 31 x 8 + 5) and an odd last tile depth (251).
+PERLIN_RAGGED = ("perlin", dict(shape=(251, 253, 254), seed=23, eb_rel=1e-4))
+PEAKS_RAGGED = ("peaks", dict(shape=(251, 253, 254), seed=24, eb_rel=1e-4))
 BATCH = 64
 
 
@@ -47,7 +52,8 @@ def refs():
     """Every oracle job of this module, submitted at once."""
     pool = oracle_pool.Pool()
     jobs = {"perlin256": pool.submit(PERLIN_256), "peaks256": pool.submit(PEAKS_256),
-            "perlin512": pool.submit(PERLIN_512)}
+            "perlin512": pool.submit(PERLIN_512), "perlin_ragged": pool.submit(PERLIN_RAGGED),
+            "peaks_ragged": pool.submit(PEAKS_RAGGED)}
     for k in range(BATCH):
         jobs[("batch", k)] = pool.submit(("batch", k))
     yield jobs
@@ -110,6 +116,20 @@ def test_peaks256_bit_exact(api, refs, kw):
     ref = refs["peaks256"].result()
     assert ref.sweeps > 10
     check(res, ref, worklist_column=kw.get("dense_min_items") == -1)
+    if kw.get("dense_min_items") == 1:
+        assert res.stats["dense_sweeps"] == res.stats["sweeps"] + 1
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(tile_z=8), dict(tile_z=24)], ids=["default", "tile_z8", "tile_z24"])
+def test_perlin_ragged_bit_exact(api, refs, kw):
+    fl, res = _correct(api, PERLIN_RAGGED, **kw)
+    check(res, refs["perlin_ragged"].result())
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(dense_min_items=1)], ids=["default", "always_dense"])
+def test_peaks_ragged_bit_exact(api, refs, kw):
+    fl, res = _correct(api, PEAKS_RAGGED, **kw)
+    check(res, refs["peaks_ragged"].result())
     if kw.get("dense_min_items") == 1:
         assert res.stats["dense_sweeps"] == res.stats["sweeps"] + 1
 
