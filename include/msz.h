@@ -370,7 +370,10 @@ msz_status msz_learned_features(const float *d_f, const float *d_fhat, float xi,
  * 32 each) from FP32 weights d_w[27][cout_real][cin_real], zero-padded;
  * mirror != 0: the image of the backward-data conv (input = gradient of the
  * forward output, weights of the mirrored offset, channels swapped).  d_img:
- * msz_learned_weight_image_size(cin, cout) bytes. */
+ * msz_learned_weight_image_size(cin, cout) bytes (0 for an unsupported
+ * shape): per 16-channel slab pair and (dx, dz) offset, a strip of the five
+ * dy = 2 .. -2 weight blocks (the outer two zero), so that one tensor-core
+ * operand covers two output rows. */
 size_t msz_learned_weight_image_size(int32_t cin, int32_t cout);
 msz_status msz_learned_weight_image(const float *d_w, int32_t cout_real, int32_t cin_real, int32_t cin,
                                     int32_t cout, int32_t mirror, uint16_t *d_img, msz_stream_t stream);

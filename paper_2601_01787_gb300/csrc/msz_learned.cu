@@ -166,17 +166,30 @@ __device__ __forceinline__ uint16_t f_to_bf16(float v) {
     return __bfloat16_as_ushort(__float2bfloat16_rn(v));
 }
 
+// Weight image: one strip per (slab pair sp, dx, dz) of 2 K halves x 5 dy
+// blocks x COUT output channels x 8 input channels (BF16, 16 bytes a row):
+// block b holds the weights of offset dy = 2 - b, blocks 0 and 4 (dy = +-2)
+// are zero.  An MMA takes two neighbouring blocks as one B operand of N =
+// 2 COUT rows, so that one staged input line (the A operand) feeds both output
+// rows of a plane pair: block 3 - dyl for the tile's row y0 (dy = dyl - 1)
+// and the next for row y0 + 1 (dy = dyl - 2); a zero block stands for the
+// offset that reaches past the kernel.
+constexpr int kDyBlocks = 5;
+__host__ __device__ constexpr int img_strip_bytes(int cout) { return 2 * kDyBlocks * cout * 16; }
+__host__ __device__ constexpr int img_bytes(int cin, int cout) { return (cin / 16) * 9 * img_strip_bytes(cout); }
+
 template <int CIN, int COUT>
 struct ConvShape {
     static constexpr int KG = CIN / 8;                        // 8-channel slabs per voxel
     static constexpr int NP = KG / 2;                         // K = 16 slab pairs per tile (1 or 2)
-    static constexpr int WBYTES = 27 * KG * COUT * 16;        // weight image
+    static constexpr int WBYTES = img_bytes(CIN, COUT);       // weight image
     static constexpr int WAL = (WBYTES + 1023) / 1024 * 1024;
     static constexpr int SMEM = WAL + kStages * kStageBytes;
     // kind::f16: FP32 accumulator (bit 4), BF16 A and B (bits 7, 10), K-major,
-    // N >> 3 at bit 17, M >> 4 at bit 24 (M = 128)
-    static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(COUT >> 3) << 17) |
+    // N >> 3 at bit 17, M >> 4 at bit 24 (M = 128); N = 2 COUT (two output rows)
+    static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((2 * COUT) >> 3) << 17) |
                                       ((uint32_t)(128 >> 4) << 24);
+    static_assert(SMEM + 1024 <= 227 * 1024, "weight image and stages must fit one block's shared memory");
 };
 
 template <int CIN, int COUT, int MODE>
@@ -256,22 +269,27 @@ __global__ void __launch_bounds__(kConvThreads, 1)
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    // descriptors of offset 0 of this stage and slab pair; every MMA
-                    // adds a compile-time start offset (in 16-byte units: the start
-                    // field stays below 2^14 for addresses under 256 KB)
+                    // descriptors of the first line of this stage and of this slab
+                    // pair's first strip; every MMA adds a compile-time start offset
+                    // (in 16-byte units: the start field stays below 2^14 for
+                    // addresses under 256 KB)
                     const uint64_t a0 = sdesc(sstg + st * kStageBytes, kSlabBytes, 128);
-                    const uint64_t b0 = sdesc(swsm + 2 * sp * COUT * 16, COUT * 16, 128);
-                    const uint32_t d0 = tmem + buf * 4 * COUT;
+                    const uint64_t b0 = sdesc(swsm + sp * 9 * img_strip_bytes(COUT), kDyBlocks * COUT * 16, 128);
                     const uint32_t first = sp > 0 ? 1u : 0u;
+                    // plane rz of the tile: accumulators r = 2 rz (row y0) and
+                    // 2 rz + 1 (row y0 + 1) side by side, N = 2 COUT; input line
+                    // (dyl, dzl) of the staged 4 x 4 for kernel offsets (dx, dz)
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) {
+                    for (int rz = 0; rz < 2; ++rz) {
 #pragma unroll
-                        for (int o = 0; o < 27; ++o) {
-                            const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
-                            const int L = ((r >> 1) + 1 + dz) * 4 + ((r & 1) + 1 + dy);
+                        for (int i = 0; i < 36; ++i) {
+                            const int dx = i % 3 - 1, dyl = (i / 3) % 4, dz = i / 12 - 1;
+                            const int L = (rz + 1 + dz) * 4 + dyl;
                             const uint64_t a = a0 + (uint64_t)((L * kLineBytes + (1 + dx) * 16) >> 4);
-                            const uint64_t b = b0 + (uint64_t)((o * S::KG * COUT * 16) >> 4);
-                            mma_bf16(d0 + r * COUT, a, b, S::IDESC, o > 0 ? 1u : first);
+                            const int strip = (dx + 1) * 3 + (dz + 1);
+                            const uint64_t b =
+                                b0 + (uint64_t)((strip * img_strip_bytes(COUT) + (3 - dyl) * COUT * 16) >> 4);
+                            mma_bf16(tmem + (buf * 4 + 2 * rz) * COUT, a, b, S::IDESC, i > 0 ? 1u : first);
                         }
                     }
                     mma_commit(smem_u32(&bar_free[st]));
@@ -437,22 +455,32 @@ __global__ void __launch_bounds__(256) k_features(const float *f, const float *f
 
 // ------------------------------------------------------------ weights
 // FP32 weights w[o][cout][cin] (cout < cout_real, cin < cin_real) -> BF16 image
-// [o][kg][n][8] of a conv with CIN >= cin_real input and COUT >= cout_real
-// output channels (zero padding).  mirror: the backward-data image, i.e. the
-// conv of the gradient with w[26 - o] and input / output channels swapped.
+// of a conv with CIN >= cin_real input and COUT >= cout_real output channels
+// (zero padding), in strips (see img_strip_bytes): byte offset
+// (((sp * 3 + dx + 1) * 3 + dz + 1) * 2 + h) * 5 * COUT * 16 + (b * COUT + n) * 16
+// + 2 k8 holds input channel 16 sp + 8 h + k8 of output channel n at offset
+// (dx, dy = 2 - b, dz); offset o = (dz + 1) * 9 + (dy + 1) * 3 + dx + 1.
+// mirror: the backward-data image, i.e. the conv of the gradient with
+// w[26 - o] and input / output channels swapped.
 __global__ void k_weight_image(const float *w, int cout_real, int cin_real, int CIN, int COUT, int mirror,
                                uint16_t *img) {
-    const int KG = CIN / 8;
-    const int total = 27 * KG * COUT * 8;
+    const int NP = CIN / 16;
+    const int total = NP * 9 * 2 * kDyBlocks * COUT * 8;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
-        const int k8 = e & 7, n = (e >> 3) % COUT, kg = (e >> 3) / COUT % KG, o = (e >> 3) / COUT / KG;
-        const int kin = kg * 8 + k8;  // input channel of this image's conv
+        const int k8 = e & 7, n = (e >> 3) % COUT, bl = (e >> 3) / COUT % kDyBlocks;
+        const int h = (e >> 3) / COUT / kDyBlocks % 2, sdz = (e >> 3) / COUT / kDyBlocks / 2;
+        const int dz = sdz % 3 - 1, dx = sdz / 3 % 3 - 1, sp = sdz / 9;
+        const int dy = 2 - bl;
         float v = 0.0f;
-        if (!mirror) {
-            if (n < cout_real && kin < cin_real) v = w[((size_t)o * cout_real + n) * cin_real + kin];
-        } else {
-            // image conv: input = gradient channels (= forward cout), output = forward cin
-            if (kin < cout_real && n < cin_real) v = w[((size_t)(26 - o) * cout_real + kin) * cin_real + n];
+        if (dy >= -1 && dy <= 1) {
+            const int o = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+            const int kin = sp * 16 + h * 8 + k8;  // input channel of this image's conv
+            if (!mirror) {
+                if (n < cout_real && kin < cin_real) v = w[((size_t)o * cout_real + n) * cin_real + kin];
+            } else {
+                // image conv: input = gradient channels (= forward cout), output = forward cin
+                if (kin < cout_real && n < cin_real) v = w[((size_t)(26 - o) * cout_real + kin) * cin_real + n];
+            }
         }
         img[e] = f_to_bf16(v);
     }
@@ -750,7 +778,10 @@ extern "C" msz_status msz_learned_weight_image(const float *d_w, int32_t cout_re
     return cudaGetLastError() == cudaSuccess ? MSZ_OK : MSZ_ERR_CUDA;
 }
 
-extern "C" size_t msz_learned_weight_image_size(int32_t cin, int32_t cout) { return (size_t)27 * cin * cout * 2; }
+extern "C" size_t msz_learned_weight_image_size(int32_t cin, int32_t cout) {
+    if (cin % 16 || cout % 16 || cin < 16 || cout < 16 || cin > 32 || cout > 32) return 0;
+    return (size_t)img_bytes(cin, cout);
+}
 
 // Channel combinations each conv mode is built for.
 static bool conv_supported(int mode, int cin, int cout) {

@@ -113,7 +113,10 @@ def test_learned_arguments_rejected_on_host():
     assert lib.msz_learned_weight_image(a, 32, 32, 32, 48, 0, a, None) == api.ERR_INVALID_ARG
     assert lib.msz_learned_features(a, a, F(1e-3), g2, a, a, a, None) == api.ERR_INVALID_ARG
     assert lib.msz_learned_adam(a, a, a, a, 10, F(1e-3), F(0.9), F(0.999), F(1e-8), 0, None) == api.ERR_INVALID_ARG
-    assert int(lib.msz_learned_weight_image_size(32, 16)) == 27 * 32 * 16 * 2
+    # (cin / 16) slab pairs x 9 (dx, dz) strips x 2 K halves x 5 dy blocks x cout rows x 16 bytes
+    assert int(lib.msz_learned_weight_image_size(32, 16)) == 2 * 9 * 2 * 5 * 16 * 16
+    assert int(lib.msz_learned_weight_image_size(16, 32)) == 1 * 9 * 2 * 5 * 32 * 16
+    assert int(lib.msz_learned_weight_image_size(24, 32)) == 0
 
 
 def test_relaxed_arguments_rejected_on_host():
