@@ -1010,10 +1010,11 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-field batch measurement")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal comparison")
-    ap.add_argument("--large", action="store_true", help="also correct one 1024^3 field (about a minute more)")
+    ap.add_argument("--no-large", dest="large", action="store_false",
+                    help="skip the 1024^3 field (about 10 s of the run)")
     ap.add_argument("--no-relaxed", action="store_true", help="skip the relaxed-synchronization comparison")
-    ap.add_argument("--configs", action="store_true",
-                    help="also time the 2D 256^2 field and the 1024x1024x512 peak field (about a minute more)")
+    ap.add_argument("--no-configs", dest="configs", action="store_false",
+                    help="skip the 2D 256^2 field and the 1024x1024x512 peak field (about 20 s of the run)")
     ap.add_argument("--cpu-slab", type=int, default=128, help="z-planes of the CPU-baseline sample")
     ap.add_argument("--ref-slab", type=int, default=24, help="z-planes per reference-arm step")
     ap.add_argument("--shape", default=None, help="nz,ny,nx of a smaller field (profiling captures only)")
