@@ -240,9 +240,10 @@ __device__ __forceinline__ uint32_t cert4(const float *pm, const float *p0, cons
 // partial results costs about 40 ALU-pipe cycles a vertex against about 70
 // for the 7 row segments of cert4.
 //
-// The vertex itself lies in both cubes, so a strict local maximum or minimum
-// sees its own value twice and is never certified (it only costs an exact
-// examination); no other vertex's margins change.
+// The vertex itself lies in both cubes.  Where it leads the union, the
+// runner-up is taken from the two cubes' runners-up instead (cert4_diag), so
+// that a strict local maximum or minimum is not held back by its own value
+// counted twice.
 
 // The two largest and two smallest values of a multiset (NaN: no value).
 struct T2 {
@@ -327,12 +328,24 @@ __device__ __forceinline__ uint32_t cert4_diag(const float *pm, const float *p0,
     if (!carried) unit_cubes<4>(pm, p0, r - 1, lane, cc.c);
     T2 fw[5];
     unit_cubes<5>(p0, p1, r, lane, fw);
+    // the vertices' own values: both cubes hold them
+    const float4 sv = *reinterpret_cast<const float4 *>(p0 + r * PW + 4 + 4 * lane);
+    const float self[4] = {sv.x, sv.y, sv.z, sv.w};
+    const float qnan = __int_as_float(0x7fffffff);
     uint32_t cert = 0;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
         const T2 &a = fw[e + 1], &b = cc.c[e];
-        const float h1 = fmaxf(a.h1, b.h1), h2 = fmax3(fmin_nan(a.h1, b.h1), a.h2, b.h2);
-        const float l1 = fminf(a.l1, b.l1), l2 = fmin3(fmax_nan(a.l1, b.l1), a.l2, b.l2);
+        // When the leader of the union is the vertex's own value, both cubes
+        // lead with it (each holds the vertex), and the smaller leader is that
+        // same vertex counted twice, not a runner-up: the runner-up is the
+        // larger of the two cubes' runners-up (each the best of its cube
+        // after one copy of the vertex; a neighbour tied with the vertex
+        // still shows there).  Otherwise the plain union rule holds.
+        const float h1 = fmaxf(a.h1, b.h1), l1 = fminf(a.l1, b.l1);
+        const float mh = h1 == self[e] ? qnan : fmin_nan(a.h1, b.h1);
+        const float ml = l1 == self[e] ? qnan : fmax_nan(a.l1, b.l1);
+        const float h2 = fmax3(mh, a.h2, b.h2), l2 = fmin3(ml, a.l2, b.l2);
         cert |= (uint32_t)(__fsub_rd(h1, h2) > two_xi && __fsub_rd(l2, l1) > two_xi) << e;
     }
 #pragma unroll
