@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import struct
 import threading
 from dataclasses import dataclass, field
 
@@ -49,7 +50,11 @@ class Stats(ctypes.Structure):
                                               "uncertified", "local_sweeps", "tile_runs")]
 
     def as_dict(self) -> dict:
-        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+        return dict(zip(_STATS_NAMES, _STATS_LAYOUT.unpack(bytes(self))))
+
+
+_STATS_NAMES = tuple(n for n, _ in Stats._fields_)
+_STATS_LAYOUT = struct.Struct(f"={len(_STATS_NAMES)}q")
 
 
 class Field(ctypes.Structure):
@@ -239,9 +244,14 @@ def _event_handle(ev):
     return ev.cuda_event
 
 
+_NO_LOG = np.zeros(4, dtype=np.int64)
+_NO_TIMELINE = np.full(2, -1, dtype=np.int64)
+
+
 def _options(rule, max_sweeps, dense_min_items, g_init, log_capacity, tile_z=0, test_fault=0, local_cap=0):
-    log = np.zeros(max(4 * log_capacity, 4), dtype=np.int64)
-    tl = np.full(max(2 * log_capacity, 2), -1, dtype=np.int64)
+    # without a log the library writes no record: shared (empty-sliced) stand-ins
+    log = np.zeros(4 * log_capacity, dtype=np.int64) if log_capacity else _NO_LOG
+    tl = np.full(2 * log_capacity, -1, dtype=np.int64) if log_capacity else _NO_TIMELINE
     opt = Options(RULES[rule] if isinstance(rule, str) else int(rule), int(test_fault), int(max_sweeps),
                   int(dense_min_items),
                   _dptr(g_init), log.ctypes.data if log_capacity else None, int(log_capacity),
@@ -269,9 +279,9 @@ def correct(f: torch.Tensor, fhat: torch.Tensor, xi: float, *, rule="halve", max
         edit_idx = torch.empty(max(cap, 1), dtype=torch.int32, device=f.device)
     if edit_delta is None or edit_delta.numel() < cap:
         edit_delta = torch.empty(max(cap, 1), dtype=torch.float32, device=f.device)
-    need = int(lib.msz_workspace_size_rule(g, RULES[rule] if isinstance(rule, str) else int(rule)))
     if ws is None:
-        ws = workspace(need, f.device)
+        ws = workspace(int(lib.msz_workspace_size_rule(g, RULES[rule] if isinstance(rule, str) else int(rule))),
+                       f.device)
     opt, log = _options(rule, max_sweeps, dense_min_items, g_init, log_capacity, tile_z, test_fault)
     if events is not None:
         for i, ev in enumerate(events):
