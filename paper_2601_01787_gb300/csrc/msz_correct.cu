@@ -792,6 +792,7 @@ struct msz_pipeline {
         cudaEvent_t in_done, comp_done, out_done;
         bool used;
         bool stream_dev;  // the encoded stream went to the host buffer from the device (stream_out_async)
+        bool field_dev;   // g and the edit list went to the host buffers from the device (k_field_out)
         float *h_out;
         uint32_t *h_idx;
         float *h_del;
@@ -909,6 +910,27 @@ __global__ void k_readback(const uint32_t *ctrl, uint32_t *h_ctrl, const uint32_
     }
 }
 
+// The corrected field and the edit list into host memory the device
+// addresses (pipelined, field results): a grid-stride copy of g (16 bytes a
+// thread where both ends are aligned), then of the first min(count, cap)
+// entries of the edit list, the count read on the device.  A copy engine's
+// download queued on another stream would wait for the correction in the
+// engine's queue and hold up the next field's upload behind it.
+__global__ void k_field_out(float *h_g, const float *g, uint32_t n, uint32_t *h_idx, float *h_del,
+                            const uint32_t *idx, const float *del, const unsigned long long *count, uint64_t cap) {
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (uint64_t)gridDim.x * blockDim.x;
+    const bool vec = ((reinterpret_cast<uintptr_t>(h_g) | reinterpret_cast<uintptr_t>(g)) & 15u) == 0;
+    const uint64_t nv = vec ? n / 4u : 0u;
+    for (uint64_t i = tid; i < nv; i += stride)
+        reinterpret_cast<float4 *>(h_g)[i] = reinterpret_cast<const float4 *>(g)[i];
+    for (uint64_t i = 4u * nv + tid; i < n; i += stride) h_g[i] = g[i];
+    const uint64_t c = *count, m = c < cap ? c : cap;
+    for (uint64_t i = tid; i < m; i += stride) {
+        h_idx[i] = idx[i];
+        h_del[i] = del[i];
+    }
+}
+
 // The device address of host buffer p when the device can write it (pinned
 // or registered memory), else null.
 static void *device_view(void *p) {
@@ -950,6 +972,21 @@ static msz_status pipeline_submit(msz_pipeline *pl, const float *h_f, const floa
     if (sl.used && cudaStreamWaitEvent(pl->s_comp, sl.out_done, 0) != cudaSuccess) return MSZ_ERR_CUDA;
     if ((st = enqueue_correct(sl.P, dev, pl->s_comp)) != MSZ_OK) return st;
     sl.stream_dev = false;
+    sl.field_dev = false;
+    if (!pl->encoded) {
+        // g and the edit list into the caller's buffers from the device when
+        // it can address all three, else by copies (g queued below, the edit
+        // list at collect, when its length is known on the host)
+        float *ho = (float *)device_view(h_out);
+        uint32_t *hi = pl->cap ? (uint32_t *)device_view(h_idx) : nullptr;
+        float *hd = pl->cap ? (float *)device_view(h_del) : nullptr;
+        if (ho && (!pl->cap || (hi && hd))) {
+            k_field_out<<<dev.sms * 2, 256, 0, pl->s_comp>>>(ho, b.g, pl->G.n, hi, hd, b.idx, b.del,
+                                                            &sl.P.ctrl->edit_count, (uint64_t)pl->cap);
+            if (cudaGetLastError() != cudaSuccess) return MSZ_ERR_CUDA;
+            sl.field_dev = true;
+        }
+    }
     if (pl->encoded) {
         st = encode_async(b.fhat, b.g, pl->G.n, b.idx, &sl.P.ctrl->edit_count, (uint64_t)pl->cap, b.stream,
                           pl->stream_cap, b.enc_ws, dev, pl->s_comp);
@@ -972,7 +1009,8 @@ static msz_status pipeline_submit(msz_pipeline *pl, const float *h_f, const floa
     // the corrected field down (an encoded pipeline's stream comes down at
     // collect, when its length is known)
     if (cudaStreamWaitEvent(pl->s_out, sl.comp_done, 0) != cudaSuccess) return MSZ_ERR_CUDA;
-    if (!pl->encoded && cudaMemcpyAsync(h_out, b.g, bytes, cudaMemcpyDeviceToHost, pl->s_out) != cudaSuccess)
+    if (!pl->encoded && !sl.field_dev &&
+        cudaMemcpyAsync(h_out, b.g, bytes, cudaMemcpyDeviceToHost, pl->s_out) != cudaSuccess)
         return MSZ_ERR_CUDA;
     if (cudaEventRecord(sl.out_done, pl->s_out) != cudaSuccess) return MSZ_ERR_CUDA;
     sl.used = true;
@@ -1016,7 +1054,7 @@ static msz_status pipeline_results(msz_pipeline *pl, int k, int64_t *h_edit_coun
         }
     } else {
         const int64_t ne = count < pl->cap ? count : pl->cap;
-        if (ne > 0 && listed) {
+        if (ne > 0 && listed && !sl.field_dev) {
             // the edit list down, behind the field (its length is known now)
             if (cudaMemcpyAsync(sl.h_idx, b.idx, (size_t)ne * 4, cudaMemcpyDeviceToHost, pl->s_out) != cudaSuccess ||
                 cudaMemcpyAsync(sl.h_del, b.del, (size_t)ne * 4, cudaMemcpyDeviceToHost, pl->s_out) != cudaSuccess ||
