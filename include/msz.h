@@ -115,7 +115,9 @@ typedef struct {
     int64_t *h_timeline;      /* NULL, or 2*log_capacity int64 (needs h_sweep_log): device
                                  time in ns from the start of the correction (sweep 0's pass)
                                  to the end of sweep k's detection and of its edit phase
-                                 (-1: none) */
+                                 (-1: none).  The batch entry points write one timeline for
+                                 the whole batch here (filled by msz_batch_collect, or by
+                                 msz_correct_batch; they need no h_sweep_log in this struct) */
     int32_t tile_z;           /* z-planes per tile of the code pass (3D); at most 1024; 0: the
                                  deepest of 24, 16, 8 that gives every block of the persistent
                                  grid two tiles (msz_correct; the batch and relaxed entry points

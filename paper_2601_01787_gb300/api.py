@@ -518,6 +518,9 @@ def verify(f: torch.Tensor, g: torch.Tensor) -> dict:
 class BatchResult:
     status: int
     fields: list  # CorrectResult per field
+    # device ns from the code pass's start to the end of sweep k's detection
+    # (column 0) and edit phase (column 1), -1 for none; empty unless asked for
+    timeline: np.ndarray = field(default_factory=lambda: np.zeros((0, 2), np.int64))
 
 
 def _batch_fields(fs, fhats, xis, edit_capacities, outs, tile_z):
@@ -546,7 +549,7 @@ def _batch_workspace(lib, arr, max_sweeps, ws, device):
     return workspace(need, device) if ws is None else ws
 
 
-def _batch_results(arr, keep, log, log_capacity, status) -> "BatchResult":
+def _batch_results(arr, keep, log, log_capacity, status, timeline=None) -> "BatchResult":
     results = []
     for k in range(len(arr)):
         out, idx, dl, cap = keep[k]
@@ -557,7 +560,8 @@ def _batch_results(arr, keep, log, log_capacity, status) -> "BatchResult":
         lg = log[4 * k * log_capacity:4 * (k * log_capacity + nlog)].reshape(-1, 4).copy() if log_capacity else \
             np.zeros((0, 4), np.int64)
         results.append(CorrectResult(int(fk.status), out, idx[:m], dl[:m], int(fk.edit_count), stats, lg))
-    return BatchResult(int(status), results)
+    tl = timeline.reshape(-1, 2).copy() if timeline is not None else np.zeros((0, 2), np.int64)
+    return BatchResult(int(status), results, tl)
 
 
 class BatchPlan:
@@ -566,11 +570,12 @@ class BatchPlan:
     per-field results.  The plan keeps every buffer it points to alive."""
 
     def __init__(self, fs, fhats, xis, *, rule="halve", max_sweeps: int = 0, dense_min_items: int = 0,
-                 edit_capacities=None, outs=None, ws: torch.Tensor | None = None, stream=None, tile_z=None):
+                 edit_capacities=None, outs=None, ws: torch.Tensor | None = None, stream=None, tile_z=None,
+                 timeline_capacity: int = 0):
         lib = load()
         arr, keep = _batch_fields(fs, fhats, xis, edit_capacities, outs, tile_z)
         ws = _batch_workspace(lib, arr, max_sweeps, ws, fs[0].device)
-        opt, _ = _options(rule, max_sweeps, dense_min_items, None, 0)
+        opt, _ = _options(rule, max_sweeps, dense_min_items, None, int(timeline_capacity))
         handle = ctypes.c_void_p()
         st = lib.msz_batch_plan_create(len(arr), arr, ctypes.byref(opt), _dptr(ws), ws.numel(), _stream(stream),
                                        ctypes.byref(handle))
@@ -593,7 +598,8 @@ class BatchPlan:
         log = np.zeros(max(4 * self.n * log_capacity, 4), dtype=np.int64)
         st = self._lib.msz_batch_collect(self._h, self.arr, log.ctypes.data if log_capacity else None,
                                          int(log_capacity), _stream(stream))
-        return _batch_results(self.arr, self._keep[2], log, log_capacity, st)
+        tl = self._keep[4]._keep[1] if self._keep[4].log_capacity else None
+        return _batch_results(self.arr, self._keep[2], log, log_capacity, st, tl)
 
     def graph(self, stream=None) -> "torch.cuda.CUDAGraph":
         """Capture one launch in a CUDA graph; replay() then reruns the whole
@@ -620,16 +626,18 @@ class BatchPlan:
 
 def correct_batch(fs, fhats, xis, *, rule="halve", max_sweeps: int = 0, dense_min_items: int = 0,
                   edit_capacities=None, log_capacity: int = 0, outs=None, ws: torch.Tensor | None = None,
-                  stream=None, tile_z=None) -> BatchResult:
-    """msz_correct_batch: many 3D fields (CUDA tensors) in one persistent launch."""
+                  stream=None, tile_z=None, timeline_capacity: int = 0) -> BatchResult:
+    """msz_correct_batch: many 3D fields (CUDA tensors) in one persistent
+    launch.  timeline_capacity > 0: the result's timeline holds the device
+    times of the first that many sweeps."""
     lib = load()
     arr, keep = _batch_fields(fs, fhats, xis, edit_capacities, outs, tile_z)
     ws = _batch_workspace(lib, arr, max_sweeps, ws, fs[0].device)
-    opt, _ = _options(rule, max_sweeps, dense_min_items, None, 0)
+    opt, _ = _options(rule, max_sweeps, dense_min_items, None, int(timeline_capacity))
     log = np.zeros(max(4 * len(arr) * log_capacity, 4), dtype=np.int64)
     st = lib.msz_correct_batch(len(arr), arr, ctypes.byref(opt), log.ctypes.data if log_capacity else None,
                                log_capacity, _dptr(ws), ws.numel(), _stream(stream))
-    return _batch_results(arr, keep, log, log_capacity, st)
+    return _batch_results(arr, keep, log, log_capacity, st, opt._keep[1] if timeline_capacity else None)
 
 
 # ------------------------------------------------------------ edit encoding

@@ -36,6 +36,12 @@ namespace {
 constexpr int kThreads = tile::THREADS;
 constexpr int kMinBlocksB = 3;
 constexpr uint32_t kDenseFactorB = 6;
+constexpr int kListRoundsB = 4;  // edit-list rounds whose loads are grouped
+static_assert(kListRoundsB == 4, "the edit list's round group is written out for four rounds");
+// a sweep keeps chunk flags when its worklist is bounded by the larger of
+// this and 1/256 of the batch's vertices (the walks they spare read every
+// bitmap word of every field)
+constexpr unsigned long long kSparseWorklistB = 1ull << 19;
 
 struct FieldDev {
     FieldView F;
@@ -49,8 +55,17 @@ struct FieldDev {
 struct BatchRec {
     uint32_t worklist, distorted, targets, changed;
     uint32_t dense;  // the detection of this sweep scanned every uncertified vertex
+    // field 0's record only: [0] the tile counter of a whole-field detection;
+    // [1] / [2] device time (ns from the code pass's start, 0: none) at the
+    // end of this sweep's detection / edit phase
     uint32_t pad[3];
 };
+
+// Nanoseconds since t0 for a timeline record (0 is kept for "none").
+__device__ __forceinline__ uint32_t stamp_since(uint64_t t0) {
+    const uint64_t d = global_ns() - t0;
+    return d >= 0xffffffffull ? 0xffffffffu : d == 0 ? 1u : (uint32_t)d;
+}
 
 struct FieldRes {
     unsigned long long edit_count;
@@ -65,6 +80,8 @@ struct BatchProblem {
     GridDev all;  // the shared index space (only n, words used)
     Ctrl *ctrl;
     BatchRec *log;  // [sweep][field]
+    uint32_t *stb, *sdm[2];          // chunk flags of tb, dm[0], dm[1] (kept in sparse sweeps)
+    unsigned long long sparse_max;   // worklist bound of a sweep that keeps them
     FieldRes *res;
     uint32_t *bsum;
     uint32_t max_sweeps;
@@ -74,7 +91,7 @@ struct BatchProblem {
 };
 
 struct BatchLayout {
-    size_t ctrl, fields, log, res, bsum, tb, d0, d1, eb, ub, codes, bfield, total, zero_bytes;
+    size_t ctrl, fields, log, res, bsum, tb, d0, d1, eb, ub, stb, sd0, sd1, codes, bfield, total, zero_bytes;
 };
 
 BatchLayout batch_layout(uint32_t nfields, uint64_t ntot, uint32_t max_sweeps) {
@@ -90,6 +107,9 @@ BatchLayout batch_layout(uint32_t nfields, uint64_t ntot, uint32_t max_sweeps) {
     L.d1 = o;     o = align_up(o + words * 4);
     L.eb = o;     o = align_up(o + words * 4);
     L.ub = o;     o = align_up(o + words * 4);
+    L.stb = o;    o = align_up(o + ntot / 1024 * 4);
+    L.sd0 = o;    o = align_up(o + ntot / 1024 * 4);
+    L.sd1 = o;    o = align_up(o + ntot / 1024 * 4);
     L.zero_bytes = o;
     L.fields = o; o = align_up(o + nfields * sizeof(FieldDev));
     L.codes = o;  o = align_up(o + ntot);
@@ -130,13 +150,61 @@ __device__ __forceinline__ void flush_counts(uint32_t (*cnt)[4], uint32_t nf, Ba
     __syncthreads();
 }
 
+// A field's view of shared-space chunk flags (null stays null): field bases
+// are 1024-aligned, so a field-local vertex v has chunk (base >> 10) + (v >> 10).
+__device__ __forceinline__ uint32_t *field_flags(uint32_t *flags, uint32_t base) {
+    return flags ? flags + (base >> 10) : nullptr;
+}
+
+// walk_words_pairs over the chunks (32 words) whose flags are set, clearing
+// the flags: the bits of word w are finish(w, fetch(w)), the next flagged
+// chunk's words loaded before the current one is queued; chunk c belongs to
+// warp c mod (warps of the grid), a warp reading 32 of its flags at once.
+// rq: the warp's kRoundCap entries of shared memory.
+template <class FE, class FI, class F>
+__device__ __forceinline__ void walk_flagged_words(uint32_t *flags, const GridDev &G, FE &&fetch, FI &&finish,
+                                                   uint32_t *rq, F &&fn) {
+    const uint32_t lane = lane_id();
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t chunks = (G.words + 31u) / 32u;
+    RoundQueue<true> Q{rq};
+    for (uint32_t c0 = gw; c0 < chunks; c0 += 32u * nw) {
+        const uint32_t mine = c0 + lane * nw;  // this lane's chunk of the round
+        const bool set = mine < chunks && flags[mine] != 0u;
+        if (set) flags[mine] = 0u;
+        uint32_t marks = __ballot_sync(kFull, set);
+        if (!marks) continue;
+        uint32_t c = c0 + (uint32_t)(__ffs(marks) - 1) * nw;
+        marks &= marks - 1u;
+        uint32_t nxt = c * 32u + lane < G.words ? fetch(c * 32u + lane) : 0u;
+        for (;;) {
+            const uint32_t base = c * 32u;
+            const uint32_t wi = base + lane;
+            const uint32_t raw = nxt;
+            const bool more = marks != 0u;
+            if (more) {
+                c = c0 + (uint32_t)(__ffs(marks) - 1) * nw;
+                marks &= marks - 1u;
+                nxt = c * 32u + lane < G.words ? fetch(c * 32u + lane) : 0u;
+            }
+            const uint32_t bits = wi < G.words ? finish(wi, raw) : 0u;
+            Q.push_chunk(base, bits, fn);
+            if (!more) break;
+        }
+    }
+    Q.flush(fn);
+}
+
 // Detection of two vertices per lane of the shared index space (each may lie
 // in a different field): the neighbour loads of both are issued before either
 // code is formed; distorted vertices are counted per field in s_cnt[f][1].
+// sums: the marks also set the chunk flags of the targets and of the next
+// worklist.
 template <class Alive>
 __device__ __forceinline__ void detect_pair(const BatchProblem &P, const uint32_t *s_base, uint32_t nf,
-                                            uint32_t (*s_cnt)[4], uint32_t next_parity, Alive &&alive, bool h1,
-                                            uint32_t v1, bool h2, uint32_t v2) {
+                                            uint32_t (*s_cnt)[4], uint32_t next_parity, bool sums, Alive &&alive,
+                                            bool h1, uint32_t v1, bool h2, uint32_t v2) {
     const uint32_t f1 = h1 ? field_of(P.bfield, v1) : 0u, f2 = h2 ? field_of(P.bfield, v2) : 0u;
     const bool l1 = h1 && alive(f1), l2 = h2 && alive(f2);
     const FieldView &F1 = P.fields[f1].F;
@@ -147,9 +215,10 @@ __device__ __forceinline__ void detect_pair(const BatchProblem &P, const uint32_
     gather_closed<3>(F2.g, F2.G, l2, i2, b);
     const uint32_t cf1 = l1 ? __ldg(&F1.codes_f[i1]) : 0u;
     const uint32_t cf2 = l2 ? __ldg(&F2.codes_f[i2]) : 0u;
-    Emitter E1{F1.dm[next_parity], 0};
+    uint32_t *const dsum = sums ? P.sdm[next_parity] : nullptr, *const tsum = sums ? P.stb : nullptr;
+    Emitter E1{F1.dm[next_parity], 0, field_flags(dsum, s_base[f1]), field_flags(tsum, s_base[f1])};
     report(F1, E1, l1, i1, cf1, code_of_closed<3>(a));
-    Emitter E2{F2.dm[next_parity], 0};
+    Emitter E2{F2.dm[next_parity], 0, field_flags(dsum, s_base[f2]), field_flags(tsum, s_base[f2])};
     report(F2, E2, l2, i2, cf2, code_of_closed<3>(b));
     // distorted counts per field, aggregated over the warp's lanes of one field
     const uint32_t lane = lane_id();
@@ -207,7 +276,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
     __shared__ uint32_t s_cnt[MSZ_BATCH_MAX_FIELDS][4];
     __shared__ uint32_t s_alive[(MSZ_BATCH_MAX_FIELDS + 31) / 32];
     __shared__ uint32_t s_next;
-    __shared__ unsigned long long s_sum;
+    __shared__ unsigned long long s_sum, s_chg;
     __shared__ uint32_t sm[40];
     __shared__ uint32_t s_rq[kThreads / 32][kRoundCap];  // each warp's round queue
     uint32_t *rq = s_rq[threadIdx.x >> 5];
@@ -224,11 +293,17 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
     auto alive = [&](uint32_t k) { return (s_alive[k >> 5] >> (k & 31u)) & 1u; };
     bool ok = ld_relaxed(&C->error) == 0;  // every block reads k_batch_codes' verdict
     if (leader) C->t_codes = global_ns();
+    // Chunk flags are kept only in sparse sweeps.  sum_k: the phases of
+    // sweep k keep them -- decided before sweep k's detection from a bound on
+    // its worklist (15 x changed + distorted of sweep k-1, over all fields),
+    // so that every mark into sweep k's targets and into the next worklist
+    // sets its chunk's flag whenever a walk relies on it.  Sweep 0 keeps none.
+    bool sum_k = false;
     uint32_t k = 0;
     while (ok) {
         BatchRec *rec = P.log + (size_t)k * nf;
         // every block derives the same verdicts from the same records
-        if (threadIdx.x == 0) s_sum = 0;
+        if (threadIdx.x == 0) s_sum = s_chg = 0;
         __syncthreads();
         unsigned long long m_all = 0;
         for (uint32_t f = threadIdx.x; f < nf; f += blockDim.x) {
@@ -247,12 +322,14 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
         }
         if (k >= P.max_sweeps) {
             uint32_t nt = 0;
-            walk_bits<true>(P.tb, nullptr, P.all, nt, [&](bool has, uint32_t t) {
+            auto count = [&](bool has, uint32_t t) {
                 if (has) {
                     const uint32_t f = field_of(P.bfield, t);
                     if (alive(f)) atomicAdd(&s_cnt[f][2], 1u);
                 }
-            });
+            };
+            if (!sum_k) walk_bits<true>(P.tb, nullptr, P.all, nt, count);
+            else walk_flagged<true, false>(P.tb, P.stb, nullptr, P.all, nt, rq, count);
             flush_counts(s_cnt, nf, rec);
             if (leader) { C->status = MSZ_ERR_MAX_SWEEPS; C->sweeps = k; }
             ok = grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
@@ -263,13 +340,15 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
         // ---- edit phase of sweep k
         {
             uint32_t targets = 0;
-            walk_bits<true>(P.tb, nullptr, P.all, targets, [&](bool has, uint32_t t) {
+            uint32_t *const dsum = sum_k ? P.sdm[(k + 1) & 1] : nullptr;
+            auto edit = [&](bool has, uint32_t t) {
                 const uint32_t f = has ? field_of(P.bfield, t) : 0u;
                 const bool live = has && alive(f);
                 bool changed = false;
                 if (live) {
                     const FieldView &F = P.fields[f].F;
-                    changed = apply_target<3>(F, t - s_base[f], dense_next, F.dm[(k + 1) & 1]);
+                    changed = apply_target<3>(F, t - s_base[f], dense_next, F.dm[(k + 1) & 1],
+                                              field_flags(dsum, s_base[f]));
                 }
                 // counts per field, aggregated over the warp's lanes of one field
                 const uint32_t peers = __match_any_sync(kFull, live ? f : 0xffffffffu);
@@ -278,27 +357,38 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
                     atomicAdd(&s_cnt[f][2], (uint32_t)__popc(peers));
                     if (nch) atomicAdd(&s_cnt[f][3], nch);
                 }
-            }, rq);
+            };
+            if (!sum_k) walk_bits<true>(P.tb, nullptr, P.all, targets, edit, rq);
+            else walk_flagged<true, false>(P.tb, P.stb, nullptr, P.all, targets, rq, edit);
             (void)targets;
             flush_counts(s_cnt, nf, rec);
         }
         ok = grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
         if (!ok) break;
+        if (leader) rec[0].pad[2] = stamp_since(C->t_start);
         // fields whose targets were all at their floor are stuck
         uint32_t any_changed = 0;
+        unsigned long long chg = 0;
         for (uint32_t f = threadIdx.x; f < nf; f += blockDim.x) {
             if (!alive(f)) continue;
-            if (ld_relaxed(&rec[f].changed) == 0) atomicAnd(&s_alive[f >> 5], ~(1u << (f & 31u)));
+            const uint32_t c = ld_relaxed(&rec[f].changed);
+            if (c == 0) atomicAnd(&s_alive[f >> 5], ~(1u << (f & 31u)));
             else any_changed = 1;
+            chg += c;
         }
+        if (chg) atomicAdd(&s_chg, chg);
         if (!__syncthreads_or(any_changed)) {
             if (leader) { C->status = MSZ_STUCK; C->sweeps = k + 1; }
             break;
         }
-        // ---- detection phase of sweep k + 1
+        const bool sum_k1 = 15ull * s_chg + m_tot <= P.sparse_max;
+        // ---- detection phase of sweep k + 1: its marks keep the flags of its
+        // targets and of the next worklist when sum_k1; the current worklist
+        // has them when sweep k kept them (sum_k)
         const uint32_t k1 = k + 1;
         BatchRec *rec1 = P.log + (size_t)k1 * nf;
         uint32_t *dcur = P.dm[k1 & 1];
+        uint32_t *const dsum1 = sum_k1 ? P.sdm[(k1 + 1) & 1] : nullptr, *const tsum1 = sum_k1 ? P.stb : nullptr;
         {
             const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
             for (uint32_t f = gtid; f < nf; f += stride)
@@ -311,6 +401,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
                 // tile by tile over the shared tile queue (g staged in shared
                 // memory); the worklist bitmap is cleared for the next sweep
                 for (uint32_t w = gtid; w < P.all.words; w += stride) dcur[w] = 0u;
+                if (sum_k)
+                    for (uint32_t c = gtid; c < P.all.words / 32u; c += stride) P.sdm[k1 & 1][c] = 0u;
                 uint32_t *counter = &rec1[0].pad[0];
                 for (;;) {
                     __syncthreads();
@@ -327,50 +419,79 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
                     const int zb = (int)(tzi * tg.bz);
                     uint32_t dist = 0;
                     detect_tile_cp(F, (int)(txi * tile::BX), (int)(tyi * tile::BY), zb,
-                                   min(zb + (int)tg.bz, (int)F.G.nz), smem, F.dm[(k1 + 1) & 1], dist);
+                                   min(zb + (int)tg.bz, (int)F.G.nz), smem, F.dm[(k1 + 1) & 1], dist,
+                                   field_flags(dsum1, s_base[f]), field_flags(tsum1, s_base[f]));
                     warp_add(dist, &s_cnt[f][1]);
                 }
-            } else
-            // per word: the uncertified vertices of a live field's worklist;
-            // done fields none.  The worklist is cleared as it is read (a
-            // word never straddles two fields: bases are 1024-aligned).
-            walk_words_pairs(
-                P.all, [&](uint32_t wi) -> uint32_t { return dcur[wi]; },
-                [&](uint32_t wi, uint32_t wl) -> uint32_t {
+            } else {
+                // per word: the uncertified vertices of a live field's
+                // worklist; done fields none.  The worklist is cleared as it
+                // is read (a word never straddles two fields: bases are
+                // 1024-aligned).
+                auto fetch = [&](uint32_t wi) -> uint32_t { return dcur[wi]; };
+                auto finish = [&](uint32_t wi, uint32_t wl) -> uint32_t {
                     const uint32_t f = field_of(P.bfield, wi * 32u);
                     if (wl) dcur[wi] = 0u;
                     if (!alive(f)) return 0u;
                     if (!wl) return 0u;
                     atomicAdd(&s_cnt[f][0], (uint32_t)__popc(wl));
                     return wl & P.ub[wi];
-                },
-                [&](bool h1, uint32_t v1, bool h2, uint32_t v2) {
-                    detect_pair(P, s_base, nf, s_cnt, (k1 + 1) & 1, alive, h1, v1, h2, v2);
-                },
-                rq);
+                };
+                auto detect = [&](bool h1, uint32_t v1, bool h2, uint32_t v2) {
+                    detect_pair(P, s_base, nf, s_cnt, (k1 + 1) & 1, sum_k1, alive, h1, v1, h2, v2);
+                };
+                if (sum_k) walk_flagged_words(P.sdm[k1 & 1], P.all, fetch, finish, rq, detect);
+                else walk_words_pairs(P.all, fetch, finish, detect, rq);
+            }
         }
         flush_counts(s_cnt, nf, rec1);
         ok = grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
+        if (leader) rec1[0].pad[1] = stamp_since(C->t_start);
         k = k1;
+        sum_k = sum_k1;
     }
     if (!ok) return;
 
-    // ---- edit lists, split per field, ascending index
+    // ---- edit lists, split per field, ascending index.  Each warp owns a
+    // contiguous range of bitmap words; a block scan of the warps' counts and
+    // a grid-wide prefix over the blocks give each warp its first position in
+    // the shared order, and a field's list starts at the edits of the fields
+    // before it (fields lie in the shared space in order).  The warp writes
+    // its range 32 words a round, a round's edits going to the lanes in index
+    // order (ChunkBits) so that the stores coalesce.
     const uint32_t W = P.all.words;
-    const uint32_t per = (W + gridDim.x - 1) / gridDim.x;
-    const uint32_t w0 = min(blockIdx.x * per, W), w1 = min(w0 + per, W);
+    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    const uint32_t nwarps = gridDim.x * wpb;
+    const uint32_t per = (W + nwarps - 1) / nwarps;
+    const uint32_t gw = blockIdx.x * wpb + warp;
+    const uint32_t w0 = min(gw * per, W), w1 = min(w0 + per, W);
     uint32_t cnt = 0;
-    for (uint32_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) {
-        const uint32_t c = __popc(P.eb[w]), u = __popc(P.ub[w]);
-        cnt += c;
-        if (c | u) {
+    {
+        // per-field counts, kept in registers while a lane's words stay in
+        // one field
+        uint32_t cur = 0xffffffffu, ac = 0, au = 0;
+#pragma unroll 4
+        for (uint32_t w = w0 + lane; w < w1; w += 32) {
+            const uint32_t c = __popc(P.eb[w]), u = __popc(P.ub[w]);
+            cnt += c;
+            if (!(c | u)) continue;
             const uint32_t f = field_of(P.bfield, w * 32u);
-            if (c) atomicAdd(&s_cnt[f][0], c);
-            if (u) atomicAdd(&s_cnt[f][1], u);
+            if (f != cur) {
+                if (ac) atomicAdd(&s_cnt[cur][0], ac);
+                if (au) atomicAdd(&s_cnt[cur][1], au);
+                cur = f;
+                ac = au = 0;
+            }
+            ac += c;
+            au += u;
         }
+        if (ac) atomicAdd(&s_cnt[cur][0], ac);
+        if (au) atomicAdd(&s_cnt[cur][1], au);
     }
     uint32_t tot;
-    block_exclusive_scan(cnt, sm, tot);
+    const uint32_t wcnt = __reduce_add_sync(kFull, cnt);
+    const uint32_t wpre = block_exclusive_scan(lane == 0 ? wcnt : 0u, sm, tot);
+    const uint32_t warp_pre = __shfl_sync(kFull, wpre, 0);  // this warp's offset in its block
     if (threadIdx.x == 0) P.bsum[blockIdx.x] = tot;
     __syncthreads();
     for (uint32_t f = threadIdx.x; f < nf; f += blockDim.x) {
@@ -386,39 +507,77 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
     if (!grid_barrier(&C->bar_count, &C->bar_gen, &C->error)) return;
     uint32_t pre = 0;
     for (uint32_t b = threadIdx.x; b < blockIdx.x; b += blockDim.x) pre += ld_relaxed(&P.bsum[b]);
-    uint32_t prefix;
-    block_exclusive_scan(pre, sm, prefix);
-    // s_tile reused: exclusive prefix of the per-field edit counts
-    if (threadIdx.x == 0) {
-        unsigned long long acc = 0;
-        for (uint32_t f = 0; f < nf; ++f) {
-            s_tile[f] = (uint32_t)acc;
-            acc += ((volatile FieldRes *)P.res)[f].edit_count;
-        }
+    uint32_t bpre;
+    block_exclusive_scan(pre, sm, bpre);
+    // s_tile reused: exclusive prefix of the per-field edit counts (one a
+    // thread: nf <= blockDim.x; every count and their sum fit 32 bits)
+    static_assert(MSZ_BATCH_MAX_FIELDS <= kThreads, "one field a thread in the edit-count scan");
+    {
+        const uint32_t ec = threadIdx.x < nf ? (uint32_t)((volatile FieldRes *)P.res)[threadIdx.x].edit_count : 0u;
+        uint32_t all_edits;
+        const uint32_t ex = block_exclusive_scan(ec, sm, all_edits);
+        if (threadIdx.x < nf) s_tile[threadIdx.x] = ex;
     }
     __syncthreads();
-    for (uint32_t r = w0; r < w1; r += blockDim.x) {
-        const uint32_t w = r + threadIdx.x;
-        const uint32_t word = w < w1 ? P.eb[w] : 0u;
-        uint32_t rt;
-        const uint32_t ex = block_exclusive_scan((uint32_t)__popc(word), sm, rt);
-        if (word) {
-            const uint32_t f = field_of(P.bfield, w * 32u);
-            const FieldDev &D = P.fields[f];
-            unsigned long long pos = (unsigned long long)(prefix + ex) - s_tile[f];
-            uint32_t bits = word;
-            while (bits) {
-                const uint32_t b = (uint32_t)(__ffs(bits) - 1);
-                bits &= bits - 1;
-                const uint32_t i = w * 32u + b - s_base[f];
-                if (pos < D.edit_cap) {
-                    D.edit_idx[pos] = i;
-                    D.edit_delta[pos] = __fsub_rn(D.F.g[i], __ldg(&D.F.fhat[i]));
-                }
-                ++pos;
-            }
+    uint32_t prefix = bpre + warp_pre;  // shared-order position of the warp's first edit
+    // edit j of a round (lane-picked vertex v, shared index): its field's
+    // list position and value
+    auto emit = [&](bool h, uint32_t v, uint32_t pos, float gv, float fv, uint32_t f) {
+        if (!h) return;
+        const FieldDev &D = P.fields[f];
+        const unsigned long long q = (unsigned long long)(pos - s_tile[f]);
+        if (q < D.edit_cap) {
+            D.edit_idx[q] = v - s_base[f];
+            D.edit_delta[q] = __fsub_rn(gv, fv);
         }
-        prefix += rt;
+    };
+    auto gather = [&](bool h, uint32_t v, uint32_t &f, float &gv, float &fv) {
+        f = h ? field_of(P.bfield, v) : 0u;
+        const FieldView &F = P.fields[f].F;
+        const uint32_t i = h ? v - s_base[f] : 0u;
+        gv = h ? F.g[i] : 0.f;
+        fv = h ? __ldg(&F.fhat[i]) : 0.f;
+    };
+    // kListRoundsB rounds at a time: their words loaded together, then the
+    // first 32 edits of each gathered before any is stored, and the next
+    // group's words loaded before this group's stores
+    constexpr int R = kListRoundsB;
+    auto word_at = [&](uint32_t w) -> uint32_t { return w < w1 ? P.eb[w] : 0u; };
+    uint32_t wd[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) wd[q] = word_at(w0 + 32u * q + lane);
+    for (uint32_t r = w0; r < w1; r += 32u * R) {
+        ChunkBits cb[R] = {ChunkBits(r, wd[0]), ChunkBits(r + 32u, wd[1]), ChunkBits(r + 64u, wd[2]),
+                           ChunkBits(r + 96u, wd[3])};
+        bool h[R];
+        uint32_t v[R], fq[R];
+        float gv[R], fv[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            cb[q].pick(lane, h[q], v[q]);
+            gather(h[q], v[q], fq[q], gv[q], fv[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) wd[q] = word_at(r + 32u * (R + q) + lane);
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            emit(h[q], v[q], prefix + lane, gv[q], fv[q], fq[q]);
+            // a chunk with more than 32 edits: the rest four rounds at a
+            // time, gathers first
+            for (uint32_t j0 = 32u; j0 < cb[q].total; j0 += 32u * R) {
+                bool hj[R];
+                uint32_t vj[R], fj[R];
+                float gj[R], sj[R];
+#pragma unroll
+                for (int u = 0; u < R; ++u) {
+                    cb[q].pick(j0 + 32u * u + lane, hj[u], vj[u]);
+                    gather(hj[u], vj[u], fj[u], gj[u], sj[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < R; ++u) emit(hj[u], vj[u], prefix + j0 + 32u * u + lane, gj[u], sj[u], fj[u]);
+            }
+            prefix += cb[q].total;
+        }
     }
     if (!grid_barrier(&C->bar_count, &C->bar_gen, &C->error)) return;
     if (leader) C->t_end = global_ns();
@@ -509,6 +668,8 @@ struct BatchPlanImpl {
     BatchLayout L;
     BatchProblem P;
     std::vector<GridDev> grids;
+    int64_t *h_timeline;  // the options' timeline (2 * timeline_cap int64) or NULL
+    int64_t timeline_cap;
 };
 
 }  // namespace
@@ -603,6 +764,10 @@ extern "C" msz_status msz_batch_plan_create(int32_t n, const msz_field *fields, 
     P.dm[1] = (uint32_t *)(ws + L.d1);
     P.eb = (uint32_t *)(ws + L.eb);
     P.ub = (uint32_t *)(ws + L.ub);
+    P.stb = (uint32_t *)(ws + L.stb);
+    P.sdm[0] = (uint32_t *)(ws + L.sd0);
+    P.sdm[1] = (uint32_t *)(ws + L.sd1);
+    P.sparse_max = ntot / 256 > kSparseWorklistB ? ntot / 256 : kSparseWorklistB;
     P.bfield = (const uint8_t *)(ws + L.bfield);
     std::vector<uint8_t> bfield(ntot / 1024, 0);
     for (int32_t k = 0; k < n; ++k)
@@ -630,6 +795,8 @@ extern "C" msz_status msz_batch_plan_create(int32_t n, const msz_field *fields, 
     p->impl.L = L;
     p->impl.P = P;
     p->impl.grids = std::move(grids);
+    p->impl.h_timeline = o.log_capacity > 0 ? o.h_timeline : nullptr;
+    p->impl.timeline_cap = o.log_capacity;
     *out_plan = p;
     return MSZ_OK;
 }
@@ -684,6 +851,19 @@ extern "C" msz_status msz_batch_collect(const msz_batch_plan *plan, msz_field *f
         return MSZ_ERR_CUDA;
     const int64_t kernel_ns = hc.t_end > hc.t_start ? (int64_t)(hc.t_end - hc.t_start) : 0;
     const int64_t codes_ns = hc.t_codes > hc.t_start ? (int64_t)(hc.t_codes - hc.t_start) : 0;
+    if (B.h_timeline) {
+        // sweep 0's detection ends with the code pass; later stamps are field 0's records
+        for (int64_t q = 0; q < B.timeline_cap; ++q) {
+            int64_t td = -1, te = -1;
+            if (q <= (int64_t)S) {
+                const BatchRec &r = log[(size_t)q * n];
+                td = q == 0 ? (codes_ns ? codes_ns : -1) : r.pad[1] ? (int64_t)r.pad[1] : -1;
+                te = r.pad[2] ? (int64_t)r.pad[2] : -1;
+            }
+            B.h_timeline[2 * q] = td;
+            B.h_timeline[2 * q + 1] = te;
+        }
+    }
     for (int32_t k = 0; k < n; ++k) {
         msz_field &F = fields[k];
         msz_stats &stt = F.stats;

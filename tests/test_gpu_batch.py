@@ -146,6 +146,30 @@ def test_batch_plan_launch_matches_one_call(api):
             {k: v for k, v in b.stats.items() if not k.endswith("_ns")}
 
 
+def test_batch_timeline(api):
+    """The batch's timeline: one row per sweep the launch reached (detection
+    end, edit end), non-decreasing, inside the kernels' time; -1 beyond."""
+    fields = _small_batch()
+    fs = [torch.from_numpy(fl.f).cuda() for fl in fields]
+    fhs = [torch.from_numpy(fl.fhat).cuda() for fl in fields]
+    cap = 64
+    res = api.correct_batch(fs, fhs, [fl.xi for fl in fields], timeline_capacity=cap)
+    assert res.status == api.OK and res.timeline.shape == (cap, 2)
+    S = max(r.stats["sweeps"] for r in res.fields)
+    assert 0 < S < cap - 1
+    tl = res.timeline
+    # sweeps 0 .. S-1 detect and edit; sweep S detects only (nothing left)
+    seq = [t for q in range(S) for t in tl[q]] + [tl[S, 0]]
+    assert all(t > 0 for t in seq) and seq == sorted(seq)
+    assert tl[S, 1] == -1 and (tl[S + 1:] == -1).all()
+    assert seq[-1] <= res.fields[0].stats["kernel_ns"]
+    plan = api.BatchPlan(fs, fhs, [fl.xi for fl in fields], timeline_capacity=cap)
+    plan.launch()
+    two = plan.collect()
+    assert two.status == api.OK and ((two.timeline > 0) == (tl > 0)).all()
+    assert api.correct_batch(fs, fhs, [fl.xi for fl in fields]).timeline.shape == (0, 2)
+
+
 def test_batch_at_the_field_limit(api):
     """MSZ_BATCH_MAX_FIELDS tiny uneven fields in one launch, each equal to its
     own correction; one more field is rejected."""
