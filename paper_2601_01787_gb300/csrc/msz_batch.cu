@@ -81,6 +81,7 @@ struct BatchProblem {
     Ctrl *ctrl;
     BatchRec *log;  // [sweep][field]
     uint32_t *stb, *sdm[2];          // chunk flags of tb, dm[0], dm[1] (kept in sparse sweeps)
+    uint32_t *cpre;                  // per chunk: its first edit's position in the shared order
     unsigned long long sparse_max;   // worklist bound of a sweep that keeps them
     FieldRes *res;
     uint32_t *bsum;
@@ -91,7 +92,7 @@ struct BatchProblem {
 };
 
 struct BatchLayout {
-    size_t ctrl, fields, log, res, bsum, tb, d0, d1, eb, ub, stb, sd0, sd1, codes, bfield, total, zero_bytes;
+    size_t ctrl, fields, log, res, bsum, tb, d0, d1, eb, ub, stb, sd0, sd1, codes, bfield, cpre, total, zero_bytes;
 };
 
 BatchLayout batch_layout(uint32_t nfields, uint64_t ntot, uint32_t max_sweeps) {
@@ -114,6 +115,7 @@ BatchLayout batch_layout(uint32_t nfields, uint64_t ntot, uint32_t max_sweeps) {
     L.fields = o; o = align_up(o + nfields * sizeof(FieldDev));
     L.codes = o;  o = align_up(o + ntot);
     L.bfield = o; o = align_up(o + ntot / 1024);
+    L.cpre = o;   o = align_up(o + ntot / 1024 * 4);
     L.total = o;
     return L;
 }
@@ -452,45 +454,53 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
     }
     if (!ok) return;
 
-    // ---- edit lists, split per field, ascending index.  Each warp owns a
-    // contiguous range of bitmap words; a block scan of the warps' counts and
-    // a grid-wide prefix over the blocks give each warp its first position in
-    // the shared order, and a field's list starts at the edits of the fields
-    // before it (fields lie in the shared space in order).  The warp writes
-    // its range 32 words a round, a round's edits going to the lanes in index
-    // order (ChunkBits) so that the stores coalesce.
-    const uint32_t W = P.all.words;
+    // ---- edit lists, split per field, ascending index, chunk (32 words,
+    // 1024 vertices, one field) by chunk.  (1) Each warp counts the edits of
+    // a contiguous range of chunks, recording each chunk's count; a block
+    // scan of the warps' totals and a grid-wide prefix over the blocks turn
+    // the counts into each chunk's first position in the shared order, and a
+    // field's list starts at the edits of the fields before it (fields lie
+    // in the shared space in order).  (2) Warps then take chunks from a
+    // shared queue, kListRoundsB at a time, so that the densely edited
+    // regions spread over the grid instead of the warps that own them; a
+    // chunk's edits go to the lanes in index order (ChunkBits), 32 a round,
+    // so that the stores coalesce.
+    const uint32_t CH = P.all.words / 32u;  // chunks of the shared space
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     const uint32_t nwarps = gridDim.x * wpb;
-    const uint32_t per = (W + nwarps - 1) / nwarps;
+    const uint32_t per = (CH + nwarps - 1) / nwarps;
     const uint32_t gw = blockIdx.x * wpb + warp;
-    const uint32_t w0 = min(gw * per, W), w1 = min(w0 + per, W);
-    uint32_t cnt = 0;
+    const uint32_t c0 = min(gw * per, CH), c1 = min(c0 + per, CH);
+    uint32_t cnt = 0;  // the warp's edits so far (warp-uniform)
     {
-        // per-field counts, kept in registers while a lane's words stay in
-        // one field
-        uint32_t cur = 0xffffffffu, ac = 0, au = 0;
+        uint32_t cur = 0xffffffffu, ac = 0, au = 0;  // lane 0: per-field counts of the current field
 #pragma unroll 4
-        for (uint32_t w = w0 + lane; w < w1; w += 32) {
-            const uint32_t c = __popc(P.eb[w]), u = __popc(P.ub[w]);
-            cnt += c;
-            if (!(c | u)) continue;
-            const uint32_t f = field_of(P.bfield, w * 32u);
-            if (f != cur) {
-                if (ac) atomicAdd(&s_cnt[cur][0], ac);
-                if (au) atomicAdd(&s_cnt[cur][1], au);
-                cur = f;
-                ac = au = 0;
+        for (uint32_t c = c0; c < c1; ++c) {
+            const uint32_t e = __reduce_add_sync(kFull, (uint32_t)__popc(P.eb[c * 32u + lane]));
+            const uint32_t u = __reduce_add_sync(kFull, (uint32_t)__popc(P.ub[c * 32u + lane]));
+            if (lane == 0) {
+                P.cpre[c] = cnt;  // warp-local for now
+                if (e | u) {
+                    const uint32_t f = field_of(P.bfield, c * 1024u);
+                    if (f != cur) {
+                        if (ac) atomicAdd(&s_cnt[cur][0], ac);
+                        if (au) atomicAdd(&s_cnt[cur][1], au);
+                        cur = f;
+                        ac = au = 0;
+                    }
+                    ac += e;
+                    au += u;
+                }
             }
-            ac += c;
-            au += u;
+            cnt += e;
         }
-        if (ac) atomicAdd(&s_cnt[cur][0], ac);
-        if (au) atomicAdd(&s_cnt[cur][1], au);
+        if (lane == 0) {
+            if (ac) atomicAdd(&s_cnt[cur][0], ac);
+            if (au) atomicAdd(&s_cnt[cur][1], au);
+        }
     }
     uint32_t tot;
-    const uint32_t wcnt = __reduce_add_sync(kFull, cnt);
-    const uint32_t wpre = block_exclusive_scan(lane == 0 ? wcnt : 0u, sm, tot);
+    const uint32_t wpre = block_exclusive_scan(lane == 0 ? cnt : 0u, sm, tot);
     const uint32_t warp_pre = __shfl_sync(kFull, wpre, 0);  // this warp's offset in its block
     if (threadIdx.x == 0) P.bsum[blockIdx.x] = tot;
     __syncthreads();
@@ -509,6 +519,10 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
     for (uint32_t b = threadIdx.x; b < blockIdx.x; b += blockDim.x) pre += ld_relaxed(&P.bsum[b]);
     uint32_t bpre;
     block_exclusive_scan(pre, sm, bpre);
+    {
+        const uint32_t base = bpre + warp_pre;
+        for (uint32_t c = c0 + lane; c < c1; c += 32u) P.cpre[c] += base;
+    }
     // s_tile reused: exclusive prefix of the per-field edit counts (one a
     // thread: nf <= blockDim.x; every count and their sum fit 32 bits)
     static_assert(MSZ_BATCH_MAX_FIELDS <= kThreads, "one field a thread in the edit-count scan");
@@ -518,9 +532,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
         const uint32_t ex = block_exclusive_scan(ec, sm, all_edits);
         if (threadIdx.x < nf) s_tile[threadIdx.x] = ex;
     }
-    __syncthreads();
-    uint32_t prefix = bpre + warp_pre;  // shared-order position of the warp's first edit
-    // edit j of a round (lane-picked vertex v, shared index): its field's
+    if (!grid_barrier(&C->bar_count, &C->bar_gen, &C->error)) return;
+    // edit j of a chunk (lane-picked vertex v, shared index): its field's
     // list position and value
     auto emit = [&](bool h, uint32_t v, uint32_t pos, float gv, float fv, uint32_t f) {
         if (!h) return;
@@ -531,26 +544,36 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
             D.edit_delta[q] = __fsub_rn(gv, fv);
         }
     };
-    auto gather = [&](bool h, uint32_t v, uint32_t &f, float &gv, float &fv) {
-        f = h ? field_of(P.bfield, v) : 0u;
+    auto gather = [&](bool h, uint32_t v, uint32_t f, float &gv, float &fv) {
         const FieldView &F = P.fields[f].F;
         const uint32_t i = h ? v - s_base[f] : 0u;
         gv = h ? F.g[i] : 0.f;
         fv = h ? __ldg(&F.fhat[i]) : 0.f;
     };
-    // kListRoundsB rounds at a time: their words loaded together, then the
-    // first 32 edits of each gathered before any is stored, and the next
-    // group's words loaded before this group's stores
     constexpr int R = kListRoundsB;
-    auto word_at = [&](uint32_t w) -> uint32_t { return w < w1 ? P.eb[w] : 0u; };
-    uint32_t wd[R];
+    uint32_t *const queue = &C->tcount[0];
+    uint32_t next = 0;
+    if (lane == 0) next = atomicAdd(queue, (uint32_t)R);
+    next = __shfl_sync(kFull, next, 0);
+    while (next < CH) {
+        const uint32_t g0 = next;
+        // the words and first positions of this grab's chunks, and the next
+        // grab, requested together
+        uint32_t wd[R], pos[R], fq[R];
 #pragma unroll
-    for (int q = 0; q < R; ++q) wd[q] = word_at(w0 + 32u * q + lane);
-    for (uint32_t r = w0; r < w1; r += 32u * R) {
-        ChunkBits cb[R] = {ChunkBits(r, wd[0]), ChunkBits(r + 32u, wd[1]), ChunkBits(r + 64u, wd[2]),
-                           ChunkBits(r + 96u, wd[3])};
+        for (int q = 0; q < R; ++q) {
+            const uint32_t c = g0 + (uint32_t)q;
+            wd[q] = c < CH ? P.eb[c * 32u + lane] : 0u;
+            pos[q] = c < CH ? P.cpre[c] : 0u;
+            fq[q] = c < CH ? field_of(P.bfield, c * 1024u) : 0u;
+        }
+        if (lane == 0) next = atomicAdd(queue, (uint32_t)R);
+        next = __shfl_sync(kFull, next, 0);
+        ChunkBits cb[R] = {ChunkBits((g0 + 0u) * 32u, wd[0]), ChunkBits((g0 + 1u) * 32u, wd[1]),
+                           ChunkBits((g0 + 2u) * 32u, wd[2]), ChunkBits((g0 + 3u) * 32u, wd[3])};
+        // the first 32 edits of every chunk gathered before any is stored
         bool h[R];
-        uint32_t v[R], fq[R];
+        uint32_t v[R];
         float gv[R], fv[R];
 #pragma unroll
         for (int q = 0; q < R; ++q) {
@@ -558,25 +581,22 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
             gather(h[q], v[q], fq[q], gv[q], fv[q]);
         }
 #pragma unroll
-        for (int q = 0; q < R; ++q) wd[q] = word_at(r + 32u * (R + q) + lane);
-#pragma unroll
         for (int q = 0; q < R; ++q) {
-            emit(h[q], v[q], prefix + lane, gv[q], fv[q], fq[q]);
+            emit(h[q], v[q], pos[q] + lane, gv[q], fv[q], fq[q]);
             // a chunk with more than 32 edits: the rest four rounds at a
             // time, gathers first
             for (uint32_t j0 = 32u; j0 < cb[q].total; j0 += 32u * R) {
                 bool hj[R];
-                uint32_t vj[R], fj[R];
+                uint32_t vj[R];
                 float gj[R], sj[R];
 #pragma unroll
                 for (int u = 0; u < R; ++u) {
                     cb[q].pick(j0 + 32u * u + lane, hj[u], vj[u]);
-                    gather(hj[u], vj[u], fj[u], gj[u], sj[u]);
+                    gather(hj[u], vj[u], fq[q], gj[u], sj[u]);
                 }
 #pragma unroll
-                for (int u = 0; u < R; ++u) emit(hj[u], vj[u], prefix + j0 + 32u * u + lane, gj[u], sj[u], fj[u]);
+                for (int u = 0; u < R; ++u) emit(hj[u], vj[u], pos[q] + j0 + 32u * u + lane, gj[u], sj[u], fq[q]);
             }
-            prefix += cb[q].total;
         }
     }
     if (!grid_barrier(&C->bar_count, &C->bar_gen, &C->error)) return;
@@ -767,6 +787,7 @@ extern "C" msz_status msz_batch_plan_create(int32_t n, const msz_field *fields, 
     P.stb = (uint32_t *)(ws + L.stb);
     P.sdm[0] = (uint32_t *)(ws + L.sd0);
     P.sdm[1] = (uint32_t *)(ws + L.sd1);
+    P.cpre = (uint32_t *)(ws + L.cpre);
     P.sparse_max = ntot / 256 > kSparseWorklistB ? ntot / 256 : kSparseWorklistB;
     P.bfield = (const uint8_t *)(ws + L.bfield);
     std::vector<uint8_t> bfield(ntot / 1024, 0);
