@@ -103,9 +103,10 @@ typedef struct {
     int64_t max_sweeps;       /* <= 0: MSZ_MAX_SWEEPS_LIMIT; else 1..MSZ_MAX_SWEEPS_LIMIT */
     int64_t dense_min_items;  /* > 0: the next sweep scans every uncertified vertex instead of
                                  the worklist when 6 x (vertices distorted in this sweep) >=
-                                 this; 0 (default): N on 3D grids (N: all fields' vertices in
-                                 msz_correct_batch), always the worklist on 2D ones; -1:
-                                 always the worklist.  Affects speed only, never results */
+                                 this; 0 (default): N on 3D grids, always the worklist on 2D
+                                 ones; -1: always the worklist.  The batch entry points decide
+                                 for each field by its own distorted count (and its own N).
+                                 Affects speed only, never results */
     const float *d_g_init;    /* NULL: start from fhat.  Else N floats, each in [L_i, U_i]: a
                                  proposed start (the learned proposal); edits are still
                                  reported against fhat */

@@ -86,7 +86,8 @@ struct BatchProblem {
     FieldRes *res;
     uint32_t *bsum;
     uint32_t max_sweeps;
-    long long dense_min;             // < 0: never scan whole fields after sweep 0
+    long long dense_min;             // < 0: never scan whole fields after sweep 0; 0: a field scans
+                                     // whole when 6 x its distorted >= its vertices; > 0: >= this
     uint32_t *tb, *dm[2], *eb, *ub;  // shared bitmaps (global words)
     const uint8_t *bfield;           // field of each 1024-vertex block
 };
@@ -277,6 +278,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
     __shared__ uint32_t s_tile[MSZ_BATCH_MAX_FIELDS + 1];
     __shared__ uint32_t s_cnt[MSZ_BATCH_MAX_FIELDS][4];
     __shared__ uint32_t s_alive[(MSZ_BATCH_MAX_FIELDS + 31) / 32];
+    __shared__ uint32_t s_dense[(MSZ_BATCH_MAX_FIELDS + 31) / 32];  // fields whose next detection scans whole
+    __shared__ uint32_t s_dtile[MSZ_BATCH_MAX_FIELDS + 1];          // prefix of those fields' tile counts
     __shared__ uint32_t s_next;
     __shared__ unsigned long long s_sum, s_chg;
     __shared__ uint32_t sm[40];
@@ -293,6 +296,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
     for (uint32_t i = threadIdx.x; i < (nf + 31) / 32; i += blockDim.x) s_alive[i] = 0xffffffffu;
     __syncthreads();
     auto alive = [&](uint32_t k) { return (s_alive[k >> 5] >> (k & 31u)) & 1u; };
+    auto dense = [&](uint32_t k) { return (s_dense[k >> 5] >> (k & 31u)) & 1u; };
     bool ok = ld_relaxed(&C->error) == 0;  // every block reads k_batch_codes' verdict
     if (leader) C->t_codes = global_ns();
     // Chunk flags are kept only in sparse sweeps.  sum_k: the phases of
@@ -306,6 +310,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
         BatchRec *rec = P.log + (size_t)k * nf;
         // every block derives the same verdicts from the same records
         if (threadIdx.x == 0) s_sum = s_chg = 0;
+        for (uint32_t i = threadIdx.x; i < (nf + 31) / 32; i += blockDim.x) s_dense[i] = 0u;
         __syncthreads();
         unsigned long long m_all = 0;
         for (uint32_t f = threadIdx.x; f < nf; f += blockDim.x) {
@@ -313,6 +318,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
             const uint32_t m = ld_relaxed(&rec[f].distorted);
             if (m == 0) atomicAnd(&s_alive[f >> 5], ~(1u << (f & 31u)));  // done
             m_all += m;
+            // whole-field scans for this field's next sweep, as msz_correct
+            // decides them for the field alone
+            const unsigned long long lim = P.dense_min > 0 ? (unsigned long long)P.dense_min
+                                                           : (unsigned long long)P.fields[f].F.G.n;
+            if (m && P.dense_min >= 0 && (unsigned long long)m * kDenseFactorB >= lim)
+                atomicOr(&s_dense[f >> 5], 1u << (f & 31u));
         }
         if (m_all) atomicAdd(&s_sum, m_all);
         __syncthreads();
@@ -337,9 +348,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
             ok = grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
             break;
         }
-        // whole-field scans for the next sweep (one verdict for every field)
-        const bool dense_next = P.dense_min >= 0 && m_tot * kDenseFactorB >= (unsigned long long)P.dense_min;
-        // ---- edit phase of sweep k
+        // ---- edit phase of sweep k (targets of a field whose next detection
+        // scans whole mark no worklist)
         {
             uint32_t targets = 0;
             uint32_t *const dsum = sum_k ? P.sdm[(k + 1) & 1] : nullptr;
@@ -349,7 +359,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
                 bool changed = false;
                 if (live) {
                     const FieldView &F = P.fields[f].F;
-                    changed = apply_target<3>(F, t - s_base[f], dense_next, F.dm[(k + 1) & 1],
+                    changed = apply_target<3>(F, t - s_base[f], dense(f) != 0u, F.dm[(k + 1) & 1],
                                               field_flags(dsum, s_base[f]));
                 }
                 // counts per field, aggregated over the warp's lanes of one field
@@ -394,29 +404,35 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
         {
             const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
             for (uint32_t f = gtid; f < nf; f += stride)
-                if (alive(f) && dense_next) {
+                if (alive(f) && dense(f)) {
                     rec1[f].worklist = P.fields[f].F.G.n;
                     rec1[f].dense = 1;
                 }
-            if (dense_next) {
-                // whole-field scans: every uncertified vertex of a live field,
-                // tile by tile over the shared tile queue (g staged in shared
-                // memory); the worklist bitmap is cleared for the next sweep
-                for (uint32_t w = gtid; w < P.all.words; w += stride) dcur[w] = 0u;
-                if (sum_k)
-                    for (uint32_t c = gtid; c < P.all.words / 32u; c += stride) P.sdm[k1 & 1][c] = 0u;
+            // whole-field scans: every uncertified vertex of each live field
+            // that scans whole, tile by tile over a queue of those fields'
+            // tiles (g staged in shared memory)
+            {
+                const uint32_t f = threadIdx.x;
+                const uint32_t tc = f < nf && alive(f) && dense(f) ? s_tile[f + 1] - s_tile[f] : 0u;
+                uint32_t total;
+                const uint32_t ex = block_exclusive_scan(tc, sm, total);
+                if (f < nf) s_dtile[f] = ex;
+                if (f == 0) s_dtile[nf] = total;
+                __syncthreads();
+            }
+            const uint32_t dtiles = s_dtile[nf];
+            if (dtiles) {
                 uint32_t *counter = &rec1[0].pad[0];
                 for (;;) {
                     __syncthreads();
                     if (threadIdx.x == 0) s_next = atomicAdd(counter, 1u);
                     __syncthreads();
                     const uint32_t t = s_next;
-                    if (t >= P.ntiles) break;
-                    const uint32_t f = find_field(s_tile, nf, t);
-                    if (!alive(f)) continue;
+                    if (t >= dtiles) break;
+                    const uint32_t f = find_field(s_dtile, nf, t);
                     const FieldView &F = P.fields[f].F;
                     const tile::TileGeom tg = tile::tile_geom(F.G.nx, F.G.ny, F.G.nz, F.tile_z);
-                    const uint32_t lt = t - s_tile[f];
+                    const uint32_t lt = t - s_dtile[f];
                     const uint32_t txi = lt % tg.tx, tyi = (lt / tg.tx) % tg.ty, tzi = lt / (tg.tx * tg.ty);
                     const int zb = (int)(tzi * tg.bz);
                     uint32_t dist = 0;
@@ -425,26 +441,25 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
                                    field_flags(dsum1, s_base[f]), field_flags(tsum1, s_base[f]));
                     warp_add(dist, &s_cnt[f][1]);
                 }
-            } else {
-                // per word: the uncertified vertices of a live field's
-                // worklist; done fields none.  The worklist is cleared as it
-                // is read (a word never straddles two fields: bases are
-                // 1024-aligned).
-                auto fetch = [&](uint32_t wi) -> uint32_t { return dcur[wi]; };
-                auto finish = [&](uint32_t wi, uint32_t wl) -> uint32_t {
-                    const uint32_t f = field_of(P.bfield, wi * 32u);
-                    if (wl) dcur[wi] = 0u;
-                    if (!alive(f)) return 0u;
-                    if (!wl) return 0u;
-                    atomicAdd(&s_cnt[f][0], (uint32_t)__popc(wl));
-                    return wl & P.ub[wi];
-                };
-                auto detect = [&](bool h1, uint32_t v1, bool h2, uint32_t v2) {
-                    detect_pair(P, s_base, nf, s_cnt, (k1 + 1) & 1, sum_k1, alive, h1, v1, h2, v2);
-                };
-                if (sum_k) walk_flagged_words(P.sdm[k1 & 1], P.all, fetch, finish, rq, detect);
-                else walk_words_pairs(P.all, fetch, finish, detect, rq);
             }
+            // the other live fields: per word, the uncertified vertices of
+            // the worklist.  Every word is cleared as it is read (dead fields
+            // and fields that scanned whole contribute nothing; a word never
+            // straddles two fields: bases are 1024-aligned).
+            auto fetch = [&](uint32_t wi) -> uint32_t { return dcur[wi]; };
+            auto finish = [&](uint32_t wi, uint32_t wl) -> uint32_t {
+                if (!wl) return 0u;
+                dcur[wi] = 0u;
+                const uint32_t f = field_of(P.bfield, wi * 32u);
+                if (!alive(f) || dense(f)) return 0u;
+                atomicAdd(&s_cnt[f][0], (uint32_t)__popc(wl));
+                return wl & P.ub[wi];
+            };
+            auto detect = [&](bool h1, uint32_t v1, bool h2, uint32_t v2) {
+                detect_pair(P, s_base, nf, s_cnt, (k1 + 1) & 1, sum_k1, alive, h1, v1, h2, v2);
+            };
+            if (sum_k) walk_flagged_words(P.sdm[k1 & 1], P.all, fetch, finish, rq, detect);
+            else walk_words_pairs(P.all, fetch, finish, detect, rq);
         }
         flush_counts(s_cnt, nf, rec1);
         ok = grid_barrier(&C->bar_count, &C->bar_gen, &C->error);
@@ -775,10 +790,9 @@ extern "C" msz_status msz_batch_plan_create(int32_t n, const msz_field *fields, 
     P.res = (FieldRes *)(ws + L.res);
     P.bsum = (uint32_t *)(ws + L.bsum);
     P.max_sweeps = max_sweeps;
-    // default: every field scans whole while 6 x (all fields' distorted
-    // vertices) >= N, as in msz_correct (on the batch of 64 fields: 23.2 ms
-    // against 24.3 at N/4 and N/16 and 23.1 with worklists only)
-    P.dense_min = o.dense_min_items == 0 ? (long long)(ntot > 0 ? ntot : 1) : (long long)o.dense_min_items;
+    // default: each field scans whole while 6 x its distorted vertices >=
+    // its vertex count, the rule msz_correct applies to it alone
+    P.dense_min = (long long)o.dense_min_items;
     P.tb = (uint32_t *)(ws + L.tb);
     P.dm[0] = (uint32_t *)(ws + L.d0);
     P.dm[1] = (uint32_t *)(ws + L.d1);
