@@ -524,22 +524,38 @@ class BatchResult:
 
 
 def _batch_fields(fs, fhats, xis, edit_capacities, outs, tile_z):
-    """The msz_field array of a batch and the output buffers it points to."""
+    """The msz_field array of a batch and the output buffers it points to:
+    (outs, edit_idx, edit_delta, offsets, capacities), the edit lists of all
+    fields in one pair of buffers (field k's at offsets[k])."""
     n = len(fs)
-    arr = (Field * n)()
-    keep = []
+    arr = (Field * n)()  # zero-filled: stats, edit_count and reserved start at 0
+    caps = [fs[k].numel() if edit_capacities is None else int(edit_capacities[k]) for k in range(n)]
+    offs, tot = [], 0
+    for c in caps:
+        offs.append(tot)
+        tot += max(c, 1)
+    dev = fs[0].device
+    idx_all = torch.empty(tot, dtype=torch.int32, device=dev)
+    dl_all = torch.empty(tot, dtype=torch.float32, device=dev)
+    ib, db = _dptr(idx_all), _dptr(dl_all)
+    outs = [torch.empty_like(f) for f in fs] if outs is None else list(outs)
     for k in range(n):
         f, fh = fs[k], fhats[k]
         assert f.dtype == torch.float32 and fh.dtype == torch.float32 and f.shape == fh.shape and f.dim() == 3
-        cap = f.numel() if edit_capacities is None else int(edit_capacities[k])
-        out = torch.empty_like(f) if outs is None else outs[k]
-        idx = torch.empty(max(cap, 1), dtype=torch.int32, device=f.device)
-        dl = torch.empty(max(cap, 1), dtype=torch.float32, device=f.device)
-        keep.append((out, idx, dl, cap))
-        tz = 0 if tile_z is None else int(tile_z[k])
-        arr[k] = Field(_dptr(f), _dptr(fh), ctypes.c_float(np.float32(xis[k])), -1, grid_of(f.shape), _dptr(out),
-                       _dptr(idx), _dptr(dl), cap, 0, Stats(), tz, 0)
-    return arr, keep
+        fk = arr[k]
+        fk.d_f = _dptr(f)
+        fk.d_fhat = _dptr(fh)
+        fk.xi = float(np.float32(xis[k]))
+        fk.status = -1
+        nz, ny, nx = f.shape
+        g = fk.grid
+        g.ndim, g.nx, g.ny, g.nz = 3, int(nx), int(ny), int(nz)
+        fk.d_out = _dptr(outs[k])
+        fk.d_edit_idx = ib + 4 * offs[k]
+        fk.d_edit_delta = db + 4 * offs[k]
+        fk.edit_capacity = caps[k]
+        fk.tile_z = 0 if tile_z is None else int(tile_z[k])
+    return arr, (outs, idx_all, dl_all, offs, caps)
 
 
 def _batch_workspace(lib, arr, max_sweeps, ws, device):
@@ -549,17 +565,32 @@ def _batch_workspace(lib, arr, max_sweeps, ws, device):
     return workspace(need, device) if ws is None else ws
 
 
+_NO_SWEEP_LOG = np.zeros((0, 4), np.int64)
+# the outputs of an msz_field array read as one numpy record each (offsets
+# from the ctypes layout)
+_FIELD_OUT = np.dtype({"names": ["status", "edit_count", "stats"],
+                       "formats": [np.int32, np.int64, (np.int64, len(_STATS_NAMES))],
+                       "offsets": [Field.status.offset, Field.edit_count.offset, Field.stats.offset],
+                       "itemsize": ctypes.sizeof(Field)})
+
+
 def _batch_results(arr, keep, log, log_capacity, status, timeline=None) -> "BatchResult":
+    outs, idx_all, dl_all, offs, caps = keep
+    rec = np.frombuffer(arr, dtype=_FIELD_OUT)
+    counts = rec["edit_count"].tolist()
+    statuses = rec["status"].tolist()
+    stats = rec["stats"].tolist()
     results = []
     for k in range(len(arr)):
-        out, idx, dl, cap = keep[k]
-        fk = arr[k]
-        m = min(int(fk.edit_count), cap)
-        stats = fk.stats.as_dict()
-        nlog = min(stats["sweeps"] + 1, log_capacity)
-        lg = log[4 * k * log_capacity:4 * (k * log_capacity + nlog)].reshape(-1, 4).copy() if log_capacity else \
-            np.zeros((0, 4), np.int64)
-        results.append(CorrectResult(int(fk.status), out, idx[:m], dl[:m], int(fk.edit_count), stats, lg))
+        m = min(counts[k], caps[k])
+        st = dict(zip(_STATS_NAMES, stats[k]))
+        if log_capacity:
+            nlog = min(st["sweeps"] + 1, log_capacity)
+            lg = log[4 * k * log_capacity:4 * (k * log_capacity + nlog)].reshape(-1, 4).copy()
+        else:
+            lg = _NO_SWEEP_LOG
+        o = offs[k]
+        results.append(CorrectResult(statuses[k], outs[k], idx_all[o:o + m], dl_all[o:o + m], counts[k], st, lg))
     tl = timeline.reshape(-1, 2).copy() if timeline is not None else np.zeros((0, 2), np.int64)
     return BatchResult(int(status), results, tl)
 
@@ -587,7 +618,9 @@ class BatchPlan:
     @property
     def outputs(self):
         """(out, edit_idx, edit_delta, capacity) of every field."""
-        return self._keep[2]
+        outs, idx_all, dl_all, offs, caps = self._keep[2]
+        return [(outs[k], idx_all[offs[k]:offs[k] + max(caps[k], 1)], dl_all[offs[k]:offs[k] + max(caps[k], 1)],
+                 caps[k]) for k in range(len(outs))]
 
     def launch(self, stream=None) -> None:
         st = self._lib.msz_batch_launch(self._h, _stream(stream))

@@ -153,6 +153,18 @@ __device__ __forceinline__ void flush_counts(uint32_t (*cnt)[4], uint32_t nf, Ba
     __syncthreads();
 }
 
+// Eq. 1 on target t of field F (HALVE or SNAP, the rules a batch takes)
+// with its current value gt and f_t already loaded: as apply_target.
+__device__ __forceinline__ bool edit_loaded(const FieldView &F, uint32_t t, float gt, float ft, bool dense_next,
+                                            uint32_t *dnext, uint32_t *dsum) {
+    float h;
+    if (!edit_value(gt, floor_bound(ft, F.xi), F.rule, h)) return false;
+    F.g[t] = h;
+    red_or(&F.eb[t >> 5], 1u << (t & 31u));
+    if (!dense_next) mark_closed<3>(F.G, t, dnext, dsum);
+    return true;
+}
+
 // A field's view of shared-space chunk flags (null stays null): field bases
 // are 1024-aligned, so a field-local vertex v has chunk (base >> 10) + (v >> 10).
 __device__ __forceinline__ uint32_t *field_flags(uint32_t *flags, uint32_t base) {
@@ -353,16 +365,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
         {
             uint32_t targets = 0;
             uint32_t *const dsum = sum_k ? P.sdm[(k + 1) & 1] : nullptr;
-            auto edit = [&](bool has, uint32_t t) {
-                const uint32_t f = has ? field_of(P.bfield, t) : 0u;
-                const bool live = has && alive(f);
-                bool changed = false;
-                if (live) {
-                    const FieldView &F = P.fields[f].F;
-                    changed = apply_target<3>(F, t - s_base[f], dense(f) != 0u, F.dm[(k + 1) & 1],
-                                              field_flags(dsum, s_base[f]));
-                }
-                // counts per field, aggregated over the warp's lanes of one field
+            // counts per field, aggregated over the warp's lanes of one field
+            auto count = [&](bool live, uint32_t f, bool changed) {
                 const uint32_t peers = __match_any_sync(kFull, live ? f : 0xffffffffu);
                 const uint32_t nch = (uint32_t)__popc(peers & __ballot_sync(kFull, changed));
                 if (live && lane_id() == (uint32_t)(__ffs(peers) - 1)) {
@@ -370,8 +374,24 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
                     if (nch) atomicAdd(&s_cnt[f][3], nch);
                 }
             };
-            if (!sum_k) walk_bits<true>(P.tb, nullptr, P.all, targets, edit, rq);
-            else walk_flagged<true, false>(P.tb, P.stb, nullptr, P.all, targets, rq, edit);
+            // two targets a lane: both loads in flight before either edit
+            auto edit2 = [&](bool h1, uint32_t t1, bool h2, uint32_t t2) {
+                const uint32_t f1 = h1 ? field_of(P.bfield, t1) : 0u, f2 = h2 ? field_of(P.bfield, t2) : 0u;
+                const bool l1 = h1 && alive(f1), l2 = h2 && alive(f2);
+                const FieldView &F1 = P.fields[f1].F;
+                const FieldView &F2 = P.fields[f2].F;
+                const uint32_t i1 = l1 ? t1 - s_base[f1] : 0u, i2 = l2 ? t2 - s_base[f2] : 0u;
+                const float g1 = l1 ? F1.g[i1] : 0.f, v1 = l1 ? __ldg(&F1.f[i1]) : 0.f;
+                const float g2 = l2 ? F2.g[i2] : 0.f, v2 = l2 ? __ldg(&F2.f[i2]) : 0.f;
+                const bool c1 = l1 && edit_loaded(F1, i1, g1, v1, dense(f1) != 0u, F1.dm[(k + 1) & 1],
+                                                  field_flags(dsum, s_base[f1]));
+                const bool c2 = l2 && edit_loaded(F2, i2, g2, v2, dense(f2) != 0u, F2.dm[(k + 1) & 1],
+                                                  field_flags(dsum, s_base[f2]));
+                count(l1, f1, c1);
+                count(l2, f2, c2);
+            };
+            if (!sum_k) walk_bits_pairs<true>(P.tb, nullptr, P.all, targets, edit2, AllWords(), rq);
+            else walk_flagged<true, true>(P.tb, P.stb, nullptr, P.all, targets, rq, edit2);
             (void)targets;
             flush_counts(s_cnt, nf, rec);
         }
