@@ -468,7 +468,7 @@ def run_ours(args, ws, rank, local):
         del f, fh, out, eidx, edel, hf, hfh, hout, hidx, hdel, hout2, hidx2, hdel2, sets
         api._ws_cache.clear()
         torch.cuda.empty_cache()
-        line["batch"] = run_batch(dev, stream, sm_mhz=clk.get("sm_mhz"))
+        line["batch"] = run_batch(dev, stream, sm_mhz=clk.get("sm_mhz"), count=args.batch_fields)
     if rank == 0 and args.large:
         f = fh = out = None  # drop the 512^3 buffers (if the batch leg has not already)
         api._ws_cache.clear()
@@ -609,15 +609,16 @@ def run_configs(dev, stream, reps: int = 5) -> dict:
     return out
 
 
-def run_batch(dev, stream, reps: int = 5, sm_mhz: float | None = None) -> dict:
+def run_batch(dev, stream, reps: int = 5, sm_mhz: float | None = None, count: int = 64) -> dict:
     """Secondary workload: 64 prequantized Perlin fields, axes uniform in
     64..384, eb_rel in {1e-3, 1e-4, 1e-5} (seeds 1000+k), corrected by one
     msz_correct_batch launch (tile depths from the autotuner), against the same
-    fields corrected by 64 separate msz_correct calls."""
+    fields corrected by 64 separate msz_correct calls.  count < 64: the first
+    count fields of that batch (profiling captures only)."""
     import torch
 
     from paper_2601_01787_gb300 import api, autotune, synth
-    fields = synth.batch(64)
+    fields = synth.batch(64)[:count]
     n_tot = sum(fl.n for fl in fields)
     fs = [torch.from_numpy(fl.f).to(dev) for fl in fields]
     fhs = [torch.from_numpy(fl.fhat).to(dev) for fl in fields]
@@ -677,8 +678,10 @@ def run_batch(dev, stream, reps: int = 5, sm_mhz: float | None = None) -> dict:
             "peak": round(alu_pk, 1), "unit": "Gop/s", "frac": round(ops / t_s / 1e9 / alu_pk, 4),
             "hbm": {"algorithmic_bytes": nbytes, "achieved": round(nbytes / t_s / 1e9, 1), "peak": peak,
                     "unit": "GB/s", "frac": round(nbytes / t_s / 1e9 / peak, 4), "peak_kind": peak_kind,
-                    "traffic": traffic_record("k_batch_perlin64_traffic.json", "msz_batch.cu")}}
-    return {"workload": "perlin3d_prequant batch of 64, axes U{64..384}, eb_rel in {1e-3,1e-4,1e-5}, seeds 1000+k",
+                    "traffic": traffic_record("k_batch_perlin64_traffic.json", "msz_batch.cu") if count == 64
+                    else None}}
+    what = "batch of 64" if count == 64 else f"first {count} fields of the batch of 64"
+    return {"workload": f"perlin3d_prequant {what}, axes U{{64..384}}, eb_rel in {{1e-3,1e-4,1e-5}}, seeds 1000+k",
             "n_vertices": n_tot, "unit": UNIT, "value": round(n_tot / (t_batch * 1e-3) / 1e9, 4),
             "ms": round(t_batch, 4), "graph_replay_ms": round(t_graph, 4),
             "graph_replay_value": round(n_tot / (t_graph * 1e-3) / 1e9, 4), "separate_calls_ms": round(t_single, 4),
@@ -1024,6 +1027,8 @@ def main(argv=None):
     ap.add_argument("--cpu-slab", type=int, default=128, help="z-planes of the CPU-baseline sample")
     ap.add_argument("--ref-slab", type=int, default=24, help="z-planes per reference-arm step")
     ap.add_argument("--shape", default=None, help="nz,ny,nx of a smaller field (profiling captures only)")
+    ap.add_argument("--batch-fields", type=int, default=64,
+                    help="the first N fields of the 64-field batch (profiling captures only)")
     ap.add_argument("--profile-conv", action="store_true",
                     help="run two learned proposals on a --shape peak field and exit (profiling captures only)")
     args = ap.parse_args(argv)
@@ -1032,6 +1037,8 @@ def main(argv=None):
         SHAPE = tuple(int(v) for v in args.shape.split(","))
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if not 1 <= args.batch_fields <= 64:
+        ap.error("--batch-fields must be in 1..64")
     if args.profile_conv:
         profile_conv(args)
         return

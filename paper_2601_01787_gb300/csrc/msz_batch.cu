@@ -153,6 +153,18 @@ __device__ __forceinline__ void flush_counts(uint32_t (*cnt)[4], uint32_t nf, Ba
     __syncthreads();
 }
 
+// A tile's field view, staged in shared memory by the whole block: the tile
+// passes read its members many times a row, and global loads of them miss the
+// L1 that the plane rings leave small.  Block-collective; the caller has
+// synchronized the block since the last use of buf.
+constexpr uint32_t kFieldWords = (uint32_t)(sizeof(FieldView) / 4);
+static_assert(sizeof(FieldView) % 4 == 0 && alignof(FieldView) <= 16, "FieldView is copied as aligned words");
+__device__ __forceinline__ void stage_field(uint32_t *buf, const FieldView &src) {
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(&src);
+    for (uint32_t i = threadIdx.x; i < kFieldWords; i += blockDim.x) buf[i] = w[i];
+    __syncthreads();
+}
+
 // Eq. 1 on target t of field F (HALVE or SNAP, the rules a batch takes)
 // with its current value gt and f_t already loaded: as apply_target.
 __device__ __forceinline__ bool edit_loaded(const FieldView &F, uint32_t t, float gt, float ft, bool dense_next,
@@ -252,6 +264,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch_codes(__grid_co
     __shared__ uint32_t s_tile[MSZ_BATCH_MAX_FIELDS + 1];
     __shared__ uint32_t s_cnt[MSZ_BATCH_MAX_FIELDS][4];
     __shared__ uint32_t s_next;
+    __shared__ __align__(16) uint32_t s_F[kFieldWords];  // the current tile's field view
+    const FieldView &F = *reinterpret_cast<const FieldView *>(s_F);
+    uint32_t staged = 0xffffffffu;                      // its field (block-uniform)
     const uint32_t nf = P.nfields;
     Ctrl *C = P.ctrl;
     for (uint32_t k = threadIdx.x; k <= nf; k += blockDim.x) s_tile[k] = k < nf ? P.fields[k].tile_base : P.ntiles;
@@ -266,7 +281,10 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch_codes(__grid_co
         const uint32_t t = s_next;
         if (t >= P.ntiles) break;
         const uint32_t k = find_field(s_tile, nf, t);
-        const FieldView &F = P.fields[k].F;
+        if (k != staged) {
+            stage_field(s_F, P.fields[k].F);
+            staged = k;
+        }
         const tile::TileGeom tg = tile::tile_geom(F.G.nx, F.G.ny, F.G.nz, F.tile_z);
         const uint32_t lt = t - s_tile[k];
         const uint32_t txi = lt % tg.tx, tyi = (lt / tg.tx) % tg.ty, tzi = lt / (tg.tx * tg.ty);
@@ -296,6 +314,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
     __shared__ unsigned long long s_sum, s_chg;
     __shared__ uint32_t sm[40];
     __shared__ uint32_t s_rq[kThreads / 32][kRoundCap];  // each warp's round queue
+    __shared__ __align__(16) uint32_t s_F[kFieldWords];   // the current tile's field view (whole-field scans)
     uint32_t *rq = s_rq[threadIdx.x >> 5];
     const uint32_t nf = P.nfields;
     Ctrl *C = P.ctrl;
@@ -443,6 +462,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
             const uint32_t dtiles = s_dtile[nf];
             if (dtiles) {
                 uint32_t *counter = &rec1[0].pad[0];
+                const FieldView &F = *reinterpret_cast<const FieldView *>(s_F);
+                uint32_t staged = 0xffffffffu;  // the field of s_F (block-uniform)
                 for (;;) {
                     __syncthreads();
                     if (threadIdx.x == 0) s_next = atomicAdd(counter, 1u);
@@ -450,7 +471,10 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksB) k_batch(__grid_constant
                     const uint32_t t = s_next;
                     if (t >= dtiles) break;
                     const uint32_t f = find_field(s_dtile, nf, t);
-                    const FieldView &F = P.fields[f].F;
+                    if (f != staged) {
+                        stage_field(s_F, P.fields[f].F);
+                        staged = f;
+                    }
                     const tile::TileGeom tg = tile::tile_geom(F.G.nx, F.G.ny, F.G.nz, F.tile_z);
                     const uint32_t lt = t - s_dtile[f];
                     const uint32_t txi = lt % tg.tx, tyi = (lt / tg.tx) % tg.ty, tzi = lt / (tg.tx * tg.ty);
