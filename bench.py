@@ -290,8 +290,10 @@ def run_ours(args, ws, rank, local):
     loop_ms = statistics.mean(b.elapsed_time(c) for _, b, c in kev)
     codes_gbs = alg_codes / (codes_ms * 1e-3) / 1e9
     loop_gbs = alg_loop / (loop_ms * 1e-3) / 1e9
-    traffic_codes = traffic_record("k_codes_perlin512_traffic.json", "msz_correct.cu")
-    traffic_loop = traffic_record("k_correct_perlin512_traffic.json", "msz_correct.cu")
+    # the records were taken of the 512^3 workload: none for a --shape run
+    full = SHAPE == (512, 512, 512)
+    traffic_codes = traffic_record("k_codes_perlin512_traffic.json", "msz_correct.cu") if full else None
+    traffic_loop = traffic_record("k_correct_perlin512_traffic.json", "msz_correct.cu") if full else None
 
     # k_codes against the ALU-pipe peak (the pipe that bounds it)
     alu_ops = codes_alu_ops(n, unc)
