@@ -59,3 +59,11 @@ def test_codes_kernel_share_of_the_counts():
     assert rest == 5 * int(LOG[1:, 0].sum()) + 12 * int(LOG[:, 2].sum()) + N // 8 + 8 * EDITED
     assert bench.codes_alu_ops(N, UNCERT) == bench.ALU_OPS_CERT * N + 2 * bench.ALU_OPS_CODE * UNCERT
     assert bench.codes_alu_ops(N, UNCERT) < bench.algorithmic_alu_ops(N, LOG, UNCERT)
+
+
+def test_argument_checks():
+    import pytest
+    for argv in (["--warmup", "2"], ["--batch-fields", "0"], ["--batch-fields", "65"]):
+        with pytest.raises(SystemExit) as e:
+            bench.main(argv)
+        assert e.value.code == 2  # argparse's usage error, before any GPU work
