@@ -206,3 +206,60 @@ def test_encoded_pipeline_arguments_on_host():
     assert lib.msz_pipeline_submit_encoded(None, fake, fake, ctypes.c_float(0.1), fake, 64, None) == \
         api.ERR_INVALID_ARG
     assert lib.msz_pipeline_collect_encoded(None, ctypes.byref(cnt), ctypes.byref(nb), None) == api.ERR_INVALID_ARG
+
+
+def test_batch_arguments_rejected_on_host():
+    """msz_batch_workspace_size and the batch's argument and workspace checks
+    run before any CUDA call."""
+    from paper_2601_01787_gb300 import api
+    lib = api.load()
+    fake = 256
+
+    def fields(shapes, **kw):
+        arr = (api.Field * len(shapes))()
+        for k, shp in enumerate(shapes):
+            fk = arr[k]
+            fk.d_f = fk.d_fhat = fk.d_out = fake
+            fk.xi = kw.get("xi", 0.1)
+            fk.grid = api.grid_of(shp)
+            fk.edit_capacity = kw.get("cap", 0)
+            if fk.edit_capacity > 0 and not kw.get("no_lists"):
+                fk.d_edit_idx = fk.d_edit_delta = fake
+        return arr
+
+    good = fields([(4, 5, 6), (7, 3, 9)])
+    size = lib.msz_batch_workspace_size(2, good, 0)
+    assert size > 0
+    assert lib.msz_batch_workspace_size(2, good, 8) < size             # a smaller sweep cap, a smaller log
+    assert lib.msz_batch_workspace_size(0, good, 0) == 0
+    assert lib.msz_batch_workspace_size(api.BATCH_MAX_FIELDS + 1, fields([(2, 2, 2)] * 257), 0) == 0
+    assert lib.msz_batch_workspace_size(1, fields([(5, 6)]), 0) == 0       # 3D only
+    assert lib.msz_batch_workspace_size(2, good, api.BATCH_MAX_SWEEPS + 1) == 0
+
+    plan = ctypes.c_void_p()
+
+    def create(arr, n=None, opt=None, ws_bytes=1 << 40):
+        n = len(arr) if n is None else n
+        return lib.msz_batch_plan_create(n, arr, ctypes.byref(opt) if opt is not None else None, fake, ws_bytes,
+                                         None, ctypes.byref(plan))
+
+    def options(**kw):
+        opt, _ = api._options(kw.get("rule", "halve"), kw.get("max_sweeps", 0), kw.get("dense", 0), None, 0)
+        opt.test_fault = kw.get("fault", 0)
+        if kw.get("g_init"):
+            opt.d_g_init = fake
+        return opt
+
+    assert create(good, n=0) == api.ERR_INVALID_ARG
+    assert create(fields([(5, 6)])) == api.ERR_INVALID_ARG                       # 2D field
+    assert create(good, opt=options(rule="below")) == api.ERR_INVALID_ARG  # HALVE or SNAP only
+    assert create(good, opt=options(g_init=True)) == api.ERR_INVALID_ARG        # no proposed start
+    assert create(good, opt=options(fault=1)) == api.ERR_INVALID_ARG            # no test hook
+    assert create(good, opt=options(max_sweeps=api.BATCH_MAX_SWEEPS + 1)) == api.ERR_INVALID_ARG
+    assert create(good, opt=options(dense=-2)) == api.ERR_INVALID_ARG
+    assert create(fields([(4, 5, 6)], xi=-1.0)) == api.ERR_INVALID_ARG
+    assert create(fields([(4, 5, 6)], xi=float("inf"))) == api.ERR_INVALID_ARG
+    assert create(fields([(4, 5, 6)], cap=-1)) == api.ERR_INVALID_ARG
+    assert create(fields([(4, 5, 6)], cap=10, no_lists=True)) == api.ERR_INVALID_ARG  # lists asked for, no buffers
+    assert create(good, ws_bytes=size - 1) == api.ERR_WORKSPACE
+    assert not plan.value  # no plan was made
